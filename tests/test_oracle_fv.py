@@ -1,0 +1,159 @@
+"""Pins of the oracle preconditioner pieces (Sec. 3.2-3.5)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.dg import DG
+from oracle.fv import FVLevel, Multigrid, Transfer, hierarchy, parse_mg_key, prolong, restrict
+from oracle.physics import Physics, UNIFORM
+from oracle.solver import fgmres, norm
+from oracle.tables import midpoint_weights
+
+ROBERT = Physics(cp=1005.0, cv=717.95, g=9.80665, p0=1e5, theta0=300.0)
+VISC = Physics(cp=1004.0, cv=717.0, g=9.81, p0=1e5, theta0=300.0, mu=75.0)
+
+
+def test_mg_key_parser():
+    assert parse_mg_key("mg111111V") == dict(dg_pre=1, dg_post=1, fine_pre=1, fine_post=1,
+                                             mid_pre=1, mid_post=1, cycles=1)
+    assert parse_mg_key("mg001121W")["cycles"] == 2
+    assert parse_mg_key("mg001121W")["mid_pre"] == 2
+    with pytest.raises(ValueError):
+        parse_mg_key("mg11111V")
+
+
+def test_hierarchy_level_counts_of_the_workloads():
+    # Q2 20x10 -> 3 levels; Q3 160x80 -> 5 levels; Q2 256x32 -> 4 levels
+    assert hierarchy(20, 10, 2, 3)[0] == [(60, 30), (20, 10), (10, 5)]
+    assert hierarchy(160, 80, 3, 5)[0] == [(640, 320), (320, 160), (160, 80), (80, 40), (40, 20)]
+    assert hierarchy(256, 32, 2, 4)[0] == [(768, 96), (256, 32), (128, 16), (64, 8)]
+    # the paper's k = 3 case: the subgrid adds two levels above the DG grid (Sec. 4)
+    s, f = hierarchy(8, 8, 3, 10)
+    assert s[2] == (8, 8) and f[:2] == [2, 2]
+
+
+@pytest.mark.parametrize("ph", [ROBERT, VISC])
+def test_fv_well_balanced(ph):
+    lev = FVLevel(12, 8, 0, 6000, 0, 4000, ph)
+    f = lev.rhs(np.zeros(lev.shape))
+    if ph.mu == 0:
+        assert np.all(f == 0.0)
+    else:
+        assert np.abs(f).max() < 1e-14 * 75 * 300 / 500.0 ** 2 * 10
+
+
+def test_fv_free_stream_and_conservation():
+    ph = Physics(cp=3.5, cv=2.5, g=0.0, p0=1.0, theta0=1.0, background=UNIFORM, ubg=0.2)
+    lev = FVLevel(6, 5, 0, 1, 0, 1, ph, periodic_x=True)
+    up = np.zeros(lev.shape)
+    up[0] += 0.1
+    up[1] += 0.02
+    up[3] += 0.1
+    assert np.abs(lev.rhs(up)).max() < 1e-14
+    lev = FVLevel(7, 5, 0, 7000, 0, 5000, VISC)
+    up = synth.random_perturbation(lev.shape[1:], 4, scales=(1e-2, 2, 2, 1))
+    f = lev.rhs(up)
+    for v in (0, 3):
+        assert abs(f[v].sum()) <= 1e-12 * np.abs(f[v]).sum()
+
+
+def test_restriction_and_injection():
+    u = np.random.default_rng(0).standard_normal((4, 6, 9))
+    for fac in (3,):
+        r = restrict(u, fac)
+        assert np.allclose(r.sum(axis=(1, 2)) * fac * fac, u.sum(axis=(1, 2)), rtol=1e-14)
+        v = np.random.default_rng(1).standard_normal((4, 2, 3))
+        # R P = I (exact in real arithmetic; the mean of fac^2 equal values rounds)
+        np.testing.assert_allclose(restrict(prolong(v, fac), fac), v, rtol=4e-16, atol=0)
+    assert np.allclose(restrict(u[:, :4, :8], 2)[0, 0, 0], u[0, :2, :2].mean())
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_transfer_mass_conservative_and_invertible(k):
+    dg = DG(3, 2, 0, 3000, 0, 2000, k, ROBERT)
+    T = Transfer(dg)
+    u = synth.random_perturbation(dg.shape[1:], 9)
+    v = T.to_fv(u)
+    cell = dg.hx * dg.hz / (k + 1) ** 2
+    for var in range(4):
+        m_dg = np.sum(dg.mass_weights() * u[var])
+        m_fv = cell * v[var].sum()
+        assert abs(m_fv - m_dg) <= 1e-14 * np.sum(np.abs(dg.mass_weights() * u[var]))
+    np.testing.assert_allclose(T.to_dg(v), u, atol=1e-12 * np.abs(u).max())
+    # without the mass fix T interpolates: a Q_k polynomial is sampled at the centres
+    p = lambda x, z: 1 + x / 3000 + (z / 2000) ** k
+    up = np.stack([p(dg.X, dg.Z)] * 4)
+    vp = T.to_fv(up, massfix=False)
+    n1 = k + 1
+    cx = (np.arange(3 * n1) + 0.5) * dg.hx / n1
+    cz = (np.arange(2 * n1) + 0.5) * dg.hz / n1
+    np.testing.assert_allclose(vp[0], p(cx[None, :], cz[:, None]), rtol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_midpoint_mass_equals_polynomial_mass(k):
+    # Sec. 3.3: the element mass from the FV-centre values with the modified
+    # Newton-Cotes weights equals the GL mass of the DG polynomial
+    dg = DG(2, 2, 0, 2000, 0, 2000, k, ROBERT)
+    u = synth.random_perturbation(dg.shape[1:], 2)
+    Tu = Transfer(dg).to_fv(u, massfix=False)
+    _, om = midpoint_weights(k)
+    n1 = k + 1
+    blk = Tu.reshape(4, 2, n1, 2, n1).transpose(0, 1, 3, 2, 4)
+    m_nc = dg.hx * dg.hz * np.einsum('j,i,vzxji->vzx', om, om, blk)
+    m_gl = np.einsum('ba,vzxba->vzx', dg.mass_weights(), u)
+    np.testing.assert_allclose(m_nc, m_gl, rtol=1e-12, atol=1e-12 * np.abs(m_gl).max())
+
+
+def _mg_case():
+    w = synth.BUBBLE_Q2_20x10
+    dg = DG(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, w.k, ROBERT)
+    Up = dg.init_state(w.theta_pert(dg.X, dg.Z))
+    return w, dg, Up
+
+
+def test_multigrid_converges_as_a_solver_on_the_finest_fv_level():
+    w, dg, Up = _mg_case()
+    # moderate pseudo-CFL: alpha dt = dt/10 (at the workload's alpha dt the explicit
+    # Euler smoother is not a convergent stand-alone iteration; it is used only
+    # inside GMRES there, see test_preconditioner_cuts_gmres_iterations)
+    mg = Multigrid(dg, w.fv_levels, "mg001111V")
+    mg.linearize(Up, 0.1 * w.dt)
+    b = np.random.default_rng(0).standard_normal(mg.levels[0].shape)
+    x = np.zeros_like(b)
+    res = [norm(b)]
+    for _ in range(6):
+        x = x + mg.mg(0, np.zeros_like(b), b - mg.gprime(0, x), True)
+        res.append(norm(b - mg.gprime(0, x)))
+    assert all(r1 < r0 for r0, r1 in zip(res, res[1:]))
+    assert res[-1] < 1e-2 * res[0]
+
+
+def test_preconditioner_cuts_gmres_iterations():
+    # the paper's qualitative claim (Sec. 4.1, 4.2): MG preconditioning strongly
+    # reduces the GMRES iteration count versus no preconditioner
+    w, dg, Up = _mg_case()
+    adt = w.dt
+    fU = dg.rhs(Up)
+    G, _ = dg.G(Up, adt, Up - 0.01 * fU, fU)
+    A = lambda y: dg.jv(Up, fU, y, adt)
+    _, its_none, _ = fgmres(A, -G, None, tol_abs=1e-6 * norm(G), m=30, maxit=600)
+    mg = Multigrid(dg, w.fv_levels, "mg111111V")
+    mg.linearize(Up, adt, fU)
+    _, its_mg, _ = fgmres(A, -G, mg.apply, tol_abs=1e-6 * norm(G), m=30, maxit=600)
+    assert its_mg * 3 <= its_none
+
+
+def test_fv_other_hydrostatic_state_converges_to_balance():
+    # u' = ubar(theta0=305) - ubar(theta0=300) at the cell centres: hydrostatic, so
+    # f_low -> 0 at first order; a wrong gravity sign leaves an O(1) residual
+    from oracle.physics import background
+    hot = Physics(cp=1005.0, cv=717.95, g=9.80665, p0=1e5, theta0=305.0)
+    res = []
+    for n in (8, 16, 32):
+        lev = FVLevel(2, n, 0, 1000, 0, 4000, ROBERT)
+        uh, _ = background(lev.zc, hot)
+        f = lev.rhs(np.broadcast_to(uh[:, :, None], lev.shape) - np.broadcast_to(lev.ub, lev.shape))
+        res.append(np.abs(f[2]).max())
+    assert res[0] < 0.05 * ROBERT.g * 0.017
+    assert np.log2(res[1] / res[2]) > 0.9
