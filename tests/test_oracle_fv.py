@@ -146,7 +146,10 @@ def test_preconditioner_cuts_gmres_iterations():
 
 def test_fv_other_hydrostatic_state_converges_to_balance():
     # u' = ubar(theta0=305) - ubar(theta0=300) at the cell centres: hydrostatic, so
-    # f_low -> 0 at first order; a wrong gravity sign leaves an O(1) residual
+    # f_low -> 0 in the interior (second order in the momentum); a wrong gravity
+    # sign leaves an O(1) residual.  The rows next to the slip walls keep an O(1)
+    # residual rho' g / 2: a k = 0 cell with a mirrored ghost sees its centre
+    # pressure at the wall, so they are excluded.
     from oracle.physics import background
     hot = Physics(cp=1005.0, cv=717.95, g=9.80665, p0=1e5, theta0=305.0)
     res = []
@@ -154,6 +157,6 @@ def test_fv_other_hydrostatic_state_converges_to_balance():
         lev = FVLevel(2, n, 0, 1000, 0, 4000, ROBERT)
         uh, _ = background(lev.zc, hot)
         f = lev.rhs(np.broadcast_to(uh[:, :, None], lev.shape) - np.broadcast_to(lev.ub, lev.shape))
-        res.append(np.abs(f[2]).max())
-    assert res[0] < 0.05 * ROBERT.g * 0.017
-    assert np.log2(res[1] / res[2]) > 0.9
+        res.append(np.abs(f[2, 1:-1]).max())
+    assert res[0] < 0.01 * ROBERT.g * 0.017
+    assert np.log2(res[1] / res[2]) > 1.8
