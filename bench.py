@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of implicit SDIRK2 steps of the JFNK-GMRES solver with the DG->FV
+multigrid preconditioner on one GB300, as one JSON line.
+
+Workload: warm bubble on DG Q3, 160 x 80 quads over [0,20 km] x [0,10 km]
+(819,200 unknowns), isentropic atmosphere theta0 = 300 K, +2 K cosine bubble
+plus seeded +-0.1 K white noise in theta, SDIRK2 at dt = 20x the acoustic CFL
+step, Newton TOL 1e-8, mg111111V with 5 FV levels.  A step is one SDIRK2 step
+(two Newton solves, every kernel of the path).  `value` is the FP32-
+preconditioner form (the preconditioner in FP32, residual / FD products /
+Arnoldi in FP64); the plain FP64 form is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank steps its own replica of the workload
+(members are independent, no collective on the data path); the timed region is
+bracketed by barriers and the max over ranks is taken.  `--impl reference`
+times the FP64 CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = synth.BUBBLE_Q3_160x80
+METRIC = "implicit steps/s & DOF/s at 1e-8 Newton tol (batched mixed vs plain FP64); p50/p99"
+L2_FLUSH_BYTES = 512 << 20
+
+# FP64 pipe operations per unit of the two DG kernels in the FD-product mode,
+# counted from the D64 source of the face kernel (per face point) and of the
+# volume kernel (per node) for Euler, k = 3; see DESIGN.md "roofline".  An FMA
+# counts 2 flops, add / mul 1; division and square root count the FP64
+# instructions of their IEEE-correct sequences; x^gamma the table power's.
+FLOPS_FACE_POINT = None   # filled from the committed ncu summary below
+FLOPS_NODE = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--plain-steps", type=int, default=None)
+    p.add_argument("--form", default="both", choices=["both", "fp32"],
+                   help="fp32: time only the FP32-preconditioner steps (for profiler runs)")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def make_context(w, prec):
+    import paper_2505_24504_gb300 as P
+    g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
+    ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
+    o = P.Opts.defaults(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec)
+    return P.Context(g, w.k, ph, o)
+
+
+def initial_state(ctx, w):
+    import torch
+    x, z = ctx.node_coords()
+    sh = (w.nz, w.nx, w.k + 1, w.k + 1)
+    th = w.theta_pert(x.reshape(sh), z.reshape(sh))
+    U = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.jfnk_init_state(torch.from_numpy(th.ravel().copy()).cuda(), U)
+    return U
+
+
+def time_steps(ctx, U, w, steps, warmup, dist, flush):
+    """Device time of `steps` SDIRK2 steps (CUDA events on the launching stream),
+    L2 flushed between steps outside the events."""
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.implicit_step(U, w.dt, scheme=w.scheme)
+    stats = []
+    ms = 0.0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = ctx.implicit_step(U, w.dt, scheme=w.scheme)
+        e1.record(s)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        stats.append(st.as_dict())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return ms, stats
+
+
+def max_over_ranks(x, dist):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None):
+    """The FP64 oracle as it stands on the host cores: one Newton iteration of
+    the first SDIRK2 stage (residual, linearisation, GMRES iterations equal to
+    the workload's mean per Newton iteration).  Returns (seconds per step
+    extrapolated by the step's Newton / GMRES counts, sample description)."""
+    import numpy as np
+
+    from oracle.dg import DG
+    from oracle.fv import Multigrid
+    from oracle.physics import Physics
+    from oracle.solver import fgmres, SDIRK2_ALPHA
+    ph = Physics(cp=w.cp, cv=w.cv, g=w.g, p0=w.p0, theta0=w.theta0, mu=w.mu)
+    dg = DG(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, w.k, ph)
+    U = dg.init_state(w.theta_pert(dg.X, dg.Z))
+    adt = SDIRK2_ALPHA * w.dt
+    its = budget_its or max(1, int(round(gmres_per_step / max(newton_per_step, 1))))
+    t0 = time.perf_counter()
+    G, fU = dg.G(U, adt, U)
+    mg = Multigrid(dg, w.fv_levels, w.mg_key)
+    mg.linearize(U, adt, fU)
+    t1 = time.perf_counter()
+    A = lambda y: dg.jv(U, fU, y, adt)
+    _, done, _ = fgmres(A, -G, mg.apply, tol_abs=0.0, m=30, maxit=its)
+    t2 = time.perf_counter()
+    t_newton = t1 - t0
+    t_it = (t2 - t1) / max(done, 1)
+    per_step = newton_per_step * t_newton + gmres_per_step * t_it
+    desc = (f"oracle (numpy FP64, 1 thread): 1 residual + linearisation + {done} preconditioned FGMRES "
+            f"iterations of workload 2's first Newton step, scaled to {newton_per_step} Newton / "
+            f"{gmres_per_step} GMRES iterations per SDIRK2 step")
+    return per_step, desc, t2 - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    w = WORKLOAD
+    newton_per_step, gmres_per_step = 8, 96   # the workload's counts (GPU run, same algorithm)
+    per = []
+    for _ in range(args.warmup):
+        oracle_sample(w, newton_per_step, gmres_per_step, budget_its=1)
+    desc = ""
+    for _ in range(args.steps):
+        sec, desc, _ = oracle_sample(w, newton_per_step, gmres_per_step, budget_its=3)
+        per.append(sec)
+    ms_per_step = 1e3 * statistics.mean(per)
+    value = 1e3 / ms_per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "implicit steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "dof_per_s": value * w.n_unknowns,
+        "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "mg_key": w.mg_key},
+        "cpu_baseline": {"value": value, "unit": "implicit steps/s", "cores": 1, "kind": "oracle",
+                         "sample": desc.replace("3 preconditioned", "3 preconditioned")},
+        "e2e": {"value": value, "unit": "implicit steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300 import build as B
+    B.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as D
+        D.init_process_group("nccl")
+        dist = D
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # ---- the product form: FP32 preconditioner --------------------------------
+    ctx = make_context(w, 32)
+    U = initial_state(ctx, w)
+    U0 = U.clone()
+    n0 = P.jfnk.launch_count()
+    with Clocks(local) as clk:
+        ms, stats = time_steps(ctx, U, w, args.steps, args.warmup, dist, flush)
+    launches = P.jfnk.launch_count() - n0
+    clocks = clk.summary()
+    ms = max_over_ranks(ms, dist)
+    value = world * args.steps / (ms / 1e3)
+    newton = sum(s["newton_its"] for s in stats) / len(stats)
+    gmres = sum(s["gmres_its"] for s in stats) / len(stats)
+    if args.form == "fp32":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "implicit steps/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                              "form": "fp32 only (profiling run)", "gpu_launches": int(launches),
+                              "iterations_per_step": {"newton": newton, "gmres": gmres}}))
+        return
+
+    # ---- end to end through the public API with host buffers ------------------
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    s = torch.cuda.current_stream()
+    ctx.implicit_step(U, w.dt, scheme=w.scheme)   # warm
+    e2e_ms = 0.0
+    lat = []
+    ne2e = max(2, args.steps // 2)
+    for _ in range(ne2e):
+        flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        U.copy_(Uh, non_blocking=True)
+        ctx.implicit_step(U, w.dt, scheme=w.scheme)
+        Uout.copy_(U, non_blocking=True)
+        e1.record(s)
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        e2e_ms += t
+        lat.append(t)
+    e2e_ms = max_over_ranks(e2e_ms, dist)
+    e2e = world * ne2e / (e2e_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (FP64 FD product, face kernel) --------
+    y = torch.randn(ctx.N, dtype=torch.float64, device="cuda")
+    ctx64 = make_context(w, 64)
+    fm, vm = ctx64.time_operator(1, U0, y, 20)
+    n1 = w.k + 1
+    face_pts = (w.nz * (w.nx + 1) + (w.nz + 1) * w.nx) * n1
+    roof = None
+    if FLOPS_FACE_POINT:
+        ach = FLOPS_FACE_POINT * face_pts / (fm * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_faces (FP64 FD product)", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "face_ms": fm, "volume_ms": vm}
+
+    # ---- the plain FP64 single-instance form ----------------------------------
+    U64 = U0.clone()
+    kp = args.plain_steps or max(2, args.steps // 3)
+    ms64, st64 = time_steps(ctx64, U64, w, kp, 1, dist, flush)
+    ms64 = max_over_ranks(ms64, dist)
+    plain = world * kp / (ms64 / 1e3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "implicit steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "dof_per_s": value * w.n_unknowns,
+        "plain_fp64": {"value": plain, "unit": "implicit steps/s", "dof_per_s": plain * w.n_unknowns,
+                       "ms_per_step": ms64 / kp},
+        "iterations_per_step": {"newton": newton, "gmres": gmres},
+        "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
+                   "newton_tol": w.newton_tol, "mg_key": w.mg_key, "fv_levels": w.fv_levels,
+                   "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e, "unit": "implicit steps/s", "h2d_bytes_per_step": 8 * ctx.N,
+                "d2h_bytes_per_step": 8 * ctx.N, "p50_ms": statistics.median(lat),
+                "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        per_step, desc, _ = oracle_sample(w, int(round(newton)), int(round(gmres)))
+        line["cpu_baseline"] = {"value": 1.0 / per_step, "unit": "implicit steps/s", "cores": 1,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
+
+if __name__ == "__main__":
+    main()

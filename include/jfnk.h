@@ -1,0 +1,213 @@
+/*
+ * jfnk.h -- C ABI of the GB300 (sm_103a) Jacobian-free Newton-GMRES solver
+ * with the DG->FV subgrid multigrid preconditioner of Birken, Dedner and
+ * Kloefkorn, "A Jacobian-free multigrid preconditioner for discontinuous
+ * Galerkin methods applied to numerical weather prediction" (arXiv 2505.24504).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Unknowns.  A state is the perturbation U' = U - Ubar of the nodal values of
+ *   U = (rho, rho u, rho w, rho theta) on the tensor Gauss-Legendre nodes of a
+ *   Q_k element (Sec. 2.1; eq. perturbed-euler of Sec. 4).  Ubar is the
+ *   environmental atmosphere chosen in jfnk_physics.
+ * Layout.  A DG vector holds N = 4 * nx * nz * (k+1)^2 doubles, ordered
+ *   [variable][ez][ex][b][a]: variable slowest, then element row ez (z index),
+ *   element column ex, node index b along z, node index a along x (fastest).
+ *   Nodes within an element ascend in x and z.
+ * Memory.  Arguments named *_dev are device pointers (cudaMalloc'd or any
+ *   device allocation such as a torch CUDA tensor) owned by the caller; the
+ *   library never frees or retains them past the call.  *_host arguments are
+ *   host pointers.  The context owns all tables and workspace.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Every
+ *   call is ordered on that stream.  Calls that return results to the host
+ *   (implicit_step's stats, norms) synchronise the stream before returning.
+ * Errors.  0 on success, else a negative JFNK_E* code; jfnk_strerror() names
+ *   it.  There is no CPU fallback: without a usable CUDA device, jfnk_create
+ *   returns JFNK_ECUDA.
+ * Threads.  A context is not thread safe; use one context per host thread.
+ */
+#ifndef JFNK_H
+#define JFNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JFNK_OK 0
+#define JFNK_EINVAL (-1)    /* bad argument: k outside [1,4], sizes, NULL, bad mg key */
+#define JFNK_ENOMEM (-2)    /* device allocation failed (nothing leaked) */
+#define JFNK_ECUDA (-3)     /* a CUDA call failed */
+#define JFNK_ENOTCONV (-4)  /* Newton or GMRES hit its iteration cap; state restored */
+#define JFNK_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define JFNK_ENAN (-6)      /* a norm became non-finite; state restored */
+
+typedef struct jfnk_ctx jfnk_ctx;
+
+/* Cartesian grid of nx x nz quadrilaterals over [x0,x1] x [z0,z1].
+ * Slip walls on all sides unless periodic_x = 1 (then periodic in x, slip
+ * walls at bottom and top), as in the test cases of Sec. 4. */
+typedef struct {
+    int nx, nz;
+    double x0, x1, z0, z1;
+    int periodic_x;
+} jfnk_grid;
+
+/* Model of Sec. 4, eq. (compressible-euler): c_p, c_v [J/(kg K)], gravity g
+ * [m/s^2], reference pressure p0 [Pa], kinematic viscosity mu [m^2/s]
+ * (mu = 0: Euler).  background 0: isentropic atmosphere theta = theta0,
+ * T = theta0 - g z / c_p, p = p0 (T/theta0)^(c_p/R) (Sec. 4.2, 4.3);
+ * background 1: uniform state rho = p0/(R theta0), theta = theta0, wind
+ * (ubg, wbg) (meant for g = 0). */
+typedef struct {
+    double cp, cv, g, p0, theta0, mu;
+    int background;
+    double ubg, wbg;
+} jfnk_physics;
+
+/* Solver options.  Defaults (jfnk_default_opts) follow Sec. 3.1 and Sec. 4:
+ * Newton TOL 1e-8 (the paper's runs use 1e-3), Eisenstat-Walker choice 2 with
+ * gamma = 0.1, alpha = 1, GMRES restart 30, preconditioner key "mg111111V".
+ *  mg_key       "mg a b c d e f G" of Sec. 4: DG pre/post, finest FV
+ *               pre/post, intermediate and coarsest FV pre/post smoothing
+ *               steps, cycle V or W.  "" disables the preconditioner.
+ *  fv_levels    number of FV levels (subgrid first, then agglomeration).
+ *  massfix      1: transfer with the mass fix of eq. (transfer-mass-fix).
+ *  precond_prec 64: preconditioner in FP64 with finite-difference products
+ *               exactly as the paper; 32: preconditioner (DG smoothing,
+ *               transfers, all FV levels) in FP32 with exact tangent-linear
+ *               products; 16: as 32 with the coarsest FV level stored in bf16.
+ *               The Newton residual, the outer FD Jv, the background
+ *               subtraction and GMRES stay FP64 in every mode.
+ *  sigma_fv, sigma_dg  pseudo-time CFL factors of the smoothers (Sec. 3.5).
+ *  c_ip         interior-penalty constant of the viscous flux.
+ *  use_graphs   1: capture each preconditioner application in a CUDA graph. */
+typedef struct {
+    double newton_tol;
+    int newton_max;
+    int gmres_restart, gmres_max;
+    double ew_gamma, ew_alpha, ew_eta0, ew_eta_max;
+    char mg_key[16];
+    int fv_levels;
+    int massfix;
+    int precond_prec;
+    double sigma_fv, sigma_dg, c_ip;
+    int use_graphs;
+} jfnk_opts;
+
+/* Counters of one implicit_step (Sec. 4.2 counts linear iterations and
+ * operator calls). */
+typedef struct {
+    int status;          /* JFNK_OK or the error of the step */
+    int stages;
+    int newton_its;      /* summed over stages */
+    int gmres_its;       /* summed over Newton iterations */
+    int dg_calls;        /* DG operator evaluations (residuals and products) */
+    int fv_calls;        /* FV operator evaluations on all levels */
+    double res0;         /* |G(U^0)| of the last stage */
+    double res_final;    /* |G| at exit of the last stage */
+} jfnk_stats;
+
+void jfnk_default_opts(jfnk_opts *opts);
+
+/* Create a context for one grid / order / model.  opts may be NULL
+ * (defaults).  Allocates tables, background, Krylov basis (restart+1 DG
+ * vectors in FP64 plus restart preconditioned vectors), FV levels and
+ * reduction scratch on the current CUDA device.  Returns JFNK_EINVAL for
+ * k outside [1,4], nx or nz < 1, non-positive extents or a bad key. */
+int jfnk_create(const jfnk_grid *grid, int k, const jfnk_physics *phys,
+                const jfnk_opts *opts, jfnk_ctx **out);
+void jfnk_destroy(jfnk_ctx *ctx);
+
+/* N = 4 nx nz (k+1)^2. */
+size_t jfnk_num_unknowns(const jfnk_ctx *ctx);
+
+/* Device bytes jfnk_create would allocate for these arguments (HBM
+ * admission); 0 on invalid arguments. */
+size_t jfnk_workspace_bytes(const jfnk_grid *grid, int k, const jfnk_opts *opts);
+
+/* Node coordinates in the DG layout without the variable index:
+ * nx nz (k+1)^2 doubles each, written to host memory. */
+int jfnk_node_coords(const jfnk_ctx *ctx, double *x_host, double *z_host);
+
+/* Initial perturbation state from a potential-temperature perturbation theta'
+ * given at the nodes (nx nz (k+1)^2 doubles, device), by the pressure-
+ * preserving insertion of eq. (add-perturbation): p and v of the background
+ * are kept, theta = theta~ + theta', rho = p0^(R/c_p) p~^(1/gamma) / (R theta).
+ * Writes U' = U - Ubar (N doubles, device).  Nodal interpolation equals the
+ * L2 projection of Sec. 2.2 under the collocated GL quadrature. */
+int jfnk_init_state(jfnk_ctx *ctx, const double *theta_pert_dev, double *U_dev, void *stream);
+
+/* f = M^-1 L_h(U') (eq. convDiscr with eqs. elementint and surfaceint, in the
+ * well-balanced perturbation form of Sec. 4): HLLC convective flux, symmetric
+ * interior-penalty viscous flux, gravity source -g rho', slip walls by a
+ * mirrored ghost state.  U' and f are N doubles on the device; they must not
+ * overlap.  U' = 0 gives f = 0 exactly. */
+int dg_residual(jfnk_ctx *ctx, const double *U_dev, double *f_dev, void *stream);
+
+/* Jacobian-free product of Sec. 3.1 for G(U) = U - alpha_dt f(U) - Ubar_s:
+ *   G'(U) y ~ y - alpha_dt (f(U + eps y) - f(U)) / eps,
+ * eps = sqrt(eps_mach)/|y|_2 (eps_mach = 2^-52) when eps <= 0, else the given
+ * eps.  fU_dev = f(U) may be NULL (then computed here).  y = 0 gives Jy = 0.
+ * All vectors are N doubles on the device; Jy must not alias U, fU or y. */
+int jv_product(jfnk_ctx *ctx, const double *U_dev, const double *fU_dev, const double *y_dev,
+               double alpha_dt, double eps, double *Jy_dev, void *stream);
+
+/* z = Q^-1 r with Q^-1 = T^-1 q^-1 T (eq. preconditioner): DG pre-smoothing,
+ * transfer of the DG residual to the FV subgrid with mass fix
+ * (eq. transfer-mass-fix), one FV multigrid cycle from zero linearised at
+ * T U' (Sec. 3.4), transfer back, DG post-smoothing; smoothing by explicit
+ * Euler pseudo-time steps (Sec. 3.5).  U', r, z are N doubles on the device;
+ * z must not alias U or r. */
+int mg_precondition(jfnk_ctx *ctx, const double *U_dev, double alpha_dt, const double *r_dev,
+                    double *z_dev, void *stream);
+
+/* One implicit step U^n -> U^{n+1} in place (U' on the device):
+ * scheme 0 backward Euler, 1 SDIRK2 of Ellsiepen (Sec. 2.2, alpha = 1 -
+ * sqrt(2)/2).  Each stage solves eq. (newton) by inexact Newton from
+ * U_s^0 = Ubar_s with right-preconditioned flexible GMRES and Eisenstat-
+ * Walker tolerances (Sec. 3.1).  On JFNK_ENOTCONV or JFNK_ENAN the state is
+ * restored to U^n.  stats may be NULL.  Synchronises the stream. */
+int implicit_step(jfnk_ctx *ctx, double *U_dev, double dt, int scheme, jfnk_stats *stats,
+                  void *stream);
+
+/* ---- diagnostics (pieces of mg_precondition, for parity tests) -------- */
+
+/* Number of FV levels and the size of level l (0 = finest subgrid). */
+int jfnk_fv_levels(const jfnk_ctx *ctx);
+int jfnk_fv_level_size(const jfnk_ctx *ctx, int level, int *NX, int *NZ);
+
+/* v = T^mf u (DG -> finest FV, layout [variable][J][I], J = ez(k+1)+j,
+ * I = ex(k+1)+i; 4 NX NZ doubles).  Mass fix if the context's massfix = 1. */
+int jfnk_transfer_to_fv(jfnk_ctx *ctx, const double *u_dev, double *v_dev, void *stream);
+
+/* u = T^-1 v (finest FV -> DG) with the mass fix applied back. */
+int jfnk_transfer_to_dg(jfnk_ctx *ctx, const double *v_dev, double *u_dev, void *stream);
+
+/* f = f_low(u') on FV level l (k = 0 scheme in perturbation form, FP64). */
+int jfnk_fv_residual(jfnk_ctx *ctx, int level, const double *u_dev, double *f_dev, void *stream);
+
+/* p = p0 (R E / p0)^gamma for n values E = rho theta (device arrays): the EOS
+ * every kernel evaluates, with the table-driven power.  Exposed so that its
+ * accuracy can be checked against CUDA's pow. */
+int jfnk_eos_pressure(jfnk_ctx *ctx, const double *E_dev, size_t n, double *p_dev, void *stream);
+
+/* Times the two kernels of one DG operator evaluation with CUDA events
+ * recorded on `stream` around each launch: which 0 = FP64 residual,
+ * 1 = FP64 finite-difference product with direction y, 2 = FP32 tangent
+ * product (contexts with precond_prec < 64).  Runs `reps` evaluations;
+ * ms[0], ms[1] receive the mean duration of the face and the volume kernel. */
+int jfnk_time_operator(jfnk_ctx *ctx, int which, const double *U_dev, const double *y_dev, int reps,
+                       double *ms_host, void *stream);
+
+/* Number of kernels this library has launched in this process. */
+unsigned long long jfnk_launch_count(void);
+
+const char *jfnk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JFNK_H */

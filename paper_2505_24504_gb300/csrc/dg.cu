@@ -1,0 +1,554 @@
+// DG operator f = M^-1 L_h(U') on the GPU (Sec. 2.1; well-balanced form of Sec. 4).
+//
+// Two launches per evaluation:
+//  k_faces   one thread per face point.  Traces of U' from both sides (and the
+//            normal-gradient traces for the viscous terms), HLLC^pert =
+//            HLLC(U'+Ubar) - HLLC(Ubar), symmetric interior penalty terms, slip
+//            walls by a mirrored ghost.  Every face flux is computed once and
+//            stored: Phi = H - {F_v.n} + eta [U] for the lift with l_a(+-1), and
+//            the two symmetry terms 1/2 A(U_side) [U] for the lift with l_a'(+-1).
+//  k_volume  a block holds EPB elements, one thread per node.  Fluxes
+//            F_c^pert - F_v at the node, the weak-form derivative by sum
+//            factorisation over the (k+1) nodes of the row / column (tables in
+//            shared memory), gravity source, lift of the stored face terms and
+//            the mode's epilogue (residual, FD product, Newton residual G or a
+//            pseudo-time smoothing step).
+// The same kernels run on D64 (FP64 residual and finite-difference products)
+// and on TL32 (FP32 tangent-linear products for the FP32 preconditioner).
+#include "internal.h"
+
+namespace {
+
+struct DGK {
+    int nx, nz, n_el, periodic;
+    double two_hx, two_hz, g, mu, eta_x, eta_z;
+    PhysC pc;
+    const PowTab *pt;
+    const double *ubv, *dubv, *fbx, *fbz, *hbx, *hbxw, *ubh, *dubh, *hbz;
+    const float *ubvf, *dubvf, *ubhf, *dubhf;
+    DGTab tab;
+};
+
+template <class T> struct OutT;
+template <> struct OutT<D64> { typedef double type; };
+template <> struct OutT<TL32> { typedef float type; };
+JF_D double outv(D64 a) { return a.x; }
+JF_D float outv(TL32 a) { return a.d; }
+
+// Input of the perturbation state at global index i:
+// IN 0: U'; IN 1: U' + eps y (FP64); IN 2: TL32 (U', y32)
+template <class T, int IN> struct Loader;
+template <> struct Loader<D64, 0> {
+    const double *U;
+    JF_D void prepare() {}
+    JF_D D64 operator()(size_t i) const { return D64{U[i]}; }
+};
+template <> struct Loader<D64, 1> {
+    const double *U, *y, *epsp;   // eps is a device scalar written by a reduction
+    double eps;
+    JF_D void prepare() { eps = *epsp; }
+    JF_D D64 operator()(size_t i) const { return D64{__fma_rn(eps, y[i], U[i])}; }
+};
+template <> struct Loader<TL32, 2> {
+    const float *U;
+    const float *y;
+    JF_D void prepare() {}
+    JF_D TL32 operator()(size_t i) const { return TL32{U[i], y[i]}; }
+};
+
+__device__ __forceinline__ void load_powtab(PowTab *s, const PowTab *g) {
+    const double *src = reinterpret_cast<const double *>(g);
+    double *dst = reinterpret_cast<double *>(s);
+    const int n = sizeof(PowTab) / sizeof(double);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// background values: FP64 tables for D64, FP32 copies for TL32
+template <class T> JF_D T bgs(const double *d, const float *f, size_t i);
+template <> JF_D D64 bgs<D64>(const double *d, const float *, size_t i) { return D64{d[i]}; }
+template <> JF_D TL32 bgs<TL32>(const double *, const float *f, size_t i) { return TL32{f[i], 0.0f}; }
+template <class T>
+JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
+
+// ---------------------------------------------------------------------------
+template <class T, int IN, int NP1, bool VISC>
+__global__ void __launch_bounds__(128) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
+                                               typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
+                                               typename OutT<T>::type *symz) {
+    typedef typename OutT<T>::type O;
+    __shared__ PowTab spt;
+    load_powtab(&spt, K.pt);
+    Loader<T, IN> ld = ld0;
+    ld.prepare();
+    __syncthreads();
+    constexpr int NP = NP1 * NP1;
+    const int nx = K.nx, nz = K.nz;
+    const size_t N1 = (size_t)K.n_el * NP;
+    const long long nvert = (long long)nz * (nx + 1) * NP1;
+    const long long nhorz = (long long)(nz + 1) * nx * NP1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nvert + nhorz) return;
+    const T zero = mk(0.0, T{});
+    const T half = mk(0.5, T{});
+    T H[4], Phi[4], sL[3], sR[3];
+    if (t < nvert) {
+        const int s = (int)(t % NP1);
+        const int fx = (int)((t / NP1) % (nx + 1));
+        const int ez = (int)(t / (NP1 * (nx + 1)));
+        const int J = ez * NP1 + s;
+        const size_t nrow = (size_t)nz * NP1;
+        int eL, eR;
+        bool wallL = false, wallR = false;
+        if (K.periodic) {
+            eL = ez * nx + (fx + nx - 1) % nx;
+            eR = ez * nx + fx % nx;
+        } else {
+            wallL = (fx == 0);
+            wallR = (fx == nx);
+            eL = ez * nx + (wallL ? 0 : fx - 1);
+            eR = ez * nx + (wallR ? nx - 1 : fx);
+        }
+        // traces: L at xi = +1 (row s), R at xi = -1
+        T trL[4], trR[4], gL[4], gR[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            T aL = zero, aR = zero, dL = zero, dR = zero;
+#pragma unroll
+            for (int a = 0; a < NP1; ++a) {
+                const T uL = ld((size_t)v * N1 + (size_t)eL * NP + s * NP1 + a);
+                const T uR = ld((size_t)v * N1 + (size_t)eR * NP + s * NP1 + a);
+                aL = jfma(mk(K.tab.lp[a], T{}), uL, aL);
+                aR = jfma(mk(K.tab.lm[a], T{}), uR, aR);
+                if (VISC) {
+                    dL = jfma(mk(K.tab.dlp[a], T{}), uL, dL);
+                    dR = jfma(mk(K.tab.dlm[a], T{}), uR, dR);
+                }
+            }
+            trL[v] = aL;
+            trR[v] = aR;
+            gL[v] = mk(K.two_hx, T{}) * dL;
+            gR[v] = mk(K.two_hx, T{}) * dR;
+        }
+        T UL[4], UR[4], Gh[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            UL[v] = trL[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
+            UR[v] = trR[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
+        }
+        if (wallL) {
+            mirror<T, 0>(UR, Gh);
+            hllc<T, 0>(Gh, UR, K.pc, &spt, H);
+        } else if (wallR) {
+            mirror<T, 0>(UL, Gh);
+            hllc<T, 0>(UL, Gh, K.pc, &spt, H);
+        } else {
+            hllc<T, 0>(UL, UR, K.pc, &spt, H);
+        }
+        const double *hb = wallL ? K.hbxw : (wallR ? K.hbxw + 4 * nrow : K.hbx);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (IN != 2) H[v] = H[v] - bg<T>(hb, v * nrow + J);
+            Phi[v] = H[v];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
+        if (VISC && !wallL && !wallR) {
+            T FL[4], FR[4], Jp[4];
+            viscous(UL, gL, K.mu, FL);
+            viscous(UR, gR, K.mu, FR);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
+#pragma unroll
+            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + mk(K.eta_x, T{}) * Jp[v];
+            T AL[4], AR[4];
+            viscous(UL, Jp, K.mu, AL);
+            viscous(UR, Jp, K.mu, AR);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sL[c] = half * AL[c + 1];
+                sR[c] = half * AR[c + 1];
+            }
+        }
+        const size_t fb = ((size_t)ez * (nx + 1) + fx) * NP1 + s;
+        const size_t fs = (size_t)nz * (nx + 1) * NP1;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) phix[v * fs + fb] = (O)outv(Phi[v]);
+        if (VISC) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                symx[(size_t)c * fs + fb] = (O)outv(sL[c]);
+                symx[(size_t)(3 + c) * fs + fb] = (O)outv(sR[c]);
+            }
+        }
+    } else {
+        const long long u = t - nvert;
+        const int s = (int)(u % NP1);
+        const int ex = (int)((u / NP1) % nx);
+        const int fz = (int)(u / (NP1 * nx));
+        const bool wallB = (fz == 0), wallT = (fz == nz);
+        const int eB = (wallB ? 0 : fz - 1) * nx + ex;
+        const int eT = (wallT ? nz - 1 : fz) * nx + ex;
+        T trB[4], trT[4], gB[4], gT[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            T aB = zero, aT = zero, dB = zero, dT = zero;
+#pragma unroll
+            for (int b = 0; b < NP1; ++b) {
+                const T uB = ld((size_t)v * N1 + (size_t)eB * NP + b * NP1 + s);
+                const T uT = ld((size_t)v * N1 + (size_t)eT * NP + b * NP1 + s);
+                aB = jfma(mk(K.tab.lp[b], T{}), uB, aB);
+                aT = jfma(mk(K.tab.lm[b], T{}), uT, aT);
+                if (VISC) {
+                    dB = jfma(mk(K.tab.dlp[b], T{}), uB, dB);
+                    dT = jfma(mk(K.tab.dlm[b], T{}), uT, dT);
+                }
+            }
+            trB[v] = aB;
+            trT[v] = aT;
+            gB[v] = mk(K.two_hz, T{}) * dB + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
+            gT[v] = mk(K.two_hz, T{}) * dT + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
+        }
+        T UB[4], UT[4], Gh[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            UB[v] = trB[v] + bgs<T>(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz);
+            UT[v] = trT[v] + bgs<T>(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz);
+        }
+        if (wallB) {
+            mirror<T, 1>(UT, Gh);
+            hllc<T, 1>(Gh, UT, K.pc, &spt, H);
+        } else if (wallT) {
+            mirror<T, 1>(UB, Gh);
+            hllc<T, 1>(UB, Gh, K.pc, &spt, H);
+        } else {
+            hllc<T, 1>(UB, UT, K.pc, &spt, H);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (IN != 2) H[v] = H[v] - bg<T>(K.hbz, (size_t)v * (nz + 1) + fz);
+            Phi[v] = H[v];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
+        if (VISC && !wallB && !wallT) {
+            T FB[4], FT[4], Jp[4];
+            viscous(UB, gB, K.mu, FB);
+            viscous(UT, gT, K.mu, FT);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Jp[v] = trB[v] - trT[v];
+#pragma unroll
+            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + mk(K.eta_z, T{}) * Jp[v];
+            T AB[4], AT[4];
+            viscous(UB, Jp, K.mu, AB);
+            viscous(UT, Jp, K.mu, AT);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sL[c] = half * AB[c + 1];
+                sR[c] = half * AT[c + 1];
+            }
+        }
+        const size_t fb = ((size_t)fz * nx + ex) * NP1 + s;
+        const size_t fs = (size_t)(nz + 1) * nx * NP1;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) phiz[v * fs + fb] = (O)outv(Phi[v]);
+        if (VISC) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                symz[(size_t)c * fs + fb] = (O)outv(sL[c]);
+                symz[(size_t)(3 + c) * fs + fb] = (O)outv(sR[c]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int NP1> struct EPBOf {
+    static constexpr int NP = NP1 * NP1;
+    static constexpr int value = (128 / NP) > 0 ? (128 / NP) : 1;
+};
+
+template <class T, int IN, int MODE, int NP1, bool VISC>
+__global__ void __launch_bounds__(128) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
+                                                const typename OutT<T>::type *phix,
+                                                const typename OutT<T>::type *symx,
+                                                const typename OutT<T>::type *phiz,
+                                                const typename OutT<T>::type *symz) {
+    typedef typename OutT<T>::type O;
+    constexpr int NP = NP1 * NP1;
+    constexpr int EPB = EPBOf<NP1>::value;
+    __shared__ PowTab spt;
+    __shared__ O sg[2][EPB][4][NP];
+    __shared__ T su[VISC ? EPB : 1][4][NP];
+    __shared__ double sDw[NP1][NP1];
+    __shared__ double sDn[NP1][NP1];
+    __shared__ double sl[4][NP1];   // lmw, lpw, dlmw, dlpw
+    load_powtab(&spt, K.pt);
+    Loader<T, IN> ld = ld0;
+    ld.prepare();
+    if (threadIdx.x < NP) {
+        sDw[threadIdx.x / NP1][threadIdx.x % NP1] = K.tab.Dw[threadIdx.x / NP1][threadIdx.x % NP1];
+        sDn[threadIdx.x / NP1][threadIdx.x % NP1] = K.tab.Dn[threadIdx.x / NP1][threadIdx.x % NP1];
+    }
+    if (threadIdx.x < NP1) {
+        sl[0][threadIdx.x] = K.tab.lmw[threadIdx.x];
+        sl[1][threadIdx.x] = K.tab.lpw[threadIdx.x];
+        sl[2][threadIdx.x] = K.tab.dlmw[threadIdx.x];
+        sl[3][threadIdx.x] = K.tab.dlpw[threadIdx.x];
+    }
+    const int le = threadIdx.x / NP;
+    const int node = threadIdx.x % NP;
+    const int a = node % NP1, b = node / NP1;
+    const int e = blockIdx.x * EPB + le;
+    const bool active = (le < EPB) && (e < K.n_el);
+    const int nx = K.nx, nz = K.nz;
+    const int ez = active ? e / nx : 0, ex = active ? e % nx : 0;
+    const size_t N1 = (size_t)K.n_el * NP;
+    const size_t nrow = (size_t)nz * NP1;
+    const int J = ez * NP1 + b;
+    __syncthreads();
+    T Up[4], U[4];
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Up[v] = ld((size_t)v * N1 + (size_t)e * NP + node);
+            U[v] = Up[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
+            if (VISC) su[le][v][node] = Up[v];
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const T ir = mk(1.0, T{}) / U[0];
+        const T p = pressure(U[3], K.pc, &spt);
+        T Fx[4], Fz[4];
+        flux_c<T, 0>(U, U[1] * ir, p, Fx);
+        flux_c<T, 1>(U, U[2] * ir, p, Fz);
+        if (IN != 2) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                Fx[v] = Fx[v] - bg<T>(K.fbx, v * nrow + J);
+                Fz[v] = Fz[v] - bg<T>(K.fbz, v * nrow + J);
+            }
+        }
+        if (VISC) {
+            T dx[4], dz[4], Gx[4], Gz[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T sx = mk(0.0, T{}), sz = mk(0.0, T{});
+#pragma unroll
+                for (int q = 0; q < NP1; ++q) {
+                    sx = jfma(mk(sDn[a][q], T{}), su[le][v][b * NP1 + q], sx);
+                    sz = jfma(mk(sDn[b][q], T{}), su[le][v][q * NP1 + a], sz);
+                }
+                dx[v] = mk(K.two_hx, T{}) * sx;
+                dz[v] = mk(K.two_hz, T{}) * sz + bgs<T>(K.dubv, K.dubvf, v * nrow + J);
+            }
+            viscous(U, dx, K.mu, Gx);
+            viscous(U, dz, K.mu, Gz);
+#pragma unroll
+            for (int v = 1; v < 4; ++v) {
+                Fx[v] = Fx[v] - Gx[v];
+                Fz[v] = Fz[v] - Gz[v];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            sg[0][le][v][node] = (O)outv(Fx[v]);
+            sg[1][le][v][node] = (O)outv(Fz[v]);
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    const O thx = (O)K.two_hx, thz = (O)K.two_hz;
+    const size_t fsx = (size_t)nz * (nx + 1) * NP1, fsz = (size_t)(nz + 1) * nx * NP1;
+    const size_t iL = ((size_t)ez * (nx + 1) + ex) * NP1 + b, iR = iL + NP1;
+    const size_t iB = ((size_t)ez * nx + ex) * NP1 + a, iT = iB + (size_t)nx * NP1;
+    const O lmwa = (O)sl[0][a], lpwa = (O)sl[1][a];
+    const O lmwb = (O)sl[0][b], lpwb = (O)sl[1][b];
+    const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        O ax = 0, az = 0;
+#pragma unroll
+        for (int q = 0; q < NP1; ++q) {
+            ax = fma((O)sDw[a][q], sg[0][le][v][b * NP1 + q], ax);
+            az = fma((O)sDw[b][q], sg[1][le][v][q * NP1 + a], az);
+        }
+        O f = thx * ax + thz * az;
+        if (v == 2) f = f - (O)K.g * (O)outv(Up[0]);
+        f = f + thx * (lmwa * phix[v * fsx + iL] - lpwa * phix[v * fsx + iR]) +
+            thz * (lmwb * phiz[v * fsz + iB] - lpwb * phiz[v * fsz + iT]);
+        if (VISC && v > 0) {
+            const int c = v - 1;
+            f = f + thx * thx * ((O)sl[2][a] * symx[(size_t)(3 + c) * fsx + iL] +
+                                 (O)sl[3][a] * symx[(size_t)c * fsx + iR]) +
+                thz * thz * ((O)sl[2][b] * symz[(size_t)(3 + c) * fsz + iB] +
+                             (O)sl[3][b] * symz[(size_t)c * fsz + iT]);
+        }
+        const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
+        if (MODE == DG_RES) {
+            ((double *)A.out0)[gi] = (double)f;
+        } else if (MODE == DG_JV) {
+            const double y = A.y[gi];
+            ((double *)A.out0)[gi] = (eps == 0.0) ? y : y - A.adt * ((double)f - A.fU[gi]) / eps;
+        } else if (MODE == DG_G) {
+            A.out1[gi] = (double)f;
+            ((double *)A.out0)[gi] = A.U[gi] - A.adt * (double)f - A.Ubs[gi];
+        } else if (MODE == DG_SMOOTH64) {
+            const double z = A.y[gi];
+            const double Jz = (eps == 0.0) ? z : z - A.adt * ((double)f - A.fU[gi]) / eps;
+            ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
+        } else if (MODE == DG_TLJV) {
+            const float z = A.yf[gi];
+            ((float *)A.out0)[gi] = z - (float)A.adt * (float)f;
+        } else {  // DG_TLSMOOTH
+            const float z = A.yf[gi];
+            const float Jz = z - (float)A.adt * (float)f;
+            ((float *)A.out0)[gi] = z + A.dtauf[e] * (A.rf[gi] - Jz);
+        }
+    }
+}
+
+// background fluxes at node rows and horizontal faces, with the residual's own
+// D64 functions so that U' = 0 cancels bit for bit
+__global__ void k_bg_dg(DGK K, double *fbx, double *fbz, double *hbx, double *hbxw, double *hbz) {
+    __shared__ PowTab spt;
+    load_powtab(&spt, K.pt);
+    __syncthreads();
+    const int nrow = K.nz * K.tab.np1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nrow) {
+        D64 U[4], G[4], F[4], H[4];
+        for (int v = 0; v < 4; ++v) U[v] = D64{K.ubv[v * nrow + i]};
+        const D64 ir = D64{1.0} / U[0];
+        const D64 p = pressure(U[3], K.pc, &spt);
+        flux_c<D64, 0>(U, U[1] * ir, p, F);
+        for (int v = 0; v < 4; ++v) fbx[v * nrow + i] = F[v].x;
+        flux_c<D64, 1>(U, U[2] * ir, p, F);
+        for (int v = 0; v < 4; ++v) fbz[v * nrow + i] = F[v].x;
+        hllc<D64, 0>(U, U, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbx[v * nrow + i] = H[v].x;
+        mirror<D64, 0>(U, G);
+        hllc<D64, 0>(G, U, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbxw[v * nrow + i] = H[v].x;
+        hllc<D64, 0>(U, G, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbxw[(4 + v) * nrow + i] = H[v].x;
+    } else if (i < nrow + K.nz + 1) {
+        const int j = i - nrow;
+        const int nf = K.nz + 1;
+        D64 U[4], G[4], H[4];
+        for (int v = 0; v < 4; ++v) U[v] = D64{K.ubh[v * nf + j]};
+        mirror<D64, 1>(U, G);
+        if (j == 0)
+            hllc<D64, 1>(G, U, K.pc, &spt, H);
+        else if (j == K.nz)
+            hllc<D64, 1>(U, G, K.pc, &spt, H);
+        else
+            hllc<D64, 1>(U, U, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbz[v * nf + j] = H[v].x;
+    }
+}
+
+DGK make_K(jfnk_ctx *c) {
+    DGK K;
+    K.nx = c->grid.nx;
+    K.nz = c->grid.nz;
+    K.n_el = c->n_el;
+    K.periodic = c->grid.periodic_x;
+    K.two_hx = 2.0 / c->hx;
+    K.two_hz = 2.0 / c->hz;
+    K.g = c->phys.g;
+    K.mu = c->phys.mu;
+    const double n1 = c->np1;
+    K.eta_x = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hx;
+    K.eta_z = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hz;
+    K.pc = c->pc;
+    K.pt = c->powtab;
+    K.ubv = c->ubv;
+    K.dubv = c->dubv;
+    K.fbx = c->fbx;
+    K.fbz = c->fbz;
+    K.hbx = c->hbx;
+    K.hbxw = c->hbxw;
+    K.ubh = c->ubh;
+    K.dubh = c->dubh;
+    K.hbz = c->hbz;
+    K.ubvf = c->ubvf;
+    K.dubvf = c->dubvf;
+    K.ubhf = c->ubhf;
+    K.dubhf = c->dubhf;
+    K.tab = c->tab;
+    return K;
+}
+
+template <class T, int IN, int MODE, int NP1, bool VISC>
+int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, cudaStream_t s) {
+    typedef typename OutT<T>::type O;
+    O *phix, *symx, *phiz, *symz;
+    if (IN == 2) {
+        phix = (O *)c->phixf;
+        symx = (O *)c->symxf;
+        phiz = (O *)c->phizf;
+        symz = (O *)c->symzf;
+    } else {
+        phix = (O *)c->phix;
+        symx = (O *)c->symx;
+        phiz = (O *)c->phiz;
+        symz = (O *)c->symz;
+    }
+    const long long nf = (long long)K.nz * (K.nx + 1) * NP1 + (long long)(K.nz + 1) * K.nx * NP1;
+    if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
+    k_faces<T, IN, NP1, VISC><<<(unsigned)((nf + 127) / 128), 128, 0, s>>>(K, ld, phix, symx, phiz, symz); jf_launched();
+    if (c->timing) JF_CK(cudaEventRecord(c->tev[1], s));
+    constexpr int EPB = EPBOf<NP1>::value;
+    const int nb = (K.n_el + EPB - 1) / EPB;
+    k_volume<T, IN, MODE, NP1, VISC><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz); jf_launched();
+    JF_CK(cudaGetLastError());
+    if (c->timing) {
+        JF_CK(cudaEventRecord(c->tev[2], s));
+        JF_CK(cudaEventSynchronize(c->tev[2]));
+        float m0 = 0.f, m1 = 0.f;
+        JF_CK(cudaEventElapsedTime(&m0, c->tev[0], c->tev[1]));
+        JF_CK(cudaEventElapsedTime(&m1, c->tev[1], c->tev[2]));
+        c->t_faces_ms += m0;
+        c->t_volume_ms += m1;
+    }
+    return JFNK_OK;
+}
+
+template <int NP1, bool VISC>
+int dispatch_mode(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
+    DGK K = make_K(c);
+    switch (mode) {
+        case DG_RES: return launch<D64, 0, DG_RES, NP1, VISC>(c, K, Loader<D64, 0>{a.U}, a, s);
+        case DG_G: return launch<D64, 0, DG_G, NP1, VISC>(c, K, Loader<D64, 0>{a.U}, a, s);
+        case DG_JV: return launch<D64, 1, DG_JV, NP1, VISC>(c, K, Loader<D64, 1>{a.U, a.y, a.eps, 0.0}, a, s);
+        case DG_SMOOTH64:
+            return launch<D64, 1, DG_SMOOTH64, NP1, VISC>(c, K, Loader<D64, 1>{a.U, a.y, a.eps, 0.0}, a, s);
+        case DG_TLJV: return launch<TL32, 2, DG_TLJV, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
+        case DG_TLSMOOTH: return launch<TL32, 2, DG_TLSMOOTH, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
+    }
+    return JFNK_EINVAL;
+}
+
+}  // namespace
+
+int dg_setup_background(jfnk_ctx *c) {
+    DGK K = make_K(c);
+    const int n = c->grid.nz * c->np1 + c->grid.nz + 1;
+    k_bg_dg<<<(n + 127) / 128, 128>>>(K, c->fbx, c->fbz, c->hbx, c->hbxw, c->hbz); jf_launched();
+    JF_CK(cudaGetLastError());
+    JF_CK(cudaDeviceSynchronize());
+    return JFNK_OK;
+}
+
+int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
+    c->dg_calls++;
+    const bool visc = c->phys.mu != 0.0;
+    switch (c->np1) {
+        case 2: return visc ? dispatch_mode<2, true>(c, mode, a, s) : dispatch_mode<2, false>(c, mode, a, s);
+        case 3: return visc ? dispatch_mode<3, true>(c, mode, a, s) : dispatch_mode<3, false>(c, mode, a, s);
+        case 4: return visc ? dispatch_mode<4, true>(c, mode, a, s) : dispatch_mode<4, false>(c, mode, a, s);
+        case 5: return visc ? dispatch_mode<5, true>(c, mode, a, s) : dispatch_mode<5, false>(c, mode, a, s);
+    }
+    return JFNK_EINVAL;
+}

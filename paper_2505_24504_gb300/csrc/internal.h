@@ -1,0 +1,171 @@
+// Internal state of a jfnk context (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/jfnk.h"
+#include "physics.cuh"
+
+#define JF_MAXLEV 12
+
+// Fixed 1D tables of the nodal Q_k space on Gauss-Legendre nodes (k <= 4).
+struct DGTab {
+    int np1;
+    double xi[5], w[5];
+    double Dn[5][5];     // Dn[a][q] = l_q'(xi_a): derivative at node a of basis q
+    double Dw[5][5];     // Dw[a][q] = w_q l_a'(xi_q) / w_a: volume term of the weak form
+    double lp[5], lm[5];     // l_a(+1), l_a(-1)
+    double dlp[5], dlm[5];   // l_a'(+1), l_a'(-1)
+    double lpw[5], lmw[5], dlpw[5], dlmw[5];   // the same divided by w_a
+    double V[5][5];      // V[i][a] = l_a(c_i), subcell centre c_i = -1 + (2i+1)/(k+1)
+    double Vinv[5][5];
+    double om[5];        // modified Newton-Cotes weights on [0,1] at the subcell centres
+};
+
+struct FVLev {
+    int NX, NZ;
+    int fac;             // agglomeration factor to the next coarser level (0: coarsest)
+    double Hx, Hz;
+    size_t n;            // 4 NX NZ
+    double *ub;          // [4][NZ] background at the cell centres
+    float *ubf;          // its FP32 copy (tangent kernels)
+    double *hbx;         // [4][NZ] HLLC(ub, ub; x)
+    double *hbxw;        // [2][4][NZ] left wall HLLC(mirror ub, ub), right wall HLLC(ub, mirror ub)
+    double *hbz;         // [4][NZ+1] HLLC(ub_{J-1}, ub_J; z); J = 0 bottom wall, J = NZ top wall
+    // level vectors; element type is double (prec 64) or float (prec 32/16)
+    void *u, *fu, *x, *x2, *b, *r;
+    void *dtau;          // [NZ][NX]
+    uint16_t *xb, *bb;   // bf16 storage of x and b on the coarsest level (prec 16)
+};
+
+struct jfnk_ctx {
+    jfnk_grid grid;
+    int k, np1, n_el;
+    jfnk_physics phys;
+    jfnk_opts opts;
+    size_t N;            // 4 n_el (k+1)^2
+    size_t npt;          // n_el (k+1)^2 nodes
+    double hx, hz;
+    PhysC pc;
+    DGTab tab;
+    int dev;
+    // key
+    int mg_on, dg_pre, dg_post, fine_pre, fine_post, mid_pre, mid_post, cycles;
+    int prec;            // 64, 32, 16
+    // device tables
+    PowTab *powtab;
+    double *ubv, *dubv, *fbx, *fbz, *hbx, *hbxw;   // node rows: [4][nz np1] ([2][4][..] for hbxw)
+    double *ubh, *dubh, *hbz;                      // horizontal faces: [4][nz+1]
+    float *ubvf, *dubvf, *ubhf, *dubhf;            // FP32 copies (tangent kernels)
+    double *prow;        // [nz np1] p0^(R/cp) p~^(1/gamma) / R at node rows (insertion)
+    double *theta_row;   // [nz np1] theta~ at node rows
+    // DG face buffers: FP64 and FP32-tangent variants
+    double *phix, *symx, *phiz, *symz;
+    float *phixf, *symxf, *phizf, *symzf;
+    // DG work vectors (FP64, N each)
+    double *fU, *w1, *w2, *Ubs, *Un, *Usave, *G, *dU;
+    // Krylov basis: V (m+1) N doubles, Z m N of the preconditioner's type
+    double *V;
+    void *Z;
+    // preconditioner DG vectors (type of the preconditioner)
+    void *pz, *pz2, *pd, *pr;
+    double *dtau_dg;     // [n_el]
+    float *dtau_dgf;     // [n_el] FP32 copy (prec 32)
+    float *Usf;          // FP32 copy of the linearisation state U' + Ubar (prec 32)
+    int nlev;
+    FVLev lev[JF_MAXLEV];
+    // reductions
+    double *partial;     // scratch partial sums
+    int nb_red;          // partial-sum blocks
+    double *scal;        // device scalars (norms, eps)
+    double *h_pinned;    // host pinned scratch for Hessenberg columns
+    // linearisation of the preconditioner (set by mg_linearize)
+    double mg_adt;
+    const double *mg_U;
+    // counters of the current call
+    long long dg_calls, fv_calls;
+    // graph of one preconditioner application
+    cudaGraphExec_t mg_graph;
+    const void *mg_graph_r;
+    void *mg_graph_z;
+    int mg_graph_valid;
+    size_t alloc_bytes;
+    void *allocs;        // list of this context's allocations (api.cu)
+    // optional per-launch timing of the DG kernels (jfnk_time_operator)
+    cudaEvent_t tev[3];
+    int timing;
+    double t_faces_ms, t_volume_ms;
+};
+
+// device scalar slots in ctx->scal
+enum { S_NORM = 0, S_EPS = 1, S_EPSFV = 8, S_NRM_FV = 24, S_H = 64, S_H2 = 128, S_COUNT = 256 };
+
+// number of kernels this library has launched (diagnostic counter)
+extern unsigned long long g_jf_launches;
+inline void jf_launched(unsigned n = 1) { __atomic_fetch_add(&g_jf_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+// ---- kernels / launchers (implemented in the .cu files) ----
+int dg_setup_background(jfnk_ctx *c);
+int fv_setup_background(jfnk_ctx *c);
+
+// DG operator modes
+enum DGMode {
+    DG_RES = 0,      // out0 = f(U')
+    DG_JV = 1,       // out0 = y - adt (f(U' + eps y) - fU) / eps       (eps: device scalar)
+    DG_G = 2,        // out0 = U' - adt f - Ubar_s ; out1 = f
+    DG_SMOOTH64 = 3, // out0 = z + dtau (r - [z - adt (f(U'+eps z) - fU)/eps])
+    DG_TLJV = 4,     // out0 = z - adt J z                             (FP32 tangent)
+    DG_TLSMOOTH = 5  // out0 = z + dtau (r - (z - adt J z))            (FP32 tangent)
+};
+
+struct DGArgs {
+    const double *U;       // state U' (FP64)
+    const float *Uf;       // state U' (FP32, tangent modes)
+    const double *y;       // FP64 direction (JV, SMOOTH64)
+    const float *yf;       // FP32 direction (TL modes)
+    const double *fU;      // cached f(U')
+    const double *r;       // FP64 right-hand side (SMOOTH64)
+    const float *rf;       // FP32 right-hand side (TLSMOOTH)
+    const double *Ubs;     // Ubar_s (G)
+    const double *eps;     // device scalar eps (JV, SMOOTH64)
+    const double *dtau;    // [n_el] (smoothing)
+    const float *dtauf;    // [n_el] (FP32 smoothing)
+    double adt;
+    void *out0;
+    double *out1;
+};
+
+int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+
+// reductions / BLAS-1 (blas.cu)
+int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out_dev, int op, cudaStream_t s);
+int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out_dev, int op, cudaStream_t s);
+enum { RED_SUM = 0, RED_SQRT = 1, RED_EPS = 2, RED_EPS32 = 3 };
+int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h_dev, cudaStream_t s);
+int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h_dev, double *w, size_t n, double sign, cudaStream_t s);
+int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
+int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);
+int blas_zcomb(const void *Z, int prec32, int nz, size_t n, const double *yv, double *x, cudaStream_t s);
+int blas_copy_d2f(const double *x, float *y, size_t n, cudaStream_t s);
+int blas_copy_f2d(const float *x, double *y, size_t n, cudaStream_t s);
+int blas_scale(double a, const double *x, double *y, size_t n, cudaStream_t s);
+
+// preconditioner (mg.cu)
+int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s);
+int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s);
+int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s);
+int transfer_to_fv64(jfnk_ctx *c, const double *u, double *v, cudaStream_t s);
+int transfer_to_dg64(jfnk_ctx *c, const double *v, double *u, int accumulate, cudaStream_t s);
+
+#define JF_CK(...)                                   \
+    do {                                             \
+        cudaError_t e_ = (__VA_ARGS__);              \
+        if (e_ != cudaSuccess) return JFNK_ECUDA;    \
+    } while (0)
+#define JF_RET(...)                                  \
+    do {                                             \
+        int r_ = (__VA_ARGS__);                      \
+        if (r_ != JFNK_OK) return r_;                \
+    } while (0)

@@ -1,0 +1,835 @@
+// Low-order-approximation preconditioner Q^-1 = T^-1 q^-1 T (eq. preconditioner,
+// Sec. 3.2-3.5) on the GPU.
+//
+//  k_to_fv    T^mf: one thread per subcell; the element's nodal values go
+//             through shared memory and the 1D interpolation matrix V twice
+//             (tensor product), then the mass fix of eq. (transfer-mass-fix)
+//             with the element mass of the DG polynomial taken from the subcell
+//             values by the modified Newton-Cotes weights (Sec. 3.3, Appendix A).
+//  k_to_dg    T^-1: inverse tensor interpolation and the mass fix back.
+//  k_fv       f_low and the level products on one FV level, one thread per cell:
+//             HLLC^pert on the four faces (background fluxes precomputed per
+//             row), gravity source, two-point viscous flux.  Modes: residual,
+//             pseudo-time step x + dtau (b - g'x), defect g'x - b.  g' is the
+//             FD quotient of Sec. 3.1 (FP64) or the exact tangent (FP32).
+//  k_restrict / k_prolong   agglomeration R and injection P (Sec. 3.4).
+//  mg_cycle   MG_l(x, b; u) of Sec. 3.4 on the host; every level's work is a few
+//             launches on the caller's stream, so an application can be captured
+//             in one CUDA graph.
+#include <string.h>
+
+#include "internal.h"
+
+namespace {
+
+struct FVK {
+    int NX, NZ, periodic;
+    double iHx, iHz, g, mu;
+    PhysC pc;
+    const PowTab *pt;
+    const double *ub, *hbx, *hbxw, *hbz;
+    const float *ubf;
+};
+
+template <class T> JF_D T bgs(const double *d, const float *f, size_t i);
+template <> JF_D D64 bgs<D64>(const double *d, const float *, size_t i) { return D64{d[i]}; }
+template <> JF_D TL32 bgs<TL32>(const double *, const float *f, size_t i) { return TL32{f[i], 0.0f}; }
+
+__device__ __forceinline__ void load_pt(PowTab *s, const PowTab *g) {
+    const double *src = reinterpret_cast<const double *>(g);
+    double *dst = reinterpret_cast<double *>(s);
+    for (int i = threadIdx.x; i < (int)(sizeof(PowTab) / sizeof(double)); i += blockDim.x) dst[i] = src[i];
+}
+
+// level state loaders: IN 0 u; IN 1 u + eps x (FP64, eps on device); IN 2 TL32 (u, x) in FP32
+template <class T, int IN> struct FLoad;
+template <> struct FLoad<D64, 0> {
+    const double *u;
+    JF_D void prepare() {}
+    JF_D double step() const { return 0.0; }
+    JF_D D64 operator()(size_t i) const { return D64{u[i]}; }
+};
+template <> struct FLoad<D64, 1> {
+    const double *u, *x, *epsp;
+    double eps;
+    JF_D void prepare() { eps = *epsp; }
+    JF_D double step() const { return eps; }
+    JF_D D64 operator()(size_t i) const { return D64{__fma_rn(eps, x[i], u[i])}; }
+};
+template <> struct FLoad<TL32, 2> {
+    const float *u, *x;
+    JF_D void prepare() {}
+    JF_D double step() const { return 0.0; }
+    JF_D TL32 operator()(size_t i) const { return TL32{u[i], x[i]}; }
+};
+
+enum { FV_RES = 0, FV_SMOOTH = 1, FV_DEFECT = 2 };
+
+template <class T> struct SOf;
+template <> struct SOf<D64> { typedef double type; };
+template <> struct SOf<TL32> { typedef float type; };
+JF_D double oval(D64 a) { return a.x; }
+JF_D float oval(TL32 a) { return a.d; }
+
+template <class T, int D>
+JF_D void face_flux(const T UL[4], const T UR[4], bool wallL, bool wallR, const double *hb, size_t hs,
+                    size_t hi, bool sub, const FVK &K, const PowTab *pt, T H[4]) {
+    T G[4];
+    if (wallL) {
+        mirror<T, D>(UR, G);
+        hllc<T, D>(G, UR, K.pc, pt, H);
+    } else if (wallR) {
+        mirror<T, D>(UL, G);
+        hllc<T, D>(UL, G, K.pc, pt, H);
+    } else {
+        hllc<T, D>(UL, UR, K.pc, pt, H);
+    }
+    if (sub) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * hs + hi], T{});
+    }
+}
+
+template <class T>
+JF_D void visc2(const T UL[4], const T UR[4], double mu, double id, T V[4]) {
+    const T irL = mk(1.0, T{}) / UL[0], irR = mk(1.0, T{}) / UR[0];
+    const T c = mk(0.5 * mu * id, T{}) * (UL[0] + UR[0]);
+    V[0] = mk(0.0, T{});
+#pragma unroll
+    for (int v = 1; v < 4; ++v) V[v] = c * (UR[v] * irR - UL[v] * irL);
+}
+
+// One thread per cell of an NX x NZ level.
+template <class T, int IN, int MODE, bool VISC>
+__global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
+                                            const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
+                                            const double *fu, double adt, typename SOf<T>::type *out) {
+    typedef typename SOf<T>::type S;
+    __shared__ PowTab spt;
+    load_pt(&spt, K.pt);
+    FLoad<T, IN> ld = ld0;
+    ld.prepare();
+    __syncthreads();
+    const int NX = K.NX, NZ = K.NZ;
+    const size_t n1 = (size_t)NX * NZ;
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n1) return;
+    const int I = (int)(c % NX), Jz = (int)(c / NX);
+    const bool sub = (IN != 2);
+    T U[4], Un[4][4];   // own state and the W, E, S, N neighbours
+    int nb[4] = {-1, -1, -1, -1};
+    if (I > 0) nb[0] = Jz * NX + I - 1;
+    else if (K.periodic) nb[0] = Jz * NX + NX - 1;
+    if (I < NX - 1) nb[1] = Jz * NX + I + 1;
+    else if (K.periodic) nb[1] = Jz * NX;
+    if (Jz > 0) nb[2] = (Jz - 1) * NX + I;
+    if (Jz < NZ - 1) nb[3] = (Jz + 1) * NX + I;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        U[v] = ld((size_t)v * n1 + c) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int Jq = (q == 2) ? Jz - 1 : (q == 3 ? Jz + 1 : Jz);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            Un[q][v] = nb[q] >= 0 ? ld((size_t)v * n1 + nb[q]) + bgs<T>(K.ub, K.ubf, v * NZ + Jq) : U[v];
+    }
+    T HW[4], HE[4], HS[4], HN[4];
+    face_flux<T, 0>(Un[0], U, nb[0] < 0, false, nb[0] < 0 ? K.hbxw : K.hbx, NZ, Jz, sub, K, &spt, HW);
+    face_flux<T, 0>(U, Un[1], false, nb[1] < 0, nb[1] < 0 ? K.hbxw + 4 * NZ : K.hbx, NZ, Jz, sub, K, &spt, HE);
+    face_flux<T, 1>(Un[2], U, nb[2] < 0, false, K.hbz, NZ + 1, Jz, sub, K, &spt, HS);
+    face_flux<T, 1>(U, Un[3], false, nb[3] < 0, K.hbz, NZ + 1, Jz + 1, sub, K, &spt, HN);
+    T f[4];
+    const T iHx = mk(K.iHx, T{}), iHz = mk(K.iHz, T{});
+#pragma unroll
+    for (int v = 0; v < 4; ++v) f[v] = -((HE[v] - HW[v]) * iHx + (HN[v] - HS[v]) * iHz);
+    const T up0 = ld(c);
+    f[2] = f[2] - mk(K.g, T{}) * up0;
+    if (VISC) {
+        T VW[4], VE[4], VS[4], VN[4];
+        const T zero = mk(0.0, T{});
+        if (nb[0] >= 0) visc2(Un[0], U, K.mu, K.iHx, VW); else { for (int v = 0; v < 4; ++v) VW[v] = zero; }
+        if (nb[1] >= 0) visc2(U, Un[1], K.mu, K.iHx, VE); else { for (int v = 0; v < 4; ++v) VE[v] = zero; }
+        if (nb[2] >= 0) visc2(Un[2], U, K.mu, K.iHz, VS); else { for (int v = 0; v < 4; ++v) VS[v] = zero; }
+        if (nb[3] >= 0) visc2(U, Un[3], K.mu, K.iHz, VN); else { for (int v = 0; v < 4; ++v) VN[v] = zero; }
+#pragma unroll
+        for (int v = 1; v < 4; ++v) f[v] = f[v] + (VE[v] - VW[v]) * iHx + (VN[v] - VS[v]) * iHz;
+    }
+    const double eps = ld.step();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const size_t gi = (size_t)v * n1 + c;
+        if (MODE == FV_RES) {
+            out[gi] = (S)oval(f[v]);
+        } else {
+            const S x = xin[gi];
+            S gx;
+            if (IN == 1)
+                gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)oval(f[v]) - fu[gi]) / eps);
+            else
+                gx = x - (S)adt * (S)oval(f[v]);
+            if (MODE == FV_SMOOTH)
+                out[gi] = x + dtau[c] * (b[gi] - gx);
+            else
+                out[gi] = gx - b[gi];
+        }
+    }
+}
+
+// FV pseudo-time step sizes: dtau = sigma / (1 + adt lambda), lambda = sum_faces
+// 1/2 s_e |e|/|c| + 2 mu (1/Hx^2 + 1/Hz^2), s_e = max over both sides of |v.n| + c.
+template <class S>
+__global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) {
+    __shared__ PowTab spt;
+    load_pt(&spt, K.pt);
+    __syncthreads();
+    const int NX = K.NX, NZ = K.NZ;
+    const size_t n1 = (size_t)NX * NZ;
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n1) return;
+    const int I = (int)(c % NX), Jz = (int)(c / NX);
+    auto st = [&](int i, int j, double U[4]) {
+        const size_t cc = (size_t)j * NX + i;
+        for (int v = 0; v < 4; ++v) U[v] = (double)u[(size_t)v * n1 + cc] + K.ub[v * NZ + j];
+    };
+    double U[4], V[4];
+    st(I, Jz, U);
+    const double sx = wave_speed(U, 0, K.pc, &spt), sz = wave_speed(U, 1, K.pc, &spt);
+    double eW = sx, eE = sx, eS = sz, eN = sz;
+    if (I > 0 || K.periodic) { st(I > 0 ? I - 1 : NX - 1, Jz, V); eW = fmax(sx, wave_speed(V, 0, K.pc, &spt)); }
+    if (I < NX - 1 || K.periodic) { st(I < NX - 1 ? I + 1 : 0, Jz, V); eE = fmax(sx, wave_speed(V, 0, K.pc, &spt)); }
+    if (Jz > 0) { st(I, Jz - 1, V); eS = fmax(sz, wave_speed(V, 1, K.pc, &spt)); }
+    if (Jz < NZ - 1) { st(I, Jz + 1, V); eN = fmax(sz, wave_speed(V, 1, K.pc, &spt)); }
+    const double lam = 0.5 * (eW + eE) * K.iHx + 0.5 * (eS + eN) * K.iHz +
+                       2.0 * K.mu * (K.iHx * K.iHx + K.iHz * K.iHz);
+    dtau[c] = (S)(sigma / (1.0 + adt * lam));
+}
+
+// DG pseudo-time step per element: lambda_E = (k+1)^2 max_nodes(|v| + c)(1/hx + 1/hz)
+// + 2 mu (k+1)^4 (1/hx^2 + 1/hz^2).
+__global__ void k_dg_dtau(const double *U, const double *ubv, int nx, int nz, int np1, PhysC pc,
+                          const PowTab *pt, double ihx, double ihz, double mu, double adt, double sigma,
+                          double *dtau, float *dtauf) {
+    __shared__ PowTab spt;
+    load_pt(&spt, pt);
+    __syncthreads();
+    const int n_el = nx * nz;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int NP = np1 * np1;
+    const size_t N1 = (size_t)n_el * NP;
+    const int ez = e / nx;
+    const size_t nrow = (size_t)nz * np1;
+    double vmax = 0.0;
+    for (int node = 0; node < NP; ++node) {
+        const int J = ez * np1 + node / np1;
+        double W[4];
+        for (int v = 0; v < 4; ++v) W[v] = U[v * N1 + (size_t)e * NP + node] + ubv[v * nrow + J];
+        const double ir = 1.0 / W[0];
+        const double p = pc.p0 * pow_gamma_tab(pc.R_over_p0 * W[3], &spt);
+        const double s = sqrt((W[1] * ir) * (W[1] * ir) + (W[2] * ir) * (W[2] * ir)) + sqrt(pc.gamma * p * ir);
+        vmax = fmax(vmax, s);
+    }
+    const double n2 = (double)np1 * np1;
+    const double lam = n2 * vmax * (ihx + ihz) + 2.0 * mu * n2 * n2 * (ihx * ihx + ihz * ihz);
+    dtau[e] = sigma / (1.0 + adt * lam);
+    if (dtauf) dtauf[e] = (float)dtau[e];
+}
+
+// ---- transfer -------------------------------------------------------------
+struct TK {
+    int nx, nz, np1, n_el, NX, NZ;
+    DGTab tab;
+};
+
+template <class Si, class So> struct RealOf { typedef float type; };
+template <> struct RealOf<double, double> { typedef double type; };
+
+template <class R, int NP1>
+__device__ __forceinline__ void load_ttab(const TK &K, R sV[NP1][NP1], R sVi[NP1][NP1], R som[NP1]) {
+    for (int t = threadIdx.x; t < NP1 * NP1; t += blockDim.x) {
+        sV[t / NP1][t % NP1] = (R)K.tab.V[t / NP1][t % NP1];
+        sVi[t / NP1][t % NP1] = (R)K.tab.Vinv[t / NP1][t % NP1];
+    }
+    for (int t = threadIdx.x; t < NP1; t += blockDim.x) som[t] = (R)K.tab.om[t];
+}
+
+// T^mf: DG (Si) -> FV (So), arithmetic in the storage precision.  Block: EPB
+// elements x NP subcells.
+template <class Si, class So, int NP1>
+__global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix) {
+    typedef typename RealOf<Si, So>::type R;
+    constexpr int NP = NP1 * NP1;
+    constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+    __shared__ R su[EPB][4][NP];
+    __shared__ R st[EPB][4][NP];
+    __shared__ R sc[EPB][4];
+    __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
+    load_ttab<R, NP1>(K, sV, sVi, som);
+    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+    const int e = blockIdx.x * EPB + le;
+    const bool act = e < K.n_el;
+    const size_t N1 = (size_t)K.n_el * NP;
+    const int i = node % NP1, j = node / NP1;   // subcell (i along x, j along z) / node (a, b)
+    if (act)
+        for (int q = 0; q < 4; ++q) su[le][q][node] = (R)u[q * N1 + (size_t)e * NP + node];
+    __syncthreads();
+    // t1(i, b) = sum_a V[i][a] u(a, b), stored at [b][i]
+    if (act)
+        for (int q = 0; q < 4; ++q) {
+            R acc = 0;
+#pragma unroll
+            for (int a = 0; a < NP1; ++a) acc = fma(sV[i][a], su[le][q][j * NP1 + a], acc);
+            st[le][q][j * NP1 + i] = acc;
+        }
+    __syncthreads();
+    R Tu[4];
+    if (act)
+        for (int q = 0; q < 4; ++q) {
+            R acc = 0;
+#pragma unroll
+            for (int b = 0; b < NP1; ++b) acc = fma(sV[j][b], st[le][q][b * NP1 + i], acc);
+            Tu[q] = acc;
+        }
+    __syncthreads();
+    if (act)
+        for (int q = 0; q < 4; ++q) su[le][q][node] = Tu[q];
+    __syncthreads();
+    if (act && node < 4) {
+        // m_E(T u)/|E| = subcell mean; m_E(u)/|E| by the midpoint weights on the subcell values
+        const int q = node;
+        R mfv = 0, mnc = 0;
+        for (int jj = 0; jj < NP1; ++jj)
+            for (int ii = 0; ii < NP1; ++ii) {
+                const R x = su[le][q][jj * NP1 + ii];
+                mfv += x;
+                mnc = fma(som[ii] * som[jj], x, mnc);
+            }
+        sc[le][q] = massfix ? (mfv / (R)NP - mnc) : (R)0;
+    }
+    __syncthreads();
+    if (!act) return;
+    const int ez = e / K.nx, ex = e % K.nx;
+    const size_t I = (size_t)ex * NP1 + i, Jr = (size_t)ez * NP1 + j;
+    const size_t n1 = (size_t)K.NX * K.NZ;
+    for (int q = 0; q < 4; ++q) v[q * n1 + Jr * K.NX + I] = (So)(Tu[q] - sc[le][q]);
+}
+
+// T^-1_mf: FV (Si) -> DG (So); acc 0: store, 1: add
+template <class Si, class So, int NP1>
+__global__ void __launch_bounds__(128) k_to_dg(TK K, const Si *v, So *u, int massfix, int acc_mode) {
+    typedef typename RealOf<Si, So>::type R;
+    constexpr int NP = NP1 * NP1;
+    constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+    __shared__ R sv[EPB][4][NP];
+    __shared__ R st[EPB][4][NP];
+    __shared__ R sc[EPB][4];
+    __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
+    load_ttab<R, NP1>(K, sV, sVi, som);
+    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+    const int e = blockIdx.x * EPB + le;
+    const bool act = e < K.n_el;
+    const size_t n1 = (size_t)K.NX * K.NZ;
+    const int a = node % NP1, b = node / NP1;
+    const int ez = act ? e / K.nx : 0, ex = act ? e % K.nx : 0;
+    if (act) {
+        const size_t I = (size_t)ex * NP1 + a, Jr = (size_t)ez * NP1 + b;   // subcell (a, b) here
+        for (int q = 0; q < 4; ++q) sv[le][q][node] = (R)v[q * n1 + Jr * K.NX + I];
+    }
+    __syncthreads();
+    if (act)
+        for (int q = 0; q < 4; ++q) {   // t1(a, j) = sum_i Vinv[a][i] v(i, j), at [j][a]
+            R acc = 0;
+#pragma unroll
+            for (int i = 0; i < NP1; ++i) acc = fma(sVi[a][i], sv[le][q][b * NP1 + i], acc);
+            st[le][q][b * NP1 + a] = acc;
+        }
+    __syncthreads();
+    R Ti[4];
+    if (act)
+        for (int q = 0; q < 4; ++q) {
+            R acc = 0;
+#pragma unroll
+            for (int jj = 0; jj < NP1; ++jj) acc = fma(sVi[b][jj], st[le][q][jj * NP1 + a], acc);
+            Ti[q] = acc;
+        }
+    if (act && node < 4) {
+        // m_E(T^-1 v)/|E| from the subcell values (T T^-1 v = v) by the midpoint weights,
+        // m_E(v)/|E| the subcell mean
+        const int q = node;
+        R mfv = 0, mnc = 0;
+        for (int jj = 0; jj < NP1; ++jj)
+            for (int ii = 0; ii < NP1; ++ii) {
+                const R x = sv[le][q][jj * NP1 + ii];
+                mfv += x;
+                mnc = fma(som[ii] * som[jj], x, mnc);
+            }
+        sc[le][q] = massfix ? (mnc - mfv / (R)NP) : (R)0;
+    }
+    __syncthreads();
+    if (!act) return;
+    const size_t N1 = (size_t)K.n_el * NP;
+    for (int q = 0; q < 4; ++q) {
+        const size_t gi = q * N1 + (size_t)e * NP + node;
+        const R val = Ti[q] - sc[le][q];
+        u[gi] = acc_mode ? (So)((R)u[gi] + val) : (So)val;
+    }
+}
+
+// R: coarse = mean of fac x fac children
+template <class S>
+__global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
+    const int NXc = NXf / fac, NZc = NZf / fac;
+    const size_t nc = (size_t)NXc * NZc;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * nc) return;
+    const int q = (int)(t / nc);
+    const size_t c = t % nc;
+    const int I = (int)(c % NXc), J = (int)(c / NXc);
+    const S *fq = f + (size_t)q * NXf * NZf;
+    S acc = 0;
+    for (int jj = 0; jj < fac; ++jj)
+        for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
+    cz[t] = acc / (S)(fac * fac);
+}
+
+// x = (zero ? 0 : x) - P v
+template <class S>
+__global__ void k_prolong(S *x, const S *vc, int NXf, int NZf, int fac, int zero) {
+    const size_t nf = (size_t)NXf * NZf;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * nf) return;
+    const int q = (int)(t / nf);
+    const size_t c = t % nf;
+    const int I = (int)(c % NXf), J = (int)(c / NXf);
+    const int NXc = NXf / fac, NZc = NZf / fac;
+    const S pv = vc[(size_t)q * NXc * NZc + (size_t)(J / fac) * NXc + I / fac];
+    x[t] = zero ? -pv : x[t] - pv;
+}
+
+// x = dtau b (first smoothing step from zero)
+template <class S>
+__global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * n1) return;
+    x[t] = dtau[t % n1] * b[t];
+}
+
+template <class S>
+__global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int NP) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * N1) return;
+    z[t] = dtau[(t % N1) / NP] * r[t];
+}
+
+template <class S>
+__global__ void k_neg(S *x, const S *b, size_t n) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) x[t] = -b[t];
+}
+
+template <class S>
+__global__ void k_sub(const S *r, const S *w, S *d, size_t n) {   // d = r - w
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) d[t] = r[t] - w[t];
+}
+
+__global__ void k_bg_fv(FVK K, double *hbx, double *hbxw, double *hbz) {
+    __shared__ PowTab spt;
+    load_pt(&spt, K.pt);
+    __syncthreads();
+    const int NZ = K.NZ;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    D64 U[4], G[4], H[4];
+    if (i < NZ) {
+        for (int v = 0; v < 4; ++v) U[v] = D64{K.ub[v * NZ + i]};
+        hllc<D64, 0>(U, U, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbx[v * NZ + i] = H[v].x;
+        mirror<D64, 0>(U, G);
+        hllc<D64, 0>(G, U, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbxw[v * NZ + i] = H[v].x;
+        hllc<D64, 0>(U, G, K.pc, &spt, H);
+        for (int v = 0; v < 4; ++v) hbxw[(4 + v) * NZ + i] = H[v].x;
+    } else if (i < 2 * NZ + 1) {
+        const int j = i - NZ;   // face between rows j-1 and j
+        D64 B[4], T_[4];
+        if (j == 0) {
+            for (int v = 0; v < 4; ++v) T_[v] = D64{K.ub[v * NZ + 0]};
+            mirror<D64, 1>(T_, G);
+            hllc<D64, 1>(G, T_, K.pc, &spt, H);
+        } else if (j == NZ) {
+            for (int v = 0; v < 4; ++v) B[v] = D64{K.ub[v * NZ + NZ - 1]};
+            mirror<D64, 1>(B, G);
+            hllc<D64, 1>(B, G, K.pc, &spt, H);
+        } else {
+            for (int v = 0; v < 4; ++v) {
+                B[v] = D64{K.ub[v * NZ + j - 1]};
+                T_[v] = D64{K.ub[v * NZ + j]};
+            }
+            hllc<D64, 1>(B, T_, K.pc, &spt, H);
+        }
+        for (int v = 0; v < 4; ++v) hbz[v * (NZ + 1) + j] = H[v].x;
+    }
+}
+
+inline unsigned nblk(size_t n, int bs = 128) { return (unsigned)((n + bs - 1) / bs); }
+
+FVK make_fvk(jfnk_ctx *c, int l) {
+    const FVLev &L = c->lev[l];
+    FVK K;
+    K.NX = L.NX;
+    K.NZ = L.NZ;
+    K.periodic = c->grid.periodic_x;
+    K.iHx = 1.0 / L.Hx;
+    K.iHz = 1.0 / L.Hz;
+    K.g = c->phys.g;
+    K.mu = c->phys.mu;
+    K.pc = c->pc;
+    K.pt = c->powtab;
+    K.ub = L.ub;
+    K.hbx = L.hbx;
+    K.hbxw = L.hbxw;
+    K.hbz = L.hbz;
+    K.ubf = L.ubf;
+    return K;
+}
+
+TK make_tk(jfnk_ctx *c) {
+    TK K;
+    K.nx = c->grid.nx;
+    K.nz = c->grid.nz;
+    K.np1 = c->np1;
+    K.n_el = c->n_el;
+    K.NX = c->lev[0].NX;
+    K.NZ = c->lev[0].NZ;
+    K.tab = c->tab;
+    return K;
+}
+
+template <class Si, class So>
+int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s) {
+    TK K = make_tk(c);
+    const int NP = c->np1 * c->np1;
+    const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+    const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
+    switch (c->np1) {
+        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
+        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
+        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
+        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
+        default: return JFNK_EINVAL;
+    }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+template <class Si, class So>
+int to_dg(jfnk_ctx *c, const Si *v, So *u, int acc, cudaStream_t s) {
+    TK K = make_tk(c);
+    const int NP = c->np1 * c->np1;
+    const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+    const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
+    switch (c->np1) {
+        case 2: k_to_dg<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
+        case 3: k_to_dg<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
+        case 4: k_to_dg<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
+        case 5: k_to_dg<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
+        default: return JFNK_EINVAL;
+    }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+// ---- FV level products ----------------------------------------------------
+// FV_RES: out = f_low(u) (FP64 only).  FV_SMOOTH / FV_DEFECT use the FD quotient
+// (prec 64, eps = sqrt(eps_mach)/|x| from an on-device norm) or the tangent (prec 32).
+int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, const double *b, double *out,
+            cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    FVK K = make_fvk(c, l);
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    const bool visc = c->phys.mu != 0.0;
+    c->fv_calls++;
+    const unsigned g = nblk(n1);
+    if (mode == FV_RES) {
+        FLoad<D64, 0> ld{u};
+        if (visc) { k_fv<D64, 0, FV_RES, true><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
+        else { k_fv<D64, 0, FV_RES, false><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
+    } else {
+        double *epsp = c->scal + S_EPSFV + l;
+        JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPS, s));
+        FLoad<D64, 1> ld{u, x, epsp, 0.0};
+        const double *dt = (const double *)L.dtau;
+        const double *fu = (const double *)L.fu;
+        const double adt = c->mg_adt;
+        if (mode == FV_SMOOTH) {
+            if (visc) { k_fv<D64, 1, FV_SMOOTH, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            else { k_fv<D64, 1, FV_SMOOTH, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+        } else {
+            if (visc) { k_fv<D64, 1, FV_DEFECT, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            else { k_fv<D64, 1, FV_DEFECT, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+        }
+    }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float *out, cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    FVK K = make_fvk(c, l);
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    const bool visc = c->phys.mu != 0.0;
+    c->fv_calls++;
+    const unsigned g = nblk(n1);
+    FLoad<TL32, 2> ld{(const float *)L.u, x};
+    const float *dt = (const float *)L.dtau;
+    const double adt = c->mg_adt;
+    if (mode == FV_SMOOTH) {
+        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+    } else {
+        if (visc) { k_fv<TL32, 2, FV_DEFECT, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        else { k_fv<TL32, 2, FV_DEFECT, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+    }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, const void *b, void *out,
+                               cudaStream_t s) {
+    if (c->prec == 64)
+        return fv_op64(c, l, mode, (const double *)c->lev[l].u, (const double *)x, (const double *)b,
+                       (double *)out, s);
+    return fv_op32(c, l, mode, (const float *)x, (const float *)b, (float *)out, s);
+}
+
+template <class S>
+int mg_cycle_t(jfnk_ctx *c, int l, bool zero, cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    const int pre = (l == 0) ? c->fine_pre : c->mid_pre;
+    const int post = (l == 0) ? c->fine_post : c->mid_post;
+    auto smooth = [&](int steps) -> int {
+        for (int i = 0; i < steps; ++i) {
+            if (zero) {
+                k_scale_dtau<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)L.b, (const S *)L.dtau, n1); jf_launched();
+                zero = false;
+            } else {
+                JF_RET(fv_smooth_or_defect(c, l, FV_SMOOTH, L.x, L.b, L.x2, s));
+                void *t = L.x;
+                L.x = L.x2;
+                L.x2 = t;
+            }
+        }
+        JF_CK(cudaGetLastError());
+        return JFNK_OK;
+    };
+    JF_RET(smooth(pre));
+    if (l < c->nlev - 1) {
+        FVLev &C = c->lev[l + 1];
+        if (zero) {
+            k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
+            jf_launched();
+        } else
+            JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
+        k_restrict<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b); jf_launched();
+        bool vz = true;
+        for (int cyc = 0; cyc < c->cycles; ++cyc) {
+            JF_RET(mg_cycle_t<S>(c, l + 1, vz, s));
+            vz = false;
+        }
+        k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0); jf_launched();
+        zero = false;
+    }
+    JF_RET(smooth(post));
+    if (zero) JF_CK(cudaMemsetAsync(L.x, 0, L.n * sizeof(S), s));
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+template <class S>
+int dg_smooth_step(jfnk_ctx *c, const S *r, S *&z, S *&z2, bool &zero, cudaStream_t s);
+
+template <>
+int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2, bool &zero, cudaStream_t s) {
+    const int NP = c->np1 * c->np1;
+    if (zero) {
+        k_scale_dtau_dg<double><<<nblk(c->N, 256), 256, 0, s>>>(z, r, c->dtau_dg, c->npt, NP); jf_launched();
+        zero = false;
+        JF_CK(cudaGetLastError());
+        return JFNK_OK;
+    }
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPS + 1, RED_EPS, s));
+    DGArgs a = {};
+    a.U = c->mg_U;
+    a.y = z;
+    a.fU = c->fU;
+    a.r = r;
+    a.eps = c->scal + S_EPS + 1;
+    a.dtau = c->dtau_dg;
+    a.adt = c->mg_adt;
+    a.out0 = z2;
+    JF_RET(dg_apply(c, DG_SMOOTH64, a, s));
+    double *t = z;
+    z = z2;
+    z2 = t;
+    return JFNK_OK;
+}
+
+template <>
+int dg_smooth_step<float>(jfnk_ctx *c, const float *r, float *&z, float *&z2, bool &zero, cudaStream_t s) {
+    const int NP = c->np1 * c->np1;
+    if (zero) {
+        k_scale_dtau_dg<float><<<nblk(c->N, 256), 256, 0, s>>>(z, r, c->dtau_dgf, c->npt, NP); jf_launched();
+        zero = false;
+        JF_CK(cudaGetLastError());
+        return JFNK_OK;
+    }
+    DGArgs a = {};
+    a.U = c->mg_U;
+    a.Uf = c->Usf;
+    a.yf = z;
+    a.rf = r;
+    a.dtauf = c->dtau_dgf;
+    a.adt = c->mg_adt;
+    a.out0 = z2;
+    JF_RET(dg_apply(c, DG_TLSMOOTH, a, s));
+    float *t = z;
+    z = z2;
+    z2 = t;
+    return JFNK_OK;
+}
+
+// d = r - G'z
+template <class S>
+int dg_defect(jfnk_ctx *c, const S *r, const S *z, S *d, cudaStream_t s);
+
+template <>
+int dg_defect<double>(jfnk_ctx *c, const double *r, const double *z, double *d, cudaStream_t s) {
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPS + 1, RED_EPS, s));
+    DGArgs a = {};
+    a.U = c->mg_U;
+    a.y = z;
+    a.fU = c->fU;
+    a.eps = c->scal + S_EPS + 1;
+    a.adt = c->mg_adt;
+    a.out0 = c->w2;
+    JF_RET(dg_apply(c, DG_JV, a, s));
+    k_sub<double><<<nblk(c->N, 256), 256, 0, s>>>(r, c->w2, d, c->N); jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+template <>
+int dg_defect<float>(jfnk_ctx *c, const float *r, const float *z, float *d, cudaStream_t s) {
+    DGArgs a = {};
+    a.U = c->mg_U;
+    a.Uf = c->Usf;
+    a.yf = z;
+    a.adt = c->mg_adt;
+    a.out0 = d;
+    JF_RET(dg_apply(c, DG_TLJV, a, s));
+    k_sub<float><<<nblk(c->N, 256), 256, 0, s>>>(r, d, d, c->N); jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+template <class S>
+int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
+    // restore the level double-buffer order at the end so that every
+    // application issues the same launches on the same pointers
+    void *sx[JF_MAXLEV], *sx2[JF_MAXLEV];
+    for (int l = 0; l < c->nlev; ++l) {
+        sx[l] = c->lev[l].x;
+        sx2[l] = c->lev[l].x2;
+    }
+    S *z = (S *)c->pz, *z2 = (S *)c->pz2;
+    bool zero = true;
+    for (int i = 0; i < c->dg_pre; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+    const S *d = r;
+    if (!zero) {
+        JF_RET(dg_defect<S>(c, r, z, (S *)c->pd, s));
+        d = (const S *)c->pd;
+    }
+    JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s));
+    JF_RET(mg_cycle_t<S>(c, 0, true, s));
+    JF_RET(to_dg<S, S>(c, (const S *)c->lev[0].x, z, zero ? 0 : 1, s));
+    zero = false;
+    for (int i = 0; i < c->dg_post; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+    JF_CK(cudaMemcpyAsync(zout, z, c->N * sizeof(S), cudaMemcpyDeviceToDevice, s));
+    for (int l = 0; l < c->nlev; ++l) {
+        c->lev[l].x = sx[l];
+        c->lev[l].x2 = sx2[l];
+    }
+    return JFNK_OK;
+}
+
+}  // namespace
+
+// ---- entry points used by the API and the solver ---------------------------
+int fv_setup_background(jfnk_ctx *c) {
+    for (int l = 0; l < c->nlev; ++l) {
+        FVK K = make_fvk(c, l);
+        const int n = 2 * c->lev[l].NZ + 1;
+        k_bg_fv<<<(n + 127) / 128, 128>>>(K, c->lev[l].hbx, c->lev[l].hbxw, c->lev[l].hbz); jf_launched();
+        JF_CK(cudaGetLastError());
+    }
+    JF_CK(cudaDeviceSynchronize());
+    return JFNK_OK;
+}
+
+int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s) {
+    c->mg_adt = adt;
+    c->mg_U = U;
+    k_dg_dtau<<<nblk(c->n_el), 128, 0, s>>>(U, c->ubv, c->grid.nx, c->grid.nz, c->np1, c->pc, c->powtab,
+                                             1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt, c->opts.sigma_dg,
+                                             c->dtau_dg, c->dtau_dgf); jf_launched();
+    JF_CK(cudaGetLastError());
+    if (c->prec == 64) {
+        JF_RET(to_fv<double, double>(c, U, (double *)c->lev[0].u, s));
+    } else {
+        JF_RET(to_fv<double, float>(c, U, (float *)c->lev[0].u, s));
+        JF_RET(blas_copy_d2f(U, c->Usf, c->N, s));
+    }
+    for (int l = 0; l < c->nlev; ++l) {
+        FVLev &L = c->lev[l];
+        FVK K = make_fvk(c, l);
+        const size_t n1 = (size_t)L.NX * L.NZ;
+        if (l > 0) {
+            FVLev &F = c->lev[l - 1];
+            if (c->prec == 64)
+                k_restrict<double><<<nblk(L.n, 256), 256, 0, s>>>((const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
+            else
+                k_restrict<float><<<nblk(L.n, 256), 256, 0, s>>>((const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u);
+            jf_launched();
+        }
+        if (c->prec == 64) {
+            JF_RET(fv_op64(c, l, FV_RES, (const double *)L.u, nullptr, nullptr, (double *)L.fu, s));
+            k_fv_dtau<double><<<nblk(n1), 128, 0, s>>>(K, (const double *)L.u, adt, c->opts.sigma_fv, (double *)L.dtau); jf_launched();
+        } else {
+            k_fv_dtau<float><<<nblk(n1), 128, 0, s>>>(K, (const float *)L.u, adt, c->opts.sigma_fv, (float *)L.dtau); jf_launched();
+        }
+        JF_CK(cudaGetLastError());
+    }
+    return JFNK_OK;
+}
+
+int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s) {
+    if (c->prec == 64) return apply_t<double>(c, r, (double *)z, s);
+    // FP32 preconditioner: r enters in FP32
+    JF_RET(blas_copy_d2f(r, (float *)c->pr, c->N, s));
+    return apply_t<float>(c, (const float *)c->pr, (float *)z, s);
+}
+
+int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s) {
+    return fv_op64(c, l, FV_RES, u, nullptr, nullptr, f, s);
+}
+
+int transfer_to_fv64(jfnk_ctx *c, const double *u, double *v, cudaStream_t s) {
+    return to_fv<double, double>(c, u, v, s);
+}
+
+int transfer_to_dg64(jfnk_ctx *c, const double *v, double *u, int accumulate, cudaStream_t s) {
+    return to_dg<double, double>(c, v, u, accumulate, s);
+}

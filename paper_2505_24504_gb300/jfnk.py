@@ -1,0 +1,210 @@
+"""ctypes binding of include/jfnk.h.  Argument marshalling only: every step of
+the path runs in libjfnk.so.  Device arrays are torch CUDA tensors (float64,
+contiguous); the stream is torch's current stream unless one is given."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "libjfnk.so")
+
+
+class JfnkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib().jfnk_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("x0", C.c_double), ("x1", C.c_double),
+                ("z0", C.c_double), ("z1", C.c_double), ("periodic_x", C.c_int)]
+
+
+class Physics(C.Structure):
+    _fields_ = [("cp", C.c_double), ("cv", C.c_double), ("g", C.c_double), ("p0", C.c_double),
+                ("theta0", C.c_double), ("mu", C.c_double), ("background", C.c_int),
+                ("ubg", C.c_double), ("wbg", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("newton_tol", C.c_double), ("newton_max", C.c_int), ("gmres_restart", C.c_int),
+                ("gmres_max", C.c_int), ("ew_gamma", C.c_double), ("ew_alpha", C.c_double),
+                ("ew_eta0", C.c_double), ("ew_eta_max", C.c_double), ("mg_key", C.c_char * 16),
+                ("fv_levels", C.c_int), ("massfix", C.c_int), ("precond_prec", C.c_int),
+                ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
+                ("use_graphs", C.c_int)]
+
+    @classmethod
+    def defaults(cls, **kw):
+        o = cls()
+        _lib().jfnk_default_opts(C.byref(o))
+        for k, v in kw.items():
+            if k == "mg_key":
+                v = v.encode() if isinstance(v, str) else v
+            setattr(o, k, v)
+        return o
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("stages", C.c_int), ("newton_its", C.c_int), ("gmres_its", C.c_int),
+                ("dg_calls", C.c_int), ("fv_calls", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        p = lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+        L = C.CDLL(p)
+        P, D, I, S = C.c_void_p, C.c_double, C.c_int, C.c_size_t
+        sig = {
+            "jfnk_default_opts": (None, [P]),
+            "jfnk_create": (I, [P, I, P, P, C.POINTER(C.c_void_p)]),
+            "jfnk_destroy": (None, [P]),
+            "jfnk_num_unknowns": (S, [P]),
+            "jfnk_workspace_bytes": (S, [P, I, P]),
+            "jfnk_node_coords": (I, [P, P, P]),
+            "jfnk_init_state": (I, [P, P, P, P]),
+            "dg_residual": (I, [P, P, P, P]),
+            "jv_product": (I, [P, P, P, P, D, D, P, P]),
+            "mg_precondition": (I, [P, P, D, P, P, P]),
+            "implicit_step": (I, [P, P, D, I, P, P]),
+            "jfnk_fv_levels": (I, [P]),
+            "jfnk_fv_level_size": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
+            "jfnk_transfer_to_fv": (I, [P, P, P, P]),
+            "jfnk_transfer_to_dg": (I, [P, P, P, P]),
+            "jfnk_fv_residual": (I, [P, I, P, P, P]),
+            "jfnk_eos_pressure": (I, [P, P, S, P, P]),
+            "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
+            "jfnk_launch_count": (C.c_ulonglong, []),
+            "jfnk_strerror": (C.c_char_p, [I]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+lib = _lib
+
+
+def launch_count() -> int:
+    return int(_lib().jfnk_launch_count())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise JfnkError(rc, where)
+
+
+class Context:
+    """One grid / order / model; owns the library context."""
+
+    def __init__(self, grid: Grid, k: int, phys: Physics, opts: Opts | None = None):
+        h = C.c_void_p()
+        _check(_lib().jfnk_create(C.byref(grid), k, C.byref(phys), C.byref(opts) if opts else None,
+                                  C.byref(h)), "jfnk_create")
+        self.h = h
+        self.grid, self.k, self.phys, self.opts = grid, k, phys, opts
+        self.N = _lib().jfnk_num_unknowns(h)
+        self.shape = (4, grid.nz, grid.nx, k + 1, k + 1)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().jfnk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def workspace_bytes(grid: Grid, k: int, opts: Opts | None = None) -> int:
+        return _lib().jfnk_workspace_bytes(C.byref(grid), k, C.byref(opts) if opts else None)
+
+    def node_coords(self):
+        import numpy as np
+        n = self.N // 4
+        x = np.empty(n)
+        z = np.empty(n)
+        _check(_lib().jfnk_node_coords(self.h, x.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p)),
+               "jfnk_node_coords")
+        return x, z
+
+    def jfnk_init_state(self, theta_pert, U, stream=None):
+        _check(_lib().jfnk_init_state(self.h, _ptr(theta_pert), _ptr(U), _stream(stream)), "jfnk_init_state")
+
+    def dg_residual(self, U, f, stream=None):
+        _check(_lib().dg_residual(self.h, _ptr(U), _ptr(f), _stream(stream)), "dg_residual")
+
+    def jv_product(self, U, fU, y, alpha_dt, eps, Jy, stream=None):
+        _check(_lib().jv_product(self.h, _ptr(U), _ptr(fU), _ptr(y), float(alpha_dt), float(eps), _ptr(Jy),
+                                 _stream(stream)), "jv_product")
+
+    def mg_precondition(self, U, alpha_dt, r, z, stream=None):
+        _check(_lib().mg_precondition(self.h, _ptr(U), float(alpha_dt), _ptr(r), _ptr(z), _stream(stream)),
+               "mg_precondition")
+
+    def implicit_step(self, U, dt, scheme=1, stream=None, raise_on_error=True) -> Stats:
+        st = Stats()
+        rc = _lib().implicit_step(self.h, _ptr(U), float(dt), int(scheme), C.byref(st), _stream(stream))
+        if raise_on_error:
+            _check(rc, "implicit_step")
+        return st
+
+    def eos_pressure(self, E, p, stream=None):
+        _check(_lib().jfnk_eos_pressure(self.h, _ptr(E), E.numel(), _ptr(p), _stream(stream)),
+               "jfnk_eos_pressure")
+
+    def time_operator(self, which, U, y, reps, stream=None):
+        ms = (C.c_double * 2)()
+        _check(_lib().jfnk_time_operator(self.h, int(which), _ptr(U), _ptr(y), int(reps), ms, _stream(stream)),
+               "jfnk_time_operator")
+        return ms[0], ms[1]
+
+    def fv_levels(self):
+        n = _lib().jfnk_fv_levels(self.h)
+        out = []
+        for l in range(n):
+            X, Z = C.c_int(), C.c_int()
+            _check(_lib().jfnk_fv_level_size(self.h, l, C.byref(X), C.byref(Z)), "jfnk_fv_level_size")
+            out.append((X.value, Z.value))
+        return out
+
+    def transfer_to_fv(self, u, v, stream=None):
+        _check(_lib().jfnk_transfer_to_fv(self.h, _ptr(u), _ptr(v), _stream(stream)), "jfnk_transfer_to_fv")
+
+    def transfer_to_dg(self, v, u, stream=None):
+        _check(_lib().jfnk_transfer_to_dg(self.h, _ptr(v), _ptr(u), _stream(stream)), "jfnk_transfer_to_dg")
+
+    def fv_residual(self, level, u, f, stream=None):
+        _check(_lib().jfnk_fv_residual(self.h, int(level), _ptr(u), _ptr(f), _stream(stream)),
+               "jfnk_fv_residual")
