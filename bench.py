@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=None)
     p.add_argument("--form", default="both", choices=["both", "fp32"],
                    help="fp32: time only the FP32-preconditioner steps (for profiler runs)")
+    p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
+                   help="only run REPS FP64 FD products (face + volume kernels) of the workload "
+                        "and print their CUDA-event times (small profiler captures)")
     return p.parse_args()
 
 
@@ -249,6 +252,13 @@ def main():
     torch.cuda.set_device(local)
     w = WORKLOAD
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    if args.profile_dg:
+        c64 = make_context(w, 64)
+        U0 = initial_state(c64, w)
+        y = torch.randn(c64.N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+        fm, vm = c64.time_operator(1, U0, y, args.profile_dg)
+        print(json.dumps({"profile": "FP64 FD product", "face_ms": fm, "volume_ms": vm, "reps": args.profile_dg}))
+        return
 
     # ---- the product form: FP32 preconditioner --------------------------------
     ctx = make_context(w, 32)

@@ -82,7 +82,9 @@ typedef struct {
  *               subtraction and GMRES stay FP64 in every mode.
  *  sigma_fv, sigma_dg  pseudo-time CFL factors of the smoothers (Sec. 3.5).
  *  c_ip         interior-penalty constant of the viscous flux.
- *  use_graphs   1: capture each preconditioner application in a CUDA graph. */
+ *  use_graphs   1 (default): capture one preconditioner application in a CUDA
+ *               graph on first use (and again when alpha_dt changes) and replay
+ *               it; 0: launch the kernels one by one.  Same results either way. */
 typedef struct {
     double newton_tol;
     int newton_max;

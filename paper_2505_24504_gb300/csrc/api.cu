@@ -146,10 +146,10 @@ size_t workspace(const jfnk_grid *g, int k, const jfnk_opts *o, const jfnk_physi
     const bool visc = ph ? ph->mu != 0.0 : true;
     b += 8 * (4 + (visc ? 6 : 0)) * (fx + fz);
     if (prec != 64) b += 4 * (4 + (visc ? 6 : 0)) * (fx + fz);
-    b += 8 * N * 8;                        // DG work vectors
+    b += 8 * N * 9;                        // DG work vectors
     b += 8 * N * (size_t)(m + 1);          // V
     b += sS * N * (size_t)m;               // Z
-    b += sS * N * 4;                       // pz, pz2, pd, pr
+    b += sS * N * 6;                       // pz, pz2, pd, pr, pin, pout
     b += 8 * (size_t)g->nx * g->nz;        // dtau_dg
     int NX[JF_MAXLEV], NZ[JF_MAXLEV], fac[JF_MAXLEV];
     const int nl = hierarchy(g->nx, g->nz, k, o->fv_levels < 1 ? 1 : o->fv_levels, NX, NZ, fac);
@@ -158,7 +158,7 @@ size_t workspace(const jfnk_grid *g, int k, const jfnk_opts *o, const jfnk_physi
         b += 8 * (4 * (size_t)NZ[l] * 4 + 4);
         b += sS * n * 6 + sS * n / 4;
     }
-    b += 8 * 1024 * 32 + 8 * 256;
+    b += 8 * 4096 * 32 + 8 * 256;
     if (nlev_out) *nlev_out = nl;
     return b;
 }
@@ -184,7 +184,7 @@ void jfnk_default_opts(jfnk_opts *o) {
     o->sigma_fv = 1.0;
     o->sigma_dg = 1.0;
     o->c_ip = 2.0;
-    o->use_graphs = 0;
+    o->use_graphs = 1;
 }
 
 const char *jfnk_strerror(int code) {
@@ -211,6 +211,7 @@ size_t jfnk_workspace_bytes(const jfnk_grid *g, int k, const jfnk_opts *opts) {
 void jfnk_destroy(jfnk_ctx *c) {
     if (!c) return;
     if (c->mg_graph_valid) cudaGraphExecDestroy(c->mg_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     Allocs *a = allocs_of(c);
     if (a) {
         for (void *p : a->dev) cudaFree(p);
@@ -354,6 +355,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     A_(c->Usave, 8 * N);
     A_(c->G, 8 * N);
     A_(c->dU, 8 * N);
+    A_(c->Ulin, 8 * N);
     const int m = o.gmres_restart;
     const size_t sS = c->prec == 64 ? 8 : 4;
     A_(c->V, 8 * N * (size_t)(m + 1));
@@ -362,6 +364,8 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     A_(c->pz2, sS * N);
     A_(c->pd, sS * N);
     A_(c->pr, sS * N);
+    A_(c->pin, sS * N);
+    A_(c->pout, sS * N);
     A_(c->dtau_dg, 8 * (size_t)c->n_el);
     if (c->prec != 64) {
         A_(c->dtau_dgf, 4 * (size_t)c->n_el);
@@ -431,7 +435,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
             return JFNK_ECUDA;
         }
     }
-    c->nb_red = 1024;
+    c->nb_red = 4096;
     A_(c->partial, 8 * (size_t)c->nb_red * 32);
     A_(c->scal, 8 * (size_t)S_COUNT);
     {

@@ -156,7 +156,7 @@ inline unsigned grid_for(size_t n) {
 }
 
 inline int nblocks_red(jfnk_ctx *c, size_t n) {
-    size_t g = (n + (size_t)RB * 4 - 1) / ((size_t)RB * 4);
+    size_t g = (n + (size_t)RB - 1) / (size_t)RB;
     if (g > (size_t)c->nb_red) g = c->nb_red;
     if (g < 1) g = 1;
     return (int)g;

@@ -279,21 +279,30 @@ __global__ void __launch_bounds__(128) k_volume(DGK K, Loader<T, IN> ld0, DGArgs
     __shared__ PowTab spt;
     __shared__ O sg[2][EPB][4][NP];
     __shared__ T su[VISC ? EPB : 1][4][NP];
-    __shared__ double sDw[NP1][NP1];
+    // weak-form derivative and lift tables with the 2/h factors folded in:
+    // sDx = (2/hx) Dw, sDz = (2/hz) Dw; sl[0..3] x-lifts, sl[4..7] z-lifts
+    __shared__ O sDx[NP1][NP1], sDz[NP1][NP1];
     __shared__ double sDn[NP1][NP1];
-    __shared__ double sl[4][NP1];   // lmw, lpw, dlmw, dlpw
+    __shared__ O sl[8][NP1];
     load_powtab(&spt, K.pt);
     Loader<T, IN> ld = ld0;
     ld.prepare();
     if (threadIdx.x < NP) {
-        sDw[threadIdx.x / NP1][threadIdx.x % NP1] = K.tab.Dw[threadIdx.x / NP1][threadIdx.x % NP1];
-        sDn[threadIdx.x / NP1][threadIdx.x % NP1] = K.tab.Dn[threadIdx.x / NP1][threadIdx.x % NP1];
+        const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
+        sDx[r][q] = (O)(K.two_hx * K.tab.Dw[r][q]);
+        sDz[r][q] = (O)(K.two_hz * K.tab.Dw[r][q]);
+        sDn[r][q] = K.tab.Dn[r][q];
     }
     if (threadIdx.x < NP1) {
-        sl[0][threadIdx.x] = K.tab.lmw[threadIdx.x];
-        sl[1][threadIdx.x] = K.tab.lpw[threadIdx.x];
-        sl[2][threadIdx.x] = K.tab.dlmw[threadIdx.x];
-        sl[3][threadIdx.x] = K.tab.dlpw[threadIdx.x];
+        const int q = threadIdx.x;
+        sl[0][q] = (O)(K.two_hx * K.tab.lmw[q]);
+        sl[1][q] = (O)(K.two_hx * K.tab.lpw[q]);
+        sl[2][q] = (O)(K.two_hx * K.two_hx * K.tab.dlmw[q]);
+        sl[3][q] = (O)(K.two_hx * K.two_hx * K.tab.dlpw[q]);
+        sl[4][q] = (O)(K.two_hz * K.tab.lmw[q]);
+        sl[5][q] = (O)(K.two_hz * K.tab.lpw[q]);
+        sl[6][q] = (O)(K.two_hz * K.two_hz * K.tab.dlmw[q]);
+        sl[7][q] = (O)(K.two_hz * K.two_hz * K.tab.dlpw[q]);
     }
     const int le = threadIdx.x / NP;
     const int node = threadIdx.x % NP;
@@ -358,44 +367,45 @@ __global__ void __launch_bounds__(128) k_volume(DGK K, Loader<T, IN> ld0, DGArgs
     }
     __syncthreads();
     if (!active) return;
-    const O thx = (O)K.two_hx, thz = (O)K.two_hz;
     const size_t fsx = (size_t)nz * (nx + 1) * NP1, fsz = (size_t)(nz + 1) * nx * NP1;
     const size_t iL = ((size_t)ez * (nx + 1) + ex) * NP1 + b, iR = iL + NP1;
     const size_t iB = ((size_t)ez * nx + ex) * NP1 + a, iT = iB + (size_t)nx * NP1;
-    const O lmwa = (O)sl[0][a], lpwa = (O)sl[1][a];
-    const O lmwb = (O)sl[0][b], lpwb = (O)sl[1][b];
+    const O lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
+    const O lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
     const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
+    const double ceps = eps != 0.0 ? A.adt / eps : 0.0;   // adt / eps once per thread
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        O ax = 0, az = 0;
+        O f = 0;
 #pragma unroll
         for (int q = 0; q < NP1; ++q) {
-            ax = fma((O)sDw[a][q], sg[0][le][v][b * NP1 + q], ax);
-            az = fma((O)sDw[b][q], sg[1][le][v][q * NP1 + a], az);
+            f = fma(sDx[a][q], sg[0][le][v][b * NP1 + q], f);
+            f = fma(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
         }
-        O f = thx * ax + thz * az;
-        if (v == 2) f = f - (O)K.g * (O)outv(Up[0]);
-        f = f + thx * (lmwa * phix[v * fsx + iL] - lpwa * phix[v * fsx + iR]) +
-            thz * (lmwb * phiz[v * fsz + iB] - lpwb * phiz[v * fsz + iT]);
+        if (v == 2) f = fma(-(O)K.g, (O)outv(Up[0]), f);
+        f = fma(lmxa, phix[v * fsx + iL], f);
+        f = fma(-lpxa, phix[v * fsx + iR], f);
+        f = fma(lmzb, phiz[v * fsz + iB], f);
+        f = fma(-lpzb, phiz[v * fsz + iT], f);
         if (VISC && v > 0) {
             const int c = v - 1;
-            f = f + thx * thx * ((O)sl[2][a] * symx[(size_t)(3 + c) * fsx + iL] +
-                                 (O)sl[3][a] * symx[(size_t)c * fsx + iR]) +
-                thz * thz * ((O)sl[2][b] * symz[(size_t)(3 + c) * fsz + iB] +
-                             (O)sl[3][b] * symz[(size_t)c * fsz + iT]);
+            f = fma(dlmxa, symx[(size_t)(3 + c) * fsx + iL], f);
+            f = fma(dlpxa, symx[(size_t)c * fsx + iR], f);
+            f = fma(dlmzb, symz[(size_t)(3 + c) * fsz + iB], f);
+            f = fma(dlpzb, symz[(size_t)c * fsz + iT], f);
         }
         const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
         if (MODE == DG_RES) {
             ((double *)A.out0)[gi] = (double)f;
         } else if (MODE == DG_JV) {
             const double y = A.y[gi];
-            ((double *)A.out0)[gi] = (eps == 0.0) ? y : y - A.adt * ((double)f - A.fU[gi]) / eps;
+            ((double *)A.out0)[gi] = (eps == 0.0) ? y : fma(-ceps, (double)f - A.fU[gi], y);
         } else if (MODE == DG_G) {
             A.out1[gi] = (double)f;
             ((double *)A.out0)[gi] = A.U[gi] - A.adt * (double)f - A.Ubs[gi];
         } else if (MODE == DG_SMOOTH64) {
             const double z = A.y[gi];
-            const double Jz = (eps == 0.0) ? z : z - A.adt * ((double)f - A.fU[gi]) / eps;
+            const double Jz = (eps == 0.0) ? z : fma(-ceps, (double)f - A.fU[gi], z);
             ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
         } else if (MODE == DG_TLJV) {
             const float z = A.yf[gi];

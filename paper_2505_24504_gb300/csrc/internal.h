@@ -83,14 +83,19 @@ struct jfnk_ctx {
     double *h_pinned;    // host pinned scratch for Hessenberg columns
     // linearisation of the preconditioner (set by mg_linearize)
     double mg_adt;
-    const double *mg_U;
+    const double *mg_U;  // = Ulin, the context's copy of the linearisation state
+    double *Ulin;
     // counters of the current call
     long long dg_calls, fv_calls;
-    // graph of one preconditioner application
+    // graph of one preconditioner application (captured on cap_stream, replayed
+    // on the caller's stream); valid for one linearisation adt
     cudaGraphExec_t mg_graph;
-    const void *mg_graph_r;
-    void *mg_graph_z;
+    cudaStream_t cap_stream;
     int mg_graph_valid;
+    double mg_graph_adt;
+    unsigned long long graph_launches;   // kernels in the graph
+    long long graph_dg_calls, graph_fv_calls;
+    void *pin, *pout;                    // fixed input / output of the graph
     size_t alloc_bytes;
     void *allocs;        // list of this context's allocations (api.cu)
     // optional per-launch timing of the DG kernels (jfnk_time_operator)

@@ -41,26 +41,53 @@ __device__ __forceinline__ void load_pt(PowTab *s, const PowTab *g) {
     for (int i = threadIdx.x; i < (int)(sizeof(PowTab) / sizeof(double)); i += blockDim.x) dst[i] = src[i];
 }
 
-// level state loaders: IN 0 u; IN 1 u + eps x (FP64, eps on device); IN 2 TL32 (u, x) in FP32
+// Level state loaders, addressed by (variable, cell, I, J):
+// IN 0 u; IN 1 u + eps x (FP64, eps on the device); IN 2 TL32 (u, x);
+// IN 3 TL32 (u, x - P v): the coarse correction folded into the direction.
 template <class T, int IN> struct FLoad;
 template <> struct FLoad<D64, 0> {
     const double *u;
+    size_t n1;
     JF_D void prepare() {}
     JF_D double step() const { return 0.0; }
-    JF_D D64 operator()(size_t i) const { return D64{u[i]}; }
+    JF_D double dir(int, size_t, int, int) const { return 0.0; }
+    JF_D D64 operator()(int v, size_t c, int, int) const { return D64{u[v * n1 + c]}; }
 };
 template <> struct FLoad<D64, 1> {
     const double *u, *x, *epsp;
+    size_t n1;
     double eps;
     JF_D void prepare() { eps = *epsp; }
     JF_D double step() const { return eps; }
-    JF_D D64 operator()(size_t i) const { return D64{__fma_rn(eps, x[i], u[i])}; }
+    JF_D double dir(int v, size_t c, int, int) const { return x[v * n1 + c]; }
+    JF_D D64 operator()(int v, size_t c, int, int) const {
+        const size_t i = v * n1 + c;
+        return D64{__fma_rn(eps, x[i], u[i])};
+    }
 };
 template <> struct FLoad<TL32, 2> {
     const float *u, *x;
+    size_t n1;
     JF_D void prepare() {}
     JF_D double step() const { return 0.0; }
-    JF_D TL32 operator()(size_t i) const { return TL32{u[i], x[i]}; }
+    JF_D float dir(int v, size_t c, int, int) const { return x[v * n1 + c]; }
+    JF_D TL32 operator()(int v, size_t c, int, int) const {
+        const size_t i = v * n1 + c;
+        return TL32{u[i], x[i]};
+    }
+};
+template <> struct FLoad<TL32, 3> {
+    const float *u, *x, *vc;
+    size_t n1, nc1;
+    int fac, NXc, zero;
+    JF_D void prepare() {}
+    JF_D double step() const { return 0.0; }
+    JF_D float dir(int v, size_t c, int I, int J) const {
+        const int Ic = fac == 2 ? (I >> 1) : I / fac, Jc = fac == 2 ? (J >> 1) : J / fac;
+        const float pv = vc[v * nc1 + (size_t)Jc * NXc + Ic];
+        return zero ? -pv : x[v * n1 + c] - pv;
+    }
+    JF_D TL32 operator()(int v, size_t c, int I, int J) const { return TL32{u[v * n1 + c], dir(v, c, I, J)}; }
 };
 
 enum { FV_RES = 0, FV_SMOOTH = 1, FV_DEFECT = 2 };
@@ -118,22 +145,22 @@ __global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     const bool sub = (IN != 2);
     T U[4], Un[4][4];   // own state and the W, E, S, N neighbours
     int nb[4] = {-1, -1, -1, -1};
+    int nI[4] = {I - 1, I + 1, I, I}, nJ[4] = {Jz, Jz, Jz - 1, Jz + 1};
     if (I > 0) nb[0] = Jz * NX + I - 1;
-    else if (K.periodic) nb[0] = Jz * NX + NX - 1;
+    else if (K.periodic) { nb[0] = Jz * NX + NX - 1; nI[0] = NX - 1; }
     if (I < NX - 1) nb[1] = Jz * NX + I + 1;
-    else if (K.periodic) nb[1] = Jz * NX;
+    else if (K.periodic) { nb[1] = Jz * NX; nI[1] = 0; }
     if (Jz > 0) nb[2] = (Jz - 1) * NX + I;
     if (Jz < NZ - 1) nb[3] = (Jz + 1) * NX + I;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        U[v] = ld((size_t)v * n1 + c) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
+        U[v] = ld(v, c, I, Jz) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int Jq = (q == 2) ? Jz - 1 : (q == 3 ? Jz + 1 : Jz);
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-            Un[q][v] = nb[q] >= 0 ? ld((size_t)v * n1 + nb[q]) + bgs<T>(K.ub, K.ubf, v * NZ + Jq) : U[v];
+            Un[q][v] = nb[q] >= 0 ? ld(v, (size_t)nb[q], nI[q], nJ[q]) + bgs<T>(K.ub, K.ubf, v * NZ + nJ[q]) : U[v];
     }
     T HW[4], HE[4], HS[4], HN[4];
     face_flux<T, 0>(Un[0], U, nb[0] < 0, false, nb[0] < 0 ? K.hbxw : K.hbx, NZ, Jz, sub, K, &spt, HW);
@@ -144,8 +171,8 @@ __global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     const T iHx = mk(K.iHx, T{}), iHz = mk(K.iHz, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v) f[v] = -((HE[v] - HW[v]) * iHx + (HN[v] - HS[v]) * iHz);
-    const T up0 = ld(c);
-    f[2] = f[2] - mk(K.g, T{}) * up0;
+    const T up0 = ld(0, c, I, Jz);
+    f[2] = f[2] - mk(K.g, T{}) * up0;   // -g rho' (tangent: -g x_rho)
     if (VISC) {
         T VW[4], VE[4], VS[4], VN[4];
         const T zero = mk(0.0, T{});
@@ -163,7 +190,7 @@ __global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typen
         if (MODE == FV_RES) {
             out[gi] = (S)oval(f[v]);
         } else {
-            const S x = xin[gi];
+            const S x = (S)ld.dir(v, c, I, Jz);
             S gx;
             if (IN == 1)
                 gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)oval(f[v]) - fu[gi]) / eps);
@@ -258,7 +285,7 @@ __device__ __forceinline__ void load_ttab(const TK &K, R sV[NP1][NP1], R sVi[NP1
 // T^mf: DG (Si) -> FV (So), arithmetic in the storage precision.  Block: EPB
 // elements x NP subcells.
 template <class Si, class So, int NP1>
-__global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix) {
+__global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix, So *x0, const So *dtau0) {
     typedef typename RealOf<Si, So>::type R;
     constexpr int NP = NP1 * NP1;
     constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
@@ -313,7 +340,11 @@ __global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int mas
     const int ez = e / K.nx, ex = e % K.nx;
     const size_t I = (size_t)ex * NP1 + i, Jr = (size_t)ez * NP1 + j;
     const size_t n1 = (size_t)K.NX * K.NZ;
-    for (int q = 0; q < 4; ++q) v[q * n1 + Jr * K.NX + I] = (So)(Tu[q] - sc[le][q]);
+    for (int q = 0; q < 4; ++q) {
+        const So val = (So)(Tu[q] - sc[le][q]);
+        v[q * n1 + Jr * K.NX + I] = val;
+        if (x0) x0[q * n1 + Jr * K.NX + I] = dtau0[Jr * K.NX + I] * val;   // first step from zero
+    }
 }
 
 // T^-1_mf: FV (Si) -> DG (So); acc 0: store, 1: add
@@ -392,6 +423,26 @@ __global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
     for (int jj = 0; jj < fac; ++jj)
         for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
     cz[t] = acc / (S)(fac * fac);
+}
+
+// R plus the coarse level's first pseudo-time step from zero: b_c = R r and,
+// when x_c is given, x_c = dtau_c b_c
+template <class S>
+__global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc, const S *dtau_c) {
+    const int NXc = NXf / fac, NZc = NZf / fac;
+    const size_t nc = (size_t)NXc * NZc;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * nc) return;
+    const int q = (int)(t / nc);
+    const size_t c = t % nc;
+    const int I = (int)(c % NXc), J = (int)(c / NXc);
+    const S *fq = f + (size_t)q * NXf * NZf;
+    S acc = 0;
+    for (int jj = 0; jj < fac; ++jj)
+        for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
+    const S bv = acc / (S)(fac * fac);
+    bc[t] = bv;
+    if (xc) xc[t] = dtau_c[c] * bv;
 }
 
 // x = (zero ? 0 : x) - P v
@@ -508,16 +559,16 @@ TK make_tk(jfnk_ctx *c) {
 }
 
 template <class Si, class So>
-int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s) {
+int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s, So *x0 = nullptr, const So *dtau0 = nullptr) {
     TK K = make_tk(c);
     const int NP = c->np1 * c->np1;
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
-        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
-        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
-        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix); jf_launched(); break;
+        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
+        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
+        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
+        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -553,13 +604,13 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
     c->fv_calls++;
     const unsigned g = nblk(n1);
     if (mode == FV_RES) {
-        FLoad<D64, 0> ld{u};
+        FLoad<D64, 0> ld{u, n1};
         if (visc) { k_fv<D64, 0, FV_RES, true><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
         else { k_fv<D64, 0, FV_RES, false><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
     } else {
         double *epsp = c->scal + S_EPSFV + l;
         JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPS, s));
-        FLoad<D64, 1> ld{u, x, epsp, 0.0};
+        FLoad<D64, 1> ld{u, x, epsp, n1, 0.0};
         const double *dt = (const double *)L.dtau;
         const double *fu = (const double *)L.fu;
         const double adt = c->mg_adt;
@@ -582,7 +633,7 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     const bool visc = c->phys.mu != 0.0;
     c->fv_calls++;
     const unsigned g = nblk(n1);
-    FLoad<TL32, 2> ld{(const float *)L.u, x};
+    FLoad<TL32, 2> ld{(const float *)L.u, x, n1};
     const float *dt = (const float *)L.dtau;
     const double adt = c->mg_adt;
     if (mode == FV_SMOOTH) {
@@ -604,16 +655,53 @@ inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, cons
     return fv_op32(c, l, mode, (const float *)x, (const float *)b, (float *)out, s);
 }
 
+// first post-smoothing step with the coarse correction applied on the fly:
+// out = xc + dtau (b - g' xc), xc = (zero ? 0 : x) - P v   (FP32 tangent path)
+int fv_smooth_corrected32(jfnk_ctx *c, int l, bool zero, const float *b, float *out, cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    FVLev &C = c->lev[l + 1];
+    FVK K = make_fvk(c, l);
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    c->fv_calls++;
+    FLoad<TL32, 3> ld;
+    ld.u = (const float *)L.u;
+    ld.x = (const float *)L.x;
+    ld.vc = (const float *)C.x;
+    ld.fac = L.fac;
+    ld.NXc = C.NX;
+    ld.zero = zero ? 1 : 0;
+    ld.n1 = n1;
+    ld.nc1 = (size_t)C.NX * C.NZ;
+    const float *dt = (const float *)L.dtau;
+    if (c->phys.mu != 0.0) {
+        k_fv<TL32, 3, FV_SMOOTH, true><<<nblk(n1), 128, 0, s>>>(K, ld, nullptr, b, dt, nullptr, c->mg_adt, out);
+    } else {
+        k_fv<TL32, 3, FV_SMOOTH, false><<<nblk(n1), 128, 0, s>>>(K, ld, nullptr, b, dt, nullptr, c->mg_adt, out);
+    }
+    jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+// MG_l(x, b; u) of Sec. 3.4 on level l (0 = finest subgrid).  `zero`: x = 0 on
+// entry (products with x are skipped).  `first_done`: the caller already made
+// the first pre-smoothing step from zero (x = dtau b, fused into the transfer
+// or the restriction).
 template <class S>
-int mg_cycle_t(jfnk_ctx *c, int l, bool zero, cudaStream_t s) {
+int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     FVLev &L = c->lev[l];
     const size_t n1 = (size_t)L.NX * L.NZ;
-    const int pre = (l == 0) ? c->fine_pre : c->mid_pre;
-    const int post = (l == 0) ? c->fine_post : c->mid_post;
+    int pre = (l == 0) ? c->fine_pre : c->mid_pre;
+    int post = (l == 0) ? c->fine_post : c->mid_post;
+    if (first_done) {
+        pre -= 1;
+        zero = false;
+    }
     auto smooth = [&](int steps) -> int {
         for (int i = 0; i < steps; ++i) {
             if (zero) {
-                k_scale_dtau<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)L.b, (const S *)L.dtau, n1); jf_launched();
+                k_scale_dtau<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)L.b, (const S *)L.dtau, n1);
+                jf_launched();
                 zero = false;
             } else {
                 JF_RET(fv_smooth_or_defect(c, l, FV_SMOOTH, L.x, L.b, L.x2, s));
@@ -631,15 +719,29 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, cudaStream_t s) {
         if (zero) {
             k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
             jf_launched();
-        } else
+        } else {
             JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
-        k_restrict<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b); jf_launched();
-        bool vz = true;
-        for (int cyc = 0; cyc < c->cycles; ++cyc) {
-            JF_RET(mg_cycle_t<S>(c, l + 1, vz, s));
-            vz = false;
         }
-        k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0); jf_launched();
+        const bool fuse = c->mid_pre >= 1;
+        k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
+                                                       fuse ? (S *)C.x : nullptr, (const S *)C.dtau);
+        jf_launched();
+        bool vz = true, fd = fuse;
+        for (int cyc = 0; cyc < c->cycles; ++cyc) {
+            JF_RET(mg_cycle_t<S>(c, l + 1, vz, fd, s));
+            vz = false;
+            fd = false;
+        }
+        if (post >= 1 && c->prec != 64) {
+            JF_RET(fv_smooth_corrected32(c, l, zero, (const float *)L.b, (float *)L.x2, s));
+            void *t = L.x;
+            L.x = L.x2;
+            L.x2 = t;
+            --post;
+        } else {
+            k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
+            jf_launched();
+        }
         zero = false;
     }
     JF_RET(smooth(post));
@@ -752,8 +854,9 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
         JF_RET(dg_defect<S>(c, r, z, (S *)c->pd, s));
         d = (const S *)c->pd;
     }
-    JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s));
-    JF_RET(mg_cycle_t<S>(c, 0, true, s));
+    const bool fuse0 = c->fine_pre >= 1;
+    JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s, fuse0 ? (S *)c->lev[0].x : nullptr, (const S *)c->lev[0].dtau));
+    JF_RET(mg_cycle_t<S>(c, 0, true, fuse0, s));
     JF_RET(to_dg<S, S>(c, (const S *)c->lev[0].x, z, zero ? 0 : 1, s));
     zero = false;
     for (int i = 0; i < c->dg_post; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
@@ -779,7 +882,10 @@ int fv_setup_background(jfnk_ctx *c) {
     return JFNK_OK;
 }
 
-int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s) {
+int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
+    // every pointer the captured graph holds is context-owned
+    JF_CK(cudaMemcpyAsync(c->Ulin, Uin, 8 * c->N, cudaMemcpyDeviceToDevice, s));
+    const double *U = c->Ulin;
     c->mg_adt = adt;
     c->mg_U = U;
     k_dg_dtau<<<nblk(c->n_el), 128, 0, s>>>(U, c->ubv, c->grid.nx, c->grid.nz, c->np1, c->pc, c->powtab,
@@ -815,11 +921,65 @@ int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s) {
     return JFNK_OK;
 }
 
+namespace {
+int apply_body(jfnk_ctx *c, cudaStream_t s) {
+    if (c->prec == 64) return apply_t<double>(c, (const double *)c->pin, (double *)c->pout, s);
+    return apply_t<float>(c, (const float *)c->pin, (float *)c->pout, s);
+}
+
+// Capture one application into an executable graph.  Returns JFNK_OK with
+// mg_graph_valid = 0 when capture is not possible (the caller then launches
+// the kernels directly).
+int capture(jfnk_ctx *c) {
+    if (c->mg_graph_valid) {
+        cudaGraphExecDestroy(c->mg_graph);
+        c->mg_graph_valid = 0;
+    }
+    if (!c->cap_stream) JF_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const unsigned long long n0 = __atomic_load_n(&g_jf_launches, __ATOMIC_RELAXED);
+    const long long d0 = c->dg_calls, f0 = c->fv_calls;
+    JF_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = apply_body(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->graph_launches = __atomic_load_n(&g_jf_launches, __ATOMIC_RELAXED) - n0;
+    __atomic_fetch_sub(&g_jf_launches, c->graph_launches, __ATOMIC_RELAXED);   // captured, not launched
+    c->graph_dg_calls = c->dg_calls - d0;
+    c->graph_fv_calls = c->fv_calls - f0;
+    c->dg_calls = d0;
+    c->fv_calls = f0;
+    if (rc != JFNK_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != JFNK_OK ? rc : JFNK_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->mg_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return JFNK_ECUDA;
+    }
+    c->mg_graph_valid = 1;
+    c->mg_graph_adt = c->mg_adt;
+    return JFNK_OK;
+}
+}  // namespace
+
 int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s) {
-    if (c->prec == 64) return apply_t<double>(c, r, (double *)z, s);
-    // FP32 preconditioner: r enters in FP32
-    JF_RET(blas_copy_d2f(r, (float *)c->pr, c->N, s));
-    return apply_t<float>(c, (const float *)c->pr, (float *)z, s);
+    const size_t sS = c->prec == 64 ? 8 : 4;
+    if (c->prec == 64) JF_CK(cudaMemcpyAsync(c->pin, r, 8 * c->N, cudaMemcpyDeviceToDevice, s));
+    else JF_RET(blas_copy_d2f(r, (float *)c->pin, c->N, s));   // FP32 preconditioner: r enters in FP32
+    if (c->opts.use_graphs) {
+        if (!c->mg_graph_valid || c->mg_graph_adt != c->mg_adt) JF_RET(capture(c));
+        JF_CK(cudaGraphLaunch(c->mg_graph, s));
+        jf_launched((unsigned)c->graph_launches);
+        c->dg_calls += c->graph_dg_calls;
+        c->fv_calls += c->graph_fv_calls;
+    } else {
+        JF_RET(apply_body(c, s));
+    }
+    JF_CK(cudaMemcpyAsync(z, c->pout, sS * c->N, cudaMemcpyDeviceToDevice, s));
+    return JFNK_OK;
 }
 
 int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s) {

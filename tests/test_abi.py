@@ -42,6 +42,6 @@ def test_host_only_calls(libpath):
     g = P.Grid(20, 10, 0.0, 20000.0, 0.0, 10000.0, 0)
     b20 = P.Context.workspace_bytes(g, 2, o)
     g2 = P.Grid(40, 20, 0.0, 20000.0, 0.0, 10000.0, 0)
-    assert P.Context.workspace_bytes(g2, 2, o) > 3.5 * b20
+    assert P.Context.workspace_bytes(g2, 2, o) > 3.0 * b20   # 4x the unknowns, fixed scratch aside
     assert P.Context.workspace_bytes(P.Grid(0, 10, 0, 1, 0, 1, 0), 2, o) == 0
     assert P.Context.workspace_bytes(g, 5, o) == 0
