@@ -174,6 +174,12 @@ int mg_precondition(jfnk_ctx *ctx, const double *U_dev, double alpha_dt, const d
 int implicit_step(jfnk_ctx *ctx, double *U_dev, double dt, int scheme, jfnk_stats *stats,
                   void *stream);
 
+/* Euclidean norm |x|_2 of n doubles (device) written to *out_dev (device):
+ * the unweighted l2 norm of Sec. 3.1 (Newton stop test |G(U^k)| < TOL |G(U^0)|
+ * and eps = sqrt(eps_mach)/|y|).  Deterministic: per-block partial sums in the
+ * context's scratch, then one fixed-order final sum.  n = 0 gives 0. */
+int jfnk_norm2(jfnk_ctx *ctx, const double *x_dev, size_t n, double *out_dev, void *stream);
+
 /* ---- diagnostics (pieces of mg_precondition, for parity tests) -------- */
 
 /* Number of FV levels and the size of level l (0 = finest subgrid). */

@@ -543,6 +543,16 @@ int mg_precondition(jfnk_ctx *c, const double *U, double adt, const double *r, d
     return blas_copy_f2d((const float *)c->Z, z, c->N, s);
 }
 
+int jfnk_norm2(jfnk_ctx *c, const double *x, size_t n, double *out, void *stream) {
+    if (!c || !out || (n > 0 && !x)) return JFNK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        JF_CK(cudaMemsetAsync(out, 0, sizeof(double), s));
+        return JFNK_OK;
+    }
+    return red_dot(c, x, x, n, out, RED_SQRT, s);
+}
+
 int jfnk_eos_pressure(jfnk_ctx *c, const double *E, size_t n, double *p, void *stream) {
     if (!c || !E || !p) return JFNK_EINVAL;
     if (n == 0) return JFNK_OK;

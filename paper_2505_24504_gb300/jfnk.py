@@ -85,6 +85,7 @@ def _lib():
             "jfnk_transfer_to_dg": (I, [P, P, P, P]),
             "jfnk_fv_residual": (I, [P, I, P, P, P]),
             "jfnk_eos_pressure": (I, [P, P, S, P, P]),
+            "jfnk_norm2": (I, [P, P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
             "jfnk_strerror": (C.c_char_p, [I]),
@@ -179,6 +180,10 @@ class Context:
         if raise_on_error:
             _check(rc, "implicit_step")
         return st
+
+    def norm2(self, x, out, n=None, stream=None):
+        n = x.numel() if n is None else n
+        _check(_lib().jfnk_norm2(self.h, _ptr(x), n, _ptr(out), _stream(stream)), "jfnk_norm2")
 
     def eos_pressure(self, E, p, stream=None):
         _check(_lib().jfnk_eos_pressure(self.h, _ptr(E), E.numel(), _ptr(p), _stream(stream)),

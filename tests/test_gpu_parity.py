@@ -279,3 +279,14 @@ def test_graph_replay_bitwise_equals_direct_launches(prec):
             ctx.implicit_step(U, w.dt, scheme=1)
         out.append(to_cpu(U))
     assert np.array_equal(out[0], out[1])
+
+
+def test_norm2_entry_point():
+    w = synth.scaled(W1, 10, 5)
+    ctx = gpu_context(w)
+    for n, seed in ((0, 1), (1, 2), (777, 3), (ctx.N, 4), (3_000_001, 5)):
+        x = torch.from_numpy(synth.random_vector(max(n, 1), seed)).cuda()
+        out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        ctx.norm2(x, out, n=n)
+        ref = float(np.linalg.norm(x.cpu().numpy()[:n])) if n else 0.0
+        assert abs(out.item() - ref) <= 1e-14 * max(ref, 1.0)
