@@ -180,6 +180,25 @@ int implicit_step(jfnk_ctx *ctx, double *U_dev, double dt, int scheme, jfnk_stat
  * context's scratch, then one fixed-order final sum.  n = 0 gives 0. */
 int jfnk_norm2(jfnk_ctx *ctx, const double *x_dev, size_t n, double *out_dev, void *stream);
 
+/* The norm of jfnk_norm2 without a context and without allocating anything,
+ * for callers that must not allocate device memory: code running while a CUDA
+ * graph is being captured, allocator or memory-pool callbacks, and services
+ * with a device-memory budget fixed at start-up (these cannot create a
+ * context either, since jfnk_create allocates).  The paper has no counterpart.
+ * x: n doubles (device); *out_dev (device) receives |x|_2.
+ * Scratch: a fixed 4096-double device array inside the library (32 KiB on
+ * every GPU that loads it, held until the process exits), so
+ * n <= JFNK_NORM2_NOALLOC_MAX_N = 4096 * 8192 = 33,554,432; larger n returns
+ * JFNK_EINVAL before anything is launched.
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current): make that first call before
+ * capturing a stream.  Every call uses the same array, so calls that overlap on
+ * the GPU (on different streams, or from several host threads) race; order
+ * them on one stream.  Each call overwrites every partial it later reads, so
+ * nothing needs clearing between calls. */
+#define JFNK_NORM2_NOALLOC_MAX_N ((size_t)4096 * 8192)
+int jfnk_norm2_noalloc(const double *x_dev, size_t n, double *out_dev, void *stream);
+
 /* ---- diagnostics (pieces of mg_precondition, for parity tests) -------- */
 
 /* Number of FV levels and the size of level l (0 = finest subgrid). */

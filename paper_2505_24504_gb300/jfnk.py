@@ -86,6 +86,7 @@ def _lib():
             "jfnk_fv_residual": (I, [P, I, P, P, P]),
             "jfnk_eos_pressure": (I, [P, P, S, P, P]),
             "jfnk_norm2": (I, [P, P, S, P, P]),
+            "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
             "jfnk_strerror": (C.c_char_p, [I]),
@@ -99,6 +100,13 @@ def _lib():
 
 
 lib = _lib
+
+
+def norm2_noalloc(x, out, n=None, stream=None):
+    """|x|_2 into out[0] without a context or any device allocation (fixed
+    in-library scratch; see include/jfnk.h)."""
+    n = x.numel() if n is None else n
+    _check(_lib().jfnk_norm2_noalloc(_ptr(x), n, _ptr(out), _stream(stream)), "jfnk_norm2_noalloc")
 
 
 def launch_count() -> int:
