@@ -42,8 +42,9 @@ L2_FLUSH_BYTES = 512 << 20
 # volume kernel (per node) for Euler, k = 3; see DESIGN.md "roofline".  An FMA
 # counts 2 flops, add / mul 1; division and square root count the FP64
 # instructions of their IEEE-correct sequences; x^gamma the table power's.
-FLOPS_FACE_POINT = None   # filled from the committed ncu summary below
-FLOPS_NODE = None
+FLOPS_FACE_POINT = 298.0   # k_faces, FD product (profiles/dg_fp64_fd_product_w2.md)
+FLOPS_NODE = 185.0         # k_volume, FD product
+TRAFFIC_FACE = 13_271_296  # dram read + write bytes of one k_faces FD launch (ncu, cold L2)
 
 
 def parse():
@@ -56,6 +57,9 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=None)
     p.add_argument("--form", default="both", choices=["both", "fp32"],
                    help="fp32: time only the FP32-preconditioner steps (for profiler runs)")
+    p.add_argument("--ensemble", type=int, default=64, help="members of the batched ensemble (0: skip)")
+    p.add_argument("--ensemble-steps", type=int, default=2)
+    p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
                    help="only run REPS FP64 FD products (face + volume kernels) of the workload "
                         "and print their CUDA-event times (small profiler captures)")
@@ -156,6 +160,82 @@ def time_steps(ctx, U, w, steps, warmup, dist, flush):
     if dist:
         dist.barrier()
     return ms, stats
+
+
+def make_context_for(w, prec):
+    return make_context(w, prec)
+
+
+def run_ensemble(n, steps, warmup):
+    """64-member uneven ensemble (Q1..Q4, 40x20 .. 320x160), one batched SDIRK2 step
+    per timed iteration, FP32 preconditioner; returns a dict for the JSON line."""
+    import torch
+
+    import paper_2505_24504_gb300 as P
+    members = synth.ensemble(n)
+    ctxs = [make_context(m, 32) for m in members]
+    Us = [initial_state(c, m) for c, m in zip(ctxs, members)]
+    batch = P.Batch(ctxs, max_threads=16)
+    dts = [m.dt for m in members]
+    sch = [m.scheme for m in members]
+    for _ in range(warmup):
+        batch.jfnk_batch_step(Us, dts, sch)
+    torch.cuda.synchronize()
+    t = 0.0
+    its = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        status, stats = batch.jfnk_batch_step(Us, dts, sch, raise_on_error=False)
+        torch.cuda.synchronize()
+        t += time.perf_counter() - t0
+        its.append(sum(s.gmres_its for s in stats))
+    dof = sum(m.n_unknowns for m in members)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del Us
+    torch.cuda.empty_cache()
+    return {"members": n, "unknowns_total": dof, "ensemble_steps_per_s": steps / t,
+            "member_steps_per_s": n * steps / t, "dof_per_s": dof * steps / t,
+            "ms_per_ensemble_step": 1e3 * t / steps, "failed_members": sum(1 for x in status if x != 0),
+            "gmres_its_per_ensemble_step": sum(its) / len(its), "precond": "fp32",
+            "timing": "wall clock of jfnk_batch_step (host-driven members on 16 threads / streams)"}
+
+
+def run_serving(seconds, rate=200.0):
+    """Poisson arrivals of implicit-step requests on resident states: 16 ensemble
+    members (80 %) and 4 viscous density-current states (20 %), HBM budget of half
+    the total solver footprint (admission waits and evictions happen)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300.serve import Server, StateSpec
+    ens = synth.ensemble(16)
+    visc = [synth.DENSITY_CURRENT_Q2_256x32] * 4
+    specs = {}
+    for sid, m in enumerate(ens + visc):
+        c = make_context(m, 32)
+        specs[sid] = StateSpec(grid=c.grid, k=c.k, phys=c.phys, opts=c.opts, dt=m.dt, scheme=m.scheme,
+                               U=initial_state(c, m))
+        c.close()
+    total = sum(sp.footprint for sp in specs.values())
+    budget = max(total // 2, max(sp.footprint for sp in specs.values()))
+    arr = synth.poisson_arrivals(rate, seconds, seed=7)
+    rng = np.random.Generator(np.random.Philox(11))
+    reqs = []
+    for t in arr:
+        sid = int(rng.integers(0, 16)) if rng.random() < 0.8 else 16 + int(rng.integers(0, 4))
+        reqs.append((float(t), sid))
+    srv = Server(specs, hbm_budget=budget, workers=16)
+    rep = srv.run(reqs)
+    srv.close()
+    out = rep.summary()
+    out.update({"arrival_rate_per_s": rate, "horizon_s": seconds, "hbm_budget_bytes": budget,
+                "footprint_total_bytes": total, "states": len(specs)})
+    del specs
+    torch.cuda.empty_cache()
+    return out
 
 
 def max_over_ranks(x, dist):
@@ -311,12 +391,16 @@ def main():
     fm, vm = ctx64.time_operator(1, U0, y, 20)
     n1 = w.k + 1
     face_pts = (w.nz * (w.nx + 1) + (w.nz + 1) * w.nx) * n1
-    roof = None
-    if FLOPS_FACE_POINT:
-        ach = FLOPS_FACE_POINT * face_pts / (fm * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "kernel": "k_faces (FP64 FD product)", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "face_ms": fm, "volume_ms": vm}
+    nodes = w.n_el * n1 * n1
+    ach = FLOPS_FACE_POINT * face_pts / (fm * 1e-3) / 1e12
+    ach_v = FLOPS_NODE * nodes / (vm * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS
+    roof = {"bound": "alu", "kernel": "k_faces<D64> FP64 FD product (face points)", "achieved": ach,
+            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC_FACE,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "launch_ms": fm, "flop_per_launch": FLOPS_FACE_POINT * face_pts,
+            "volume_kernel": {"achieved": ach_v, "frac": ach_v / peak, "launch_ms": vm,
+                              "flop_per_launch": FLOPS_NODE * nodes}}
 
     # ---- the plain FP64 single-instance form ----------------------------------
     U64 = U0.clone()
@@ -345,6 +429,12 @@ def main():
                 "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "roofline": roof,
     }
+    ctx.close()
+    ctx64.close()
+    if args.ensemble > 0:
+        line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1)
+    if args.serve_seconds > 0:
+        line["serving"] = run_serving(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         per_step, desc, _ = oracle_sample(w, int(round(newton)), int(round(gmres)))

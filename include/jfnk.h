@@ -199,6 +199,25 @@ int jfnk_norm2(jfnk_ctx *ctx, const double *x_dev, size_t n, double *out_dev, vo
 #define JFNK_NORM2_NOALLOC_MAX_N ((size_t)4096 * 8192)
 int jfnk_norm2_noalloc(const double *x_dev, size_t n, double *out_dev, void *stream);
 
+/* ---- batched ensembles ------------------------------------------------ */
+
+/* A batch of n member contexts (any grids, orders, models and options; each
+ * context belongs to at most one batch at a time).  The batch owns one CUDA
+ * stream per member and a pool of min(max_threads, n) host threads
+ * (max_threads <= 0: min(n, 16)).  The contexts stay owned by the caller. */
+typedef struct jfnk_batch jfnk_batch;
+int jfnk_batch_create(jfnk_ctx *const *ctxs, int n, int max_threads, jfnk_batch **out);
+void jfnk_batch_destroy(jfnk_batch *batch);
+
+/* One implicit step of every member: U[i] (device, in/out) of member i with
+ * step dt[i] and scheme[i] (0 BE, 1 SDIRK2).  Members run concurrently on
+ * their own streams, largest first; each member's result is bit-identical to
+ * implicit_step on that member alone.  status[i] / stats[i] (may be NULL)
+ * receive each member's outcome; returns JFNK_OK or the first member error.
+ * Returns when every member has finished. */
+int jfnk_batch_step(jfnk_batch *batch, double *const *U_dev, const double *dt, const int *scheme,
+                    int *status, jfnk_stats *stats);
+
 /* ---- diagnostics (pieces of mg_precondition, for parity tests) -------- */
 
 /* Number of FV levels and the size of level l (0 = finest subgrid). */

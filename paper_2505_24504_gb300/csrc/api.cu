@@ -15,6 +15,7 @@ void jf_background(const jfnk_physics *ph, double z, double U[4], double dU[4]);
 double jf_insert_coef(const jfnk_physics *ph, double z);
 
 unsigned long long g_jf_launches = 0;
+thread_local unsigned long long t_jf_launches = 0;
 
 namespace {
 

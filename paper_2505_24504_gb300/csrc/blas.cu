@@ -65,7 +65,11 @@ __global__ void __launch_bounds__(RB) k_final(const double *part, int nb, double
 // indexed (registers), warp sums go through one shared-memory pass.
 template <int NV>
 __global__ void __launch_bounds__(RB) k_mdot_partial(const double *V, size_t ldv, const double *w, size_t n,
-                                                     double *part) {
+                                                     double *part, const double *flag) {
+    if (flag && *flag == 0.0) {   // pass not needed: contribute zeros
+        if (threadIdx.x < NV) part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
     double acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) acc[j] = 0.0;
@@ -100,7 +104,8 @@ __global__ void __launch_bounds__(RB) k_mfinal(const double *part, int nb, doubl
 
 // w += sign * sum_j h_j V_j
 __global__ void k_mupdate(const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
-                          double sign) {
+                          double sign, const double *flag) {
+    if (flag && *flag == 0.0) return;
     __shared__ double sh[MAXV];
     if (threadIdx.x < nv) sh[threadIdx.x] = sign * h[threadIdx.x];
     __syncthreads();
@@ -181,34 +186,35 @@ int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out,
 }
 
 template <int NV>
-void mdot_chunk(const double *V, size_t ldv, const double *w, size_t n, double *part, int nb, cudaStream_t s) {
-    k_mdot_partial<NV><<<nb, RB, 0, s>>>(V, ldv, w, n, part);
+void mdot_chunk(const double *V, size_t ldv, const double *w, size_t n, double *part, int nb, cudaStream_t s,
+                const double *flag) {
+    k_mdot_partial<NV><<<nb, RB, 0, s>>>(V, ldv, w, n, part, flag);
 }
 
 int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h,
-              cudaStream_t s) {
+              cudaStream_t s, const double *flag) {
     constexpr int CH = 16;   // basis vectors per pass over w
     for (int j0 = 0; j0 < nv; j0 += CH) {
         const int m = nv - j0 < CH ? nv - j0 : CH;
         const int nb = nblocks_red(c, n);
         const double *Vj = V + (size_t)j0 * ldv;
         switch (m) {
-            case 1: mdot_chunk<1>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 2: mdot_chunk<2>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 3: mdot_chunk<3>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 4: mdot_chunk<4>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 5: mdot_chunk<5>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 6: mdot_chunk<6>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 7: mdot_chunk<7>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 8: mdot_chunk<8>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 9: mdot_chunk<9>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 10: mdot_chunk<10>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 11: mdot_chunk<11>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 12: mdot_chunk<12>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 13: mdot_chunk<13>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 14: mdot_chunk<14>(Vj, ldv, w, n, c->partial, nb, s); break;
-            case 15: mdot_chunk<15>(Vj, ldv, w, n, c->partial, nb, s); break;
-            default: mdot_chunk<16>(Vj, ldv, w, n, c->partial, nb, s); break;
+            case 1: mdot_chunk<1>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 2: mdot_chunk<2>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 3: mdot_chunk<3>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 4: mdot_chunk<4>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 5: mdot_chunk<5>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 6: mdot_chunk<6>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 7: mdot_chunk<7>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 8: mdot_chunk<8>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 9: mdot_chunk<9>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 10: mdot_chunk<10>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 11: mdot_chunk<11>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 12: mdot_chunk<12>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 13: mdot_chunk<13>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 14: mdot_chunk<14>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            case 15: mdot_chunk<15>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
+            default: mdot_chunk<16>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
         }
         jf_launched();
         k_mfinal<<<m, RB, 0, s>>>(c->partial, nb, h + j0); jf_launched();
@@ -218,11 +224,11 @@ int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w,
 }
 
 int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
-                 double sign, cudaStream_t s) {
+                 double sign, cudaStream_t s, const double *flag) {
     (void)c;
     for (int j0 = 0; j0 < nv; j0 += MAXV) {
         const int m = nv - j0 < MAXV ? nv - j0 : MAXV;
-        k_mupdate<<<grid_for(n), 256, 0, s>>>(V + (size_t)j0 * ldv, m, ldv, h + j0, w, n, sign); jf_launched();
+        k_mupdate<<<grid_for(n), 256, 0, s>>>(V + (size_t)j0 * ldv, m, ldv, h + j0, w, n, sign, flag); jf_launched();
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -255,6 +261,23 @@ int blas_zcomb(const void *Z, int prec32, int nzv, size_t n, const double *yv, d
             k_zcomb<double><<<grid_for(n), 256, 0, s>>>((const double *)Z + (size_t)j0 * n, m, n, y, x);
         jf_launched();
     }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+// Second Gram-Schmidt pass needed?  With w1 = w0 - V h the first pass left
+// |w1|^2 of |w0|^2 = |w1|^2 + |h|^2; reorthogonalise when |w1| < |w0| / sqrt(2)
+// ("twice is enough").  flag = 1.0 or 0.0, decided on the device.
+__global__ void k_reortho_flag(const double *w1sq, const double *h, int nv, double *flag) {
+    double hh = 0.0;
+    for (int i = threadIdx.x; i < nv; i += 32) hh += h[i] * h[i];
+    hh = warp_sum(hh);
+    if (threadIdx.x == 0) *flag = (*w1sq < 0.5 * (*w1sq + hh)) ? 1.0 : 0.0;
+}
+
+int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag, cudaStream_t s) {
+    k_reortho_flag<<<1, 32, 0, s>>>(w1sq, h, nv, flag);
+    jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }

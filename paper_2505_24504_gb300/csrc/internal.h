@@ -105,11 +105,16 @@ struct jfnk_ctx {
 };
 
 // device scalar slots in ctx->scal
-enum { S_NORM = 0, S_EPS = 1, S_EPSFV = 8, S_NRM_FV = 24, S_H = 64, S_H2 = 128, S_COUNT = 256 };
+enum { S_NORM = 0, S_EPS = 1, S_W1 = 2, S_FLAG = 3, S_EPSFV = 8, S_NRM_FV = 24, S_H = 64, S_H2 = 128, S_COUNT = 256 };
 
-// number of kernels this library has launched (diagnostic counter)
+// number of kernels this library has launched (diagnostic counter); the
+// thread-local twin lets a graph capture count only its own thread's launches
 extern unsigned long long g_jf_launches;
-inline void jf_launched(unsigned n = 1) { __atomic_fetch_add(&g_jf_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+extern thread_local unsigned long long t_jf_launches;
+inline void jf_launched(unsigned n = 1) {
+    __atomic_fetch_add(&g_jf_launches, (unsigned long long)n, __ATOMIC_RELAXED);
+    t_jf_launches += n;
+}
 
 // ---- kernels / launchers (implemented in the .cu files) ----
 int dg_setup_background(jfnk_ctx *c);
@@ -148,8 +153,11 @@ int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out_dev, int op, cudaStream_t s);
 int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out_dev, int op, cudaStream_t s);
 enum { RED_SUM = 0, RED_SQRT = 1, RED_EPS = 2, RED_EPS32 = 3 };
-int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h_dev, cudaStream_t s);
-int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h_dev, double *w, size_t n, double sign, cudaStream_t s);
+int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h_dev, cudaStream_t s,
+              const double *flag = nullptr);
+int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h_dev, double *w, size_t n, double sign,
+                 cudaStream_t s, const double *flag = nullptr);
+int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag, cudaStream_t s);
 int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);
 int blas_zcomb(const void *Z, int prec32, int nz, size_t n, const double *yv, double *x, cudaStream_t s);

@@ -936,14 +936,15 @@ int capture(jfnk_ctx *c) {
         c->mg_graph_valid = 0;
     }
     if (!c->cap_stream) JF_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    const unsigned long long n0 = __atomic_load_n(&g_jf_launches, __ATOMIC_RELAXED);
+    const unsigned long long n0 = t_jf_launches;
     const long long d0 = c->dg_calls, f0 = c->fv_calls;
     JF_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int rc = apply_body(c, c->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    c->graph_launches = __atomic_load_n(&g_jf_launches, __ATOMIC_RELAXED) - n0;
+    c->graph_launches = t_jf_launches - n0;
     __atomic_fetch_sub(&g_jf_launches, c->graph_launches, __ATOMIC_RELAXED);   // captured, not launched
+    t_jf_launches = n0;
     c->graph_dg_calls = c->dg_calls - d0;
     c->graph_fv_calls = c->fv_calls - f0;
     c->dg_calls = d0;

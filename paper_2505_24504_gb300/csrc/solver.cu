@@ -82,11 +82,14 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
             const double *zj = z_as_double(c, j, c->w1, s, &rc);
             JF_RET(rc);
             JF_RET(apply_jv(c, U, adt, zj, w, s));
-            // CGS2
+            // classical Gram-Schmidt, second pass only when the first lost more
+            // than half of |w| (decided on the device)
             JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
             JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, s));
-            JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H2, s));
-            JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, s));
+            JF_RET(red_dot(c, w, w, N, c->scal + S_W1, RED_SUM, s));
+            JF_RET(blas_reortho_flag(c->scal + S_W1, c->scal + S_H, j + 1, c->scal + S_FLAG, s));
+            JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H2, s, c->scal + S_FLAG));
+            JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, s, c->scal + S_FLAG));
             JF_RET(red_dot(c, w, w, N, c->scal + S_NORM, RED_SQRT, s));
             JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
             JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));

@@ -86,6 +86,9 @@ def _lib():
             "jfnk_fv_residual": (I, [P, I, P, P, P]),
             "jfnk_eos_pressure": (I, [P, P, S, P, P]),
             "jfnk_norm2": (I, [P, P, S, P, P]),
+            "jfnk_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
+            "jfnk_batch_destroy": (None, [P]),
+            "jfnk_batch_step": (I, [P, P, P, P, P, P]),
             "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
@@ -100,6 +103,41 @@ def _lib():
 
 
 lib = _lib
+
+
+class Batch:
+    """Ensemble members stepped concurrently (jfnk_batch_*)."""
+
+    def __init__(self, contexts, max_threads=0):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = C.c_void_p()
+        _check(_lib().jfnk_batch_create(arr, len(self.contexts), int(max_threads), C.byref(h)),
+               "jfnk_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().jfnk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def jfnk_batch_step(self, states, dts, schemes, raise_on_error=True):
+        n = len(self.contexts)
+        U = (C.c_void_p * n)(*[s.data_ptr() for s in states])
+        dt = (C.c_double * n)(*[float(x) for x in dts])
+        sc = (C.c_int * n)(*[int(x) for x in schemes])
+        status = (C.c_int * n)()
+        stats = (Stats * n)()
+        rc = _lib().jfnk_batch_step(self.h, U, dt, sc, status, stats)
+        if raise_on_error:
+            _check(rc, "jfnk_batch_step")
+        return list(status), list(stats)
 
 
 def norm2_noalloc(x, out, n=None, stream=None):

@@ -1,0 +1,215 @@
+"""Request loop for implicit-step requests on device-resident atmospheric states
+(continuous batching, not a queue alone).
+
+* States stay on the device between requests (one FP64 DG vector each).
+* A request asks for one implicit step of one state.  It is admitted when a
+  worker slot is free, no earlier request of the same state is in flight, and
+  the HBM budget has room for that state's solver context (Krylov basis, FV
+  levels, workspace: `Context.workspace_bytes`).  Contexts are created on
+  admission and kept while idle; idle contexts are destroyed least-recently-used
+  first when a new context needs room.
+* Admitted requests run concurrently: each worker thread drives the C-ABI
+  implicit step on its own CUDA stream (the binding releases the GIL), so
+  requests that arrive while others are on the GPU overlap on the device.
+* A state's requests run in arrival order and one at a time, and every
+  kernel is deterministic, so each result is bit-identical to stepping that
+  state alone.
+
+Latency = completion - arrival (wall clock); the report gives p50 / p99 and the
+sustained steps/s.  Scheduling is host logic; every solve runs in libjfnk.so.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+from . import jfnk
+
+
+@dataclass
+class StateSpec:
+    """A resident state: solver construction arguments plus its device vector."""
+    grid: "jfnk.Grid"
+    k: int
+    phys: "jfnk.Physics"
+    opts: "jfnk.Opts"
+    dt: float
+    scheme: int
+    U: object            # torch CUDA float64 tensor, the state U' (updated in place)
+    steps_done: int = 0
+
+    @property
+    def footprint(self) -> int:
+        return jfnk.Context.workspace_bytes(self.grid, self.k, self.opts)
+
+
+@dataclass
+class Record:
+    sid: int
+    arrival: float
+    start: float = 0.0
+    end: float = 0.0
+    status: int = 0
+    gmres_its: int = 0
+
+
+@dataclass
+class Report:
+    records: list
+    wall_s: float
+    peak_bytes: int
+    contexts_created: int
+    contexts_evicted: int
+    max_concurrent: int
+    extra: dict = field(default_factory=dict)
+
+    def latencies(self):
+        return sorted(r.end - r.arrival for r in self.records)
+
+    def percentile(self, p):
+        lat = self.latencies()
+        if not lat:
+            return 0.0
+        i = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
+        return lat[i]
+
+    def summary(self):
+        n = len(self.records)
+        return {"requests": n, "steps_per_s": n / self.wall_s if self.wall_s > 0 else 0.0,
+                "p50_ms": 1e3 * self.percentile(50), "p99_ms": 1e3 * self.percentile(99),
+                "wall_s": self.wall_s, "peak_context_bytes": self.peak_bytes,
+                "contexts_created": self.contexts_created, "contexts_evicted": self.contexts_evicted,
+                "max_concurrent": self.max_concurrent,
+                "failed": sum(1 for r in self.records if r.status != 0)}
+
+
+class Server:
+    def __init__(self, states: dict, hbm_budget: int, workers: int = 8):
+        self.states = states
+        self.budget = int(hbm_budget)
+        self.workers = int(workers)
+        self._ctx = collections.OrderedDict()   # sid -> Context (LRU order)
+        self._busy = set()
+        self._lock = threading.Condition()
+        self._bytes = 0
+        self.peak = 0
+        self.created = 0
+        self.evicted = 0
+        for sid, st in states.items():
+            if st.footprint > self.budget:
+                raise ValueError(f"state {sid} needs {st.footprint} bytes, budget is {self.budget}")
+
+    # -- admission (called with the lock held) -------------------------------
+    def _can_admit(self, sid) -> bool:
+        if sid in self._busy:
+            return False
+        if sid in self._ctx:
+            return True
+        need = self.states[sid].footprint
+        free = self.budget - self._bytes
+        if need <= free:
+            return True
+        idle = [s for s in self._ctx if s not in self._busy]
+        return need <= free + sum(self.states[s].footprint for s in idle)
+
+    def _acquire(self, sid):
+        if sid in self._ctx:
+            self._ctx.move_to_end(sid)
+            ctx = self._ctx[sid]
+        else:
+            need = self.states[sid].footprint
+            for s in list(self._ctx):
+                if self._bytes + need <= self.budget:
+                    break
+                if s in self._busy:
+                    continue
+                self._ctx.pop(s).close()
+                self._bytes -= self.states[s].footprint
+                self.evicted += 1
+            st = self.states[sid]
+            ctx = jfnk.Context(st.grid, st.k, st.phys, st.opts)
+            self._ctx[sid] = ctx
+            self._bytes += need
+            self.created += 1
+            self.peak = max(self.peak, self._bytes)
+        self._busy.add(sid)
+        return ctx
+
+    def run(self, arrivals):
+        """Replay (arrival_time_s, sid) requests in real time; returns a Report."""
+        import torch
+        reqs = sorted(arrivals)
+        pending = collections.deque()
+        records = []
+        t0 = time.perf_counter()
+        state = {"next": 0, "done": 0, "inflight": 0, "maxc": 0}
+        total = len(reqs)
+
+        def pick():
+            # first pending request whose state can be admitted (FIFO per state)
+            seen = set()
+            for i, rec in enumerate(pending):
+                if rec.sid in seen:
+                    continue
+                seen.add(rec.sid)
+                if self._can_admit(rec.sid):
+                    del pending[i]
+                    return rec
+            return None
+
+        def worker():
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                while True:
+                    with self._lock:
+                        while True:
+                            now = time.perf_counter() - t0
+                            while state["next"] < total and reqs[state["next"]][0] <= now:
+                                a, sid = reqs[state["next"]]
+                                pending.append(Record(sid=sid, arrival=a))
+                                state["next"] += 1
+                            if state["done"] == total:
+                                self._lock.notify_all()
+                                return
+                            rec = pick()
+                            if rec is not None:
+                                ctx = self._acquire(rec.sid)
+                                state["inflight"] += 1
+                                state["maxc"] = max(state["maxc"], state["inflight"])
+                                break
+                            wait = None
+                            if state["next"] < total:
+                                wait = max(0.0, reqs[state["next"]][0] - now)
+                            self._lock.wait(timeout=wait if wait is not None else 0.05)
+                    st = self.states[rec.sid]
+                    rec.start = time.perf_counter() - t0
+                    s = ctx.implicit_step(st.U, st.dt, scheme=st.scheme, raise_on_error=False)
+                    stream.synchronize()
+                    rec.end = time.perf_counter() - t0
+                    rec.status = s.status
+                    rec.gmres_its = s.gmres_its
+                    with self._lock:
+                        st.steps_done += 1
+                        self._busy.discard(rec.sid)
+                        state["inflight"] -= 1
+                        state["done"] += 1
+                        records.append(rec)
+                        self._lock.notify_all()
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        wall = time.perf_counter() - t0
+        return Report(records=records, wall_s=wall, peak_bytes=self.peak, contexts_created=self.created,
+                      contexts_evicted=self.evicted, max_concurrent=state["maxc"])
+
+    def close(self):
+        with self._lock:
+            for c in self._ctx.values():
+                c.close()
+            self._ctx.clear()
+            self._bytes = 0

@@ -1,0 +1,81 @@
+"""Batched ensembles and the serving loop: every member / request result is the
+same bits as running that state alone (deterministic kernels, per-member
+buffers), under concurrency, uneven grids and orders, and HBM-budget eviction."""
+import numpy as np
+import pytest
+
+import synth
+from tests._common import gpu_context, oracle_dg, to_cpu, to_gpu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    w = synth.BUBBLE_Q2_20x10
+    ms = [synth.scaled(w, 16, 8, k=1, scheme=1), synth.scaled(w, 20, 10, k=2, scheme=1),
+          synth.scaled(w, 12, 6, k=3, scheme=1, fv_levels=4), synth.scaled(w, 8, 4, k=4, scheme=1),
+          synth.scaled(synth.DENSITY_CURRENT_Q2_256x32, 24, 6, x1=19200.0, k=2)]
+    states = []
+    for m in ms:
+        dg = oracle_dg(m)
+        states.append(dg.init_state(m.theta_pert(dg.X, dg.Z)))
+    return ms, states
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_batch_step_bitwise_equals_alone(prec):
+    import paper_2505_24504_gb300 as P
+    ms, U0 = _members()
+    alone = []
+    for m, u in zip(ms, U0):
+        ctx = gpu_context(m, precond_prec=prec)
+        U = to_gpu(u)
+        for _ in range(2):
+            ctx.implicit_step(U, m.dt, scheme=m.scheme)
+        alone.append(to_cpu(U))
+        ctx.close()
+    ctxs = [gpu_context(m, precond_prec=prec) for m in ms]
+    batch = P.Batch(ctxs, max_threads=4)
+    Us = [to_gpu(u) for u in U0]
+    for _ in range(2):
+        status, stats = batch.jfnk_batch_step(Us, [m.dt for m in ms], [m.scheme for m in ms])
+        assert status == [0] * len(ms)
+        assert all(s.newton_its > 0 for s in stats)
+    torch.cuda.synchronize()
+    for a, u in zip(alone, Us):
+        assert np.array_equal(a, to_cpu(u))
+    batch.close()
+
+
+def test_serving_mix_equals_alone_under_eviction():
+    import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300.serve import Server, StateSpec
+    ms, U0 = _members()
+    specs = {}
+    for sid, (m, u) in enumerate(zip(ms, U0)):
+        c = gpu_context(m, precond_prec=32)
+        specs[sid] = StateSpec(grid=c.grid, k=c.k, phys=c.phys, opts=c.opts, dt=m.dt, scheme=m.scheme,
+                               U=to_gpu(u))
+        c.close()
+    # budget for the two largest contexts only: forces admission waits and evictions
+    fp = sorted(s.footprint for s in specs.values())
+    srv = Server(specs, hbm_budget=fp[-1] + fp[-2], workers=3)
+    arr = synth.poisson_arrivals(400.0, 0.06, seed=7)
+    rng = np.random.default_rng(3)
+    reqs = [(float(t), int(rng.integers(0, len(ms)))) for t in arr]
+    rep = srv.run(reqs)
+    srv.close()
+    summ = rep.summary()
+    assert summ["requests"] == len(reqs) and summ["failed"] == 0
+    assert summ["p99_ms"] >= summ["p50_ms"] > 0
+    assert rep.contexts_evicted > 0 and rep.peak_bytes <= fp[-1] + fp[-2]
+    # each state alone, as many steps as it was served
+    for sid, (m, u) in enumerate(zip(ms, U0)):
+        ctx = gpu_context(m, precond_prec=32)
+        U = to_gpu(u)
+        for _ in range(specs[sid].steps_done):
+            ctx.implicit_step(U, m.dt, scheme=m.scheme)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_cpu(U), to_cpu(specs[sid].U)), sid
+        ctx.close()
