@@ -38,11 +38,17 @@ __device__ __forceinline__ double block_sum(double v) {
 
 template <class S>
 __global__ void __launch_bounds__(RB) k_dot_partial(const S *x, const S *y, size_t n, double *part) {
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
-    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride)
-        acc = fma((double)x[i], (double)y[i], acc);
-    acc = block_sum(acc);
+    size_t i = (size_t)blockIdx.x * RB + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {   // two loads in flight per thread
+        const double a0 = (double)x[i], b0 = (double)y[i];
+        const double a1 = (double)x[i + stride], b1 = (double)y[i + stride];
+        acc = fma(a0, b0, acc);
+        acc2 = fma(a1, b1, acc2);
+    }
+    if (i < n) acc = fma((double)x[i], (double)y[i], acc);
+    acc = block_sum(acc + acc2);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
@@ -74,10 +80,22 @@ __global__ void __launch_bounds__(RB) k_mdot_partial(const double *V, size_t ldv
 #pragma unroll
     for (int j = 0; j < NV; ++j) acc[j] = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
-    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
-        const double wi = w[i];
+    size_t i = (size_t)blockIdx.x * RB + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {   // two elements' loads in flight
+        const double w0 = w[i], w1 = w[i + stride];
+        double v0[NV], v1[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) acc[j] = fma(V[(size_t)j * ldv + i], wi, acc[j]);
+        for (int j = 0; j < NV; ++j) {
+            v0[j] = V[(size_t)j * ldv + i];
+            v1[j] = V[(size_t)j * ldv + i + stride];
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] = fma(v1[j], w1, fma(v0[j], w0, acc[j]));
+    }
+    if (i < n) {
+        const double w0 = w[i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] = fma(V[(size_t)j * ldv + i], w0, acc[j]);
     }
     __shared__ double sw[NV][RB / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -160,8 +178,10 @@ inline unsigned grid_for(size_t n) {
     return (unsigned)g;
 }
 
+// ~8 elements per thread: the FP64 shuffle tree (5 adds per value reduced)
+// stays small next to the per-element FMAs
 inline int nblocks_red(jfnk_ctx *c, size_t n) {
-    size_t g = (n + (size_t)RB - 1) / (size_t)RB;
+    size_t g = (n + (size_t)RB * 8 - 1) / ((size_t)RB * 8);
     if (g > (size_t)c->nb_red) g = c->nb_red;
     if (g < 1) g = 1;
     return (int)g;

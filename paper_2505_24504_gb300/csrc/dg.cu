@@ -72,7 +72,7 @@ JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
 
 // ---------------------------------------------------------------------------
 template <class T, int IN, int NP1, bool VISC>
-__global__ void __launch_bounds__(128) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
+__global__ void __launch_bounds__(128, 8) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
                                                typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
                                                typename OutT<T>::type *symz) {
     typedef typename OutT<T>::type O;
@@ -268,7 +268,7 @@ template <int NP1> struct EPBOf {
 };
 
 template <class T, int IN, int MODE, int NP1, bool VISC>
-__global__ void __launch_bounds__(128) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
+__global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
                                                 const typename OutT<T>::type *phix,
                                                 const typename OutT<T>::type *symx,
                                                 const typename OutT<T>::type *phiz,

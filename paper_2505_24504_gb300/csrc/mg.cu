@@ -42,8 +42,7 @@ __device__ __forceinline__ void load_pt(PowTab *s, const PowTab *g) {
 }
 
 // Level state loaders, addressed by (variable, cell, I, J):
-// IN 0 u; IN 1 u + eps x (FP64, eps on the device); IN 2 TL32 (u, x);
-// IN 3 TL32 (u, x - P v): the coarse correction folded into the direction.
+// IN 0 u; IN 1 u + eps x (FP64, eps on the device); IN 2 TL32 (u, x).
 template <class T, int IN> struct FLoad;
 template <> struct FLoad<D64, 0> {
     const double *u;
@@ -76,20 +75,6 @@ template <> struct FLoad<TL32, 2> {
         return TL32{u[i], x[i]};
     }
 };
-template <> struct FLoad<TL32, 3> {
-    const float *u, *x, *vc;
-    size_t n1, nc1;
-    int fac, NXc, zero;
-    JF_D void prepare() {}
-    JF_D double step() const { return 0.0; }
-    JF_D float dir(int v, size_t c, int I, int J) const {
-        const int Ic = fac == 2 ? (I >> 1) : I / fac, Jc = fac == 2 ? (J >> 1) : J / fac;
-        const float pv = vc[v * nc1 + (size_t)Jc * NXc + Ic];
-        return zero ? -pv : x[v * n1 + c] - pv;
-    }
-    JF_D TL32 operator()(int v, size_t c, int I, int J) const { return TL32{u[v * n1 + c], dir(v, c, I, J)}; }
-};
-
 enum { FV_RES = 0, FV_SMOOTH = 1, FV_DEFECT = 2 };
 
 template <class T> struct SOf;
@@ -206,6 +191,20 @@ __global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typen
 
 // FV pseudo-time step sizes: dtau = sigma / (1 + adt lambda), lambda = sum_faces
 // 1/2 s_e |e|/|c| + 2 mu (1/Hx^2 + 1/Hz^2), s_e = max over both sides of |v.n| + c.
+// wave speed |v . e_D| + c in the storage precision of the level
+template <class R>
+JF_D R wave_speed_r(const R U[4], int D, const PhysC &P, const PowTab *pt);
+template <>
+JF_D double wave_speed_r<double>(const double U[4], int D, const PhysC &P, const PowTab *pt) {
+    return wave_speed(U, D, P, pt);
+}
+template <>
+JF_D float wave_speed_r<float>(const float U[4], int D, const PhysC &P, const PowTab *) {
+    const float ir = 1.0f / U[0];
+    const float p = (float)P.p0 * __powf((float)P.R_over_p0 * U[3], (float)P.gamma);
+    return fabsf(U[1 + D] * ir) + sqrtf((float)P.gamma * p * ir);
+}
+
 template <class S>
 __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) {
     __shared__ PowTab spt;
@@ -216,21 +215,21 @@ __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) 
     const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n1) return;
     const int I = (int)(c % NX), Jz = (int)(c / NX);
-    auto st = [&](int i, int j, double U[4]) {
+    auto st = [&](int i, int j, S U[4]) {
         const size_t cc = (size_t)j * NX + i;
-        for (int v = 0; v < 4; ++v) U[v] = (double)u[(size_t)v * n1 + cc] + K.ub[v * NZ + j];
+        for (int v = 0; v < 4; ++v) U[v] = u[(size_t)v * n1 + cc] + (S)K.ub[v * NZ + j];
     };
-    double U[4], V[4];
+    S U[4], V[4];
     st(I, Jz, U);
-    const double sx = wave_speed(U, 0, K.pc, &spt), sz = wave_speed(U, 1, K.pc, &spt);
-    double eW = sx, eE = sx, eS = sz, eN = sz;
-    if (I > 0 || K.periodic) { st(I > 0 ? I - 1 : NX - 1, Jz, V); eW = fmax(sx, wave_speed(V, 0, K.pc, &spt)); }
-    if (I < NX - 1 || K.periodic) { st(I < NX - 1 ? I + 1 : 0, Jz, V); eE = fmax(sx, wave_speed(V, 0, K.pc, &spt)); }
-    if (Jz > 0) { st(I, Jz - 1, V); eS = fmax(sz, wave_speed(V, 1, K.pc, &spt)); }
-    if (Jz < NZ - 1) { st(I, Jz + 1, V); eN = fmax(sz, wave_speed(V, 1, K.pc, &spt)); }
-    const double lam = 0.5 * (eW + eE) * K.iHx + 0.5 * (eS + eN) * K.iHz +
-                       2.0 * K.mu * (K.iHx * K.iHx + K.iHz * K.iHz);
-    dtau[c] = (S)(sigma / (1.0 + adt * lam));
+    const S sx = wave_speed_r<S>(U, 0, K.pc, &spt), sz = wave_speed_r<S>(U, 1, K.pc, &spt);
+    S eW = sx, eE = sx, eS = sz, eN = sz;
+    if (I > 0 || K.periodic) { st(I > 0 ? I - 1 : NX - 1, Jz, V); eW = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
+    if (I < NX - 1 || K.periodic) { st(I < NX - 1 ? I + 1 : 0, Jz, V); eE = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
+    if (Jz > 0) { st(I, Jz - 1, V); eS = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
+    if (Jz < NZ - 1) { st(I, Jz + 1, V); eN = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
+    const S iHx = (S)K.iHx, iHz = (S)K.iHz;
+    const S lam = (S)0.5 * (eW + eE) * iHx + (S)0.5 * (eS + eN) * iHz + (S)(2.0 * K.mu) * (iHx * iHx + iHz * iHz);
+    dtau[c] = (S)sigma / ((S)1 + (S)adt * lam);
 }
 
 // DG pseudo-time step per element: lambda_E = (k+1)^2 max_nodes(|v| + c)(1/hx + 1/hz)
@@ -655,34 +654,6 @@ inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, cons
     return fv_op32(c, l, mode, (const float *)x, (const float *)b, (float *)out, s);
 }
 
-// first post-smoothing step with the coarse correction applied on the fly:
-// out = xc + dtau (b - g' xc), xc = (zero ? 0 : x) - P v   (FP32 tangent path)
-int fv_smooth_corrected32(jfnk_ctx *c, int l, bool zero, const float *b, float *out, cudaStream_t s) {
-    FVLev &L = c->lev[l];
-    FVLev &C = c->lev[l + 1];
-    FVK K = make_fvk(c, l);
-    const size_t n1 = (size_t)L.NX * L.NZ;
-    c->fv_calls++;
-    FLoad<TL32, 3> ld;
-    ld.u = (const float *)L.u;
-    ld.x = (const float *)L.x;
-    ld.vc = (const float *)C.x;
-    ld.fac = L.fac;
-    ld.NXc = C.NX;
-    ld.zero = zero ? 1 : 0;
-    ld.n1 = n1;
-    ld.nc1 = (size_t)C.NX * C.NZ;
-    const float *dt = (const float *)L.dtau;
-    if (c->phys.mu != 0.0) {
-        k_fv<TL32, 3, FV_SMOOTH, true><<<nblk(n1), 128, 0, s>>>(K, ld, nullptr, b, dt, nullptr, c->mg_adt, out);
-    } else {
-        k_fv<TL32, 3, FV_SMOOTH, false><<<nblk(n1), 128, 0, s>>>(K, ld, nullptr, b, dt, nullptr, c->mg_adt, out);
-    }
-    jf_launched();
-    JF_CK(cudaGetLastError());
-    return JFNK_OK;
-}
-
 // MG_l(x, b; u) of Sec. 3.4 on level l (0 = finest subgrid).  `zero`: x = 0 on
 // entry (products with x are skipped).  `first_done`: the caller already made
 // the first pre-smoothing step from zero (x = dtau b, fused into the transfer
@@ -732,16 +703,8 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             vz = false;
             fd = false;
         }
-        if (post >= 1 && c->prec != 64) {
-            JF_RET(fv_smooth_corrected32(c, l, zero, (const float *)L.b, (float *)L.x2, s));
-            void *t = L.x;
-            L.x = L.x2;
-            L.x2 = t;
-            --post;
-        } else {
-            k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
-            jf_launched();
-        }
+        k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
+        jf_launched();
         zero = false;
     }
     JF_RET(smooth(post));
