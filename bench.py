@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--ensemble", type=int, default=64, help="members of the batched ensemble (0: skip)")
     p.add_argument("--ensemble-steps", type=int, default=2)
     p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
+    p.add_argument("--viscous-steps", type=int, default=3, help="timed steps of the viscous workload (0: skip)")
+    p.add_argument("--mg-sweep", action="store_true",
+                   help="also sweep the preconditioner key (none, mg001111V, mg111111V, mg111111W)")
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
                    help="only run REPS FP64 FD products (face + volume kernels) of the workload "
                         "and print their CUDA-event times (small profiler captures)")
@@ -116,11 +119,11 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def make_context(w, prec):
+def make_context(w, prec, **kw):
     import paper_2505_24504_gb300 as P
     g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
     ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
-    o = P.Opts.defaults(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec)
+    o = P.Opts.defaults(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec, **kw)
     return P.Context(g, w.k, ph, o)
 
 
@@ -172,9 +175,16 @@ def run_ensemble(n, steps, warmup):
     import torch
 
     import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300 import autotune
     members = synth.ensemble(n)
-    ctxs = [make_context(m, 32) for m in members]
-    Us = [initial_state(c, m) for c, m in zip(ctxs, members)]
+    ctxs, Us = [], []
+    for m in members:
+        c0 = make_context(m, 32)
+        U = initial_state(c0, m)
+        c, _ = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U)
+        c0.close()
+        ctxs.append(c)
+        Us.append(U)
     batch = P.Batch(ctxs, max_threads=16)
     dts = [m.dt for m in members]
     sch = [m.scheme for m in members]
@@ -238,13 +248,71 @@ def run_serving(seconds, rate=200.0):
     return out
 
 
-def max_over_ranks(x, dist):
+def run_viscous(steps):
+    """Viscous density current (mu = 75 m^2/s, Q2 256x32, SDIRK2, dt = 1 s), FP32 preconditioner."""
+    import torch
+    from paper_2505_24504_gb300 import autotune
+    w = synth.DENSITY_CURRENT_Q2_256x32
+    c0 = make_context(w, 32)
+    U = initial_state(c0, w)
+    ctx, _ = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U)
+    c0.close()
+    ctx.implicit_step(U, w.dt, scheme=w.scheme)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ms, its = 0.0, []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = ctx.implicit_step(U, w.dt, scheme=w.scheme)
+        e1.record(s)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        its.append((st.newton_its, st.gmres_its))
+    ctx.close()
+    return {"workload": w.name, "steps_per_s": steps / (ms / 1e3), "dof_per_s": w.n_unknowns * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "newton_gmres_per_step": its[-1], "precond": "fp32"}
+
+
+def run_mg_sweep():
+    """Iterations, operator calls and time per SDIRK2 step for the paper's key variants."""
+    import torch
+    out = {}
+    for w in (synth.BUBBLE_Q3_160x80,):
+        rows = {}
+        for key in ("", "mg001111V", "mg111111V", "mg111111W", "mg112211V"):
+            ctx = make_context(w, 32, mg_key=key, gmres_max=3000)
+            U = initial_state(ctx, w)
+            ctx.implicit_step(U, w.dt, scheme=w.scheme)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            s = torch.cuda.current_stream()
+            e0.record(s)
+            st = ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
+            e1.record(s)
+            e1.synchronize()
+            rows[key or "none"] = {"ms": e0.elapsed_time(e1), "status": st.status, "newton": st.newton_its,
+                                   "gmres": st.gmres_its, "dg_calls": st.dg_calls, "fv_calls": st.fv_calls}
+            ctx.close()
+        out[w.name] = rows
+    return out
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """Max of x over the ranks (the timed region of the slowest rank)."""
     if not dist:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_max, world):
+    """Aggregate throughput: the units all ranks processed over the max time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 # ---------------------------------------------------------------------------
@@ -340,17 +408,20 @@ def main():
         print(json.dumps({"profile": "FP64 FD product", "face_ms": fm, "volume_ms": vm, "reps": args.profile_dg}))
         return
 
-    # ---- the product form: FP32 preconditioner --------------------------------
-    ctx = make_context(w, 32)
-    U = initial_state(ctx, w)
+    # ---- the product form: FP32 preconditioner, launch shapes from the autotuner --
+    from paper_2505_24504_gb300 import autotune
+    c0 = make_context(w, 32)
+    U = initial_state(c0, w)
     U0 = U.clone()
+    ctx, tiles = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U0)
+    c0.close()
     n0 = P.jfnk.launch_count()
     with Clocks(local) as clk:
         ms, stats = time_steps(ctx, U, w, args.steps, args.warmup, dist, flush)
     launches = P.jfnk.launch_count() - n0
     clocks = clk.summary()
     ms = max_over_ranks(ms, dist)
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(args.steps, ms, world)
     newton = sum(s["newton_its"] for s in stats) / len(stats)
     gmres = sum(s["gmres_its"] for s in stats) / len(stats)
     if args.form == "fp32":
@@ -421,6 +492,7 @@ def main():
         "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
                    "newton_tol": w.newton_tol, "mg_key": w.mg_key, "fv_levels": w.fv_levels,
                    "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",
+                   "tiles": {k: tiles[k] for k in ("tile_faces", "tile_volume", "tile_fv")},
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "gpu_launches": int(launches),
@@ -431,6 +503,10 @@ def main():
     }
     ctx.close()
     ctx64.close()
+    if args.viscous_steps > 0:
+        line["viscous"] = run_viscous(args.viscous_steps)
+    if args.mg_sweep:
+        line["mg_sweep"] = run_mg_sweep()
     if args.ensemble > 0:
         line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1)
     if args.serve_seconds > 0:

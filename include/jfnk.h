@@ -84,7 +84,9 @@ typedef struct {
  *  c_ip         interior-penalty constant of the viscous flux.
  *  use_graphs   1 (default): capture one preconditioner application in a CUDA
  *               graph on first use (and again when alpha_dt changes) and replay
- *               it; 0: launch the kernels one by one.  Same results either way. */
+ *               it; 0: launch the kernels one by one.  Same results either way.
+ *  tile_*       launch shapes (results do not depend on them); jfnk_autotune
+ *               picks them by timing. */
 typedef struct {
     double newton_tol;
     int newton_max;
@@ -96,6 +98,9 @@ typedef struct {
     int precond_prec;
     double sigma_fv, sigma_dg, c_ip;
     int use_graphs;
+    int tile_faces;      /* threads per block of the DG face kernel: 64, 128, 256 (0: 128) */
+    int tile_volume;     /* elements per DG volume block: 1 = ~64 threads, 2 = ~128 (0: 2) */
+    int tile_fv;         /* threads per block of the FV cell kernels: 64, 128, 256 (0: 128) */
 } jfnk_opts;
 
 /* Counters of one implicit_step (Sec. 4.2 counts linear iterations and
@@ -246,6 +251,16 @@ int jfnk_eos_pressure(jfnk_ctx *ctx, const double *E_dev, size_t n, double *p_de
  * ms[0], ms[1] receive the mean duration of the face and the volume kernel. */
 int jfnk_time_operator(jfnk_ctx *ctx, int which, const double *U_dev, const double *y_dev, int reps,
                        double *ms_host, void *stream);
+
+/* Autotuner of the launch shapes: times every (tile_faces, tile_volume)
+ * pair on `reps` FP64 FD products at state U with direction y (CUDA events on
+ * `stream`), and every tile_fv on `reps` preconditioner applications
+ * linearised at U (contexts with a preconditioner), keeps the fastest in the
+ * context and writes them to best[0..2] (host) and their times in ms to
+ * ms[0..1] (host; ms[1] = 0 without a preconditioner).  Results of every
+ * call are independent of the shapes; only speed changes. */
+int jfnk_autotune(jfnk_ctx *ctx, const double *U_dev, const double *y_dev, int reps, int *best_host,
+                  double *ms_host, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 unsigned long long jfnk_launch_count(void);

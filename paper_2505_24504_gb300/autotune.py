@@ -1,0 +1,75 @@
+"""Launch-shape autotuner with a persisted cache.
+
+`jfnk_autotune` (C ABI) times the tile choices of one context on the device:
+threads per block of the DG face kernel, elements per DG volume block, threads
+per block of the FV cell kernels.  This module keys the winners by GPU name,
+order, grid, viscosity, preconditioner precision and mg key, stores them in a
+JSON file (default: _tune_cache.json next to this module, not versioned) and
+applies them to the options of new contexts of the same shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import jfnk
+
+_LOCK = threading.Lock()
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json")
+
+
+def _gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def key_of(grid, k, phys, opts) -> str:
+    return "|".join([_gpu_name(), f"k{k}", f"{grid.nx}x{grid.nz}", f"p{grid.periodic_x}",
+                     "visc" if phys.mu != 0.0 else "euler", f"prec{opts.precond_prec}",
+                     opts.mg_key.decode() if isinstance(opts.mg_key, bytes) else str(opts.mg_key)])
+
+
+def load(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save(cache: dict, path: str = DEFAULT_CACHE) -> None:
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(opts, entry) -> None:
+    opts.tile_faces = int(entry["tile_faces"])
+    opts.tile_volume = int(entry["tile_volume"])
+    opts.tile_fv = int(entry["tile_fv"])
+
+
+def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CACHE, seed: int = 5):
+    """A context whose launch shapes come from the cache, tuning on a miss at
+    state U (device tensor) with a seeded random direction."""
+    import torch
+    key = key_of(grid, k, phys, opts)
+    with _LOCK:
+        cache = load(path)
+        entry = cache.get(key)
+    if entry is not None:
+        apply(opts, entry)
+        return jfnk.Context(grid, k, phys, opts), dict(entry, cached=True)
+    ctx = jfnk.Context(grid, k, phys, opts)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    y = torch.randn(ctx.N, dtype=torch.float64, device="cuda", generator=g)
+    entry = ctx.jfnk_autotune(U, y, reps=reps)
+    torch.cuda.synchronize()
+    apply(ctx.opts, entry)
+    with _LOCK:
+        cache = load(path)
+        cache[key] = entry
+        save(cache, path)
+    return ctx, dict(entry, cached=False)

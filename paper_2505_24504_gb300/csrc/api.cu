@@ -186,6 +186,9 @@ void jfnk_default_opts(jfnk_opts *o) {
     o->sigma_dg = 1.0;
     o->c_ip = 2.0;
     o->use_graphs = 1;
+    o->tile_faces = 128;
+    o->tile_volume = 2;
+    o->tile_fv = 128;
 }
 
 const char *jfnk_strerror(int code) {
@@ -232,6 +235,13 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     if (o.gmres_restart < 1 || o.gmres_restart > 64 || o.gmres_max < 1 || o.newton_max < 1) return JFNK_EINVAL;
     if (o.precond_prec != 64 && o.precond_prec != 32 && o.precond_prec != 16) return JFNK_EINVAL;
     if (o.fv_levels < 1) o.fv_levels = 1;
+    if (o.tile_faces == 0) o.tile_faces = 128;
+    if (o.tile_volume == 0) o.tile_volume = 2;
+    if (o.tile_fv == 0) o.tile_fv = 128;
+    if ((o.tile_faces != 64 && o.tile_faces != 128 && o.tile_faces != 256) ||
+        (o.tile_volume != 1 && o.tile_volume != 2) ||
+        (o.tile_fv != 64 && o.tile_fv != 128 && o.tile_fv != 256))
+        return JFNK_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -599,6 +609,83 @@ int jfnk_time_operator(jfnk_ctx *c, int which, const double *U, const double *y,
     ms[0] = c->t_faces_ms / reps;
     ms[1] = c->t_volume_ms / reps;
     return rc;
+}
+
+int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *best, double *ms, void *stream) {
+    if (!c || !U || !y || !best || !ms || reps < 1) return JFNK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int keep_f = c->opts.tile_faces, keep_v = c->opts.tile_volume, keep_fv = c->opts.tile_fv;
+    double best_dg = 1e300;
+    int bf = keep_f, bv = keep_v;
+    const int fs[3] = {64, 128, 256}, vs[2] = {1, 2};
+    for (int fi = 0; fi < 3; ++fi)
+        for (int vi = 0; vi < 2; ++vi) {
+            c->opts.tile_faces = fs[fi];
+            c->opts.tile_volume = vs[vi];
+            double t[2];
+            int rc = jfnk_time_operator(c, 1, U, y, reps + 1, t, stream);   // first rep warms up
+            if (rc) {
+                c->opts.tile_faces = keep_f;
+                c->opts.tile_volume = keep_v;
+                return rc;
+            }
+            if (t[0] + t[1] < best_dg) {
+                best_dg = t[0] + t[1];
+                bf = fs[fi];
+                bv = vs[vi];
+            }
+        }
+    c->opts.tile_faces = bf;
+    c->opts.tile_volume = bv;
+    double best_mg = 0.0;
+    int bfv = keep_fv;
+    if (c->mg_on) {
+        cudaEvent_t e0, e1;
+        JF_CK(cudaEventCreate(&e0));
+        JF_CK(cudaEventCreate(&e1));
+        DGArgs a = {};
+        a.U = U;
+        a.out0 = c->fU;
+        int rc = dg_apply(c, DG_RES, a, s);
+        if (!rc) rc = mg_linearize(c, U, 1.0, s);
+        best_mg = 1e300;
+        for (int t = 64; t <= 256 && rc == JFNK_OK; t *= 2) {
+            c->opts.tile_fv = t;
+            if (c->mg_graph_valid) {   // the graph holds the old launch shapes
+                cudaGraphExecDestroy(c->mg_graph);
+                c->mg_graph_valid = 0;
+            }
+            rc = mg_apply(c, y, c->Z, s);   // warm up (and capture)
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == JFNK_OK; ++r) rc = mg_apply(c, y, c->Z, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (m / reps < best_mg) {
+                best_mg = m / reps;
+                bfv = t;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (c->mg_graph_valid) {
+            cudaGraphExecDestroy(c->mg_graph);
+            c->mg_graph_valid = 0;
+        }
+        if (rc) {
+            c->opts.tile_fv = keep_fv;
+            return rc;
+        }
+    }
+    c->opts.tile_fv = bfv;
+    best[0] = bf;
+    best[1] = bv;
+    best[2] = bfv;
+    ms[0] = best_dg;
+    ms[1] = c->mg_on ? best_mg : 0.0;
+    return JFNK_OK;
 }
 
 unsigned long long jfnk_launch_count(void) { return __atomic_load_n(&g_jf_launches, __ATOMIC_RELAXED); }

@@ -72,7 +72,7 @@ JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
 
 // ---------------------------------------------------------------------------
 template <class T, int IN, int NP1, bool VISC>
-__global__ void __launch_bounds__(128, 8) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
+__global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
                                                typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
                                                typename OutT<T>::type *symz) {
     typedef typename OutT<T>::type O;
@@ -262,12 +262,14 @@ __global__ void __launch_bounds__(128, 8) k_faces(DGK K, Loader<T, IN> ld0, type
 }
 
 // ---------------------------------------------------------------------------
-template <int NP1> struct EPBOf {
+// elements per volume block: TV = 2 -> ~128 threads, TV = 1 -> ~64 threads
+template <int NP1, int TV> struct EPBOf {
     static constexpr int NP = NP1 * NP1;
-    static constexpr int value = (128 / NP) > 0 ? (128 / NP) : 1;
+    static constexpr int T = TV == 2 ? 128 : 64;
+    static constexpr int value = (T / NP) > 0 ? (T / NP) : 1;
 };
 
-template <class T, int IN, int MODE, int NP1, bool VISC>
+template <class T, int IN, int MODE, int NP1, bool VISC, int TV>
 __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
                                                 const typename OutT<T>::type *phix,
                                                 const typename OutT<T>::type *symx,
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
                                                 const typename OutT<T>::type *symz) {
     typedef typename OutT<T>::type O;
     constexpr int NP = NP1 * NP1;
-    constexpr int EPB = EPBOf<NP1>::value;
+    constexpr int EPB = EPBOf<NP1, TV>::value;
     __shared__ PowTab spt;
     __shared__ O sg[2][EPB][4][NP];
     __shared__ T su[VISC ? EPB : 1][4][NP];
@@ -507,11 +509,19 @@ int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, 
     }
     const long long nf = (long long)K.nz * (K.nx + 1) * NP1 + (long long)(K.nz + 1) * K.nx * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
-    k_faces<T, IN, NP1, VISC><<<(unsigned)((nf + 127) / 128), 128, 0, s>>>(K, ld, phix, symx, phiz, symz); jf_launched();
+    const int tf = c->opts.tile_faces;
+    k_faces<T, IN, NP1, VISC><<<(unsigned)((nf + tf - 1) / tf), tf, 0, s>>>(K, ld, phix, symx, phiz, symz); jf_launched();
     if (c->timing) JF_CK(cudaEventRecord(c->tev[1], s));
-    constexpr int EPB = EPBOf<NP1>::value;
-    const int nb = (K.n_el + EPB - 1) / EPB;
-    k_volume<T, IN, MODE, NP1, VISC><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz); jf_launched();
+    if (c->opts.tile_volume == 1) {
+        constexpr int EPB = EPBOf<NP1, 1>::value;
+        const int nb = (K.n_el + EPB - 1) / EPB;
+        k_volume<T, IN, MODE, NP1, VISC, 1><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz);
+    } else {
+        constexpr int EPB = EPBOf<NP1, 2>::value;
+        const int nb = (K.n_el + EPB - 1) / EPB;
+        k_volume<T, IN, MODE, NP1, VISC, 2><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz);
+    }
+    jf_launched();
     JF_CK(cudaGetLastError());
     if (c->timing) {
         JF_CK(cudaEventRecord(c->tev[2], s));

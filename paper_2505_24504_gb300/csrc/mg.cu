@@ -113,7 +113,7 @@ JF_D void visc2(const T UL[4], const T UR[4], double mu, double id, T V[4]) {
 
 // One thread per cell of an NX x NZ level.
 template <class T, int IN, int MODE, bool VISC>
-__global__ void __launch_bounds__(128) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
+__global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
                                             const double *fu, double adt, typename SOf<T>::type *out) {
     typedef typename SOf<T>::type S;
@@ -601,11 +601,12 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
     const size_t n1 = (size_t)L.NX * L.NZ;
     const bool visc = c->phys.mu != 0.0;
     c->fv_calls++;
-    const unsigned g = nblk(n1);
+    const int tb = c->opts.tile_fv;
+    const unsigned g = nblk(n1, tb);
     if (mode == FV_RES) {
         FLoad<D64, 0> ld{u, n1};
-        if (visc) { k_fv<D64, 0, FV_RES, true><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
-        else { k_fv<D64, 0, FV_RES, false><<<g, 128, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
+        if (visc) { k_fv<D64, 0, FV_RES, true><<<g, tb, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
+        else { k_fv<D64, 0, FV_RES, false><<<g, tb, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
     } else {
         double *epsp = c->scal + S_EPSFV + l;
         JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPS, s));
@@ -614,11 +615,11 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
         const double *fu = (const double *)L.fu;
         const double adt = c->mg_adt;
         if (mode == FV_SMOOTH) {
-            if (visc) { k_fv<D64, 1, FV_SMOOTH, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
-            else { k_fv<D64, 1, FV_SMOOTH, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            if (visc) { k_fv<D64, 1, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            else { k_fv<D64, 1, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
         } else {
-            if (visc) { k_fv<D64, 1, FV_DEFECT, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
-            else { k_fv<D64, 1, FV_DEFECT, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            if (visc) { k_fv<D64, 1, FV_DEFECT, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            else { k_fv<D64, 1, FV_DEFECT, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
         }
     }
     JF_CK(cudaGetLastError());
@@ -631,16 +632,17 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     const size_t n1 = (size_t)L.NX * L.NZ;
     const bool visc = c->phys.mu != 0.0;
     c->fv_calls++;
-    const unsigned g = nblk(n1);
+    const int tb = c->opts.tile_fv;
+    const unsigned g = nblk(n1, tb);
     FLoad<TL32, 2> ld{(const float *)L.u, x, n1};
     const float *dt = (const float *)L.dtau;
     const double adt = c->mg_adt;
     if (mode == FV_SMOOTH) {
-        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
-        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
     } else {
-        if (visc) { k_fv<TL32, 2, FV_DEFECT, true><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
-        else { k_fv<TL32, 2, FV_DEFECT, false><<<g, 128, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        if (visc) { k_fv<TL32, 2, FV_DEFECT, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        else { k_fv<TL32, 2, FV_DEFECT, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;

@@ -38,7 +38,8 @@ class Opts(C.Structure):
                 ("ew_eta0", C.c_double), ("ew_eta_max", C.c_double), ("mg_key", C.c_char * 16),
                 ("fv_levels", C.c_int), ("massfix", C.c_int), ("precond_prec", C.c_int),
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
+                ("tile_fv", C.c_int)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -92,6 +93,7 @@ def _lib():
             "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
+            "jfnk_autotune": (I, [P, P, P, I, P, P, P]),
             "jfnk_strerror": (C.c_char_p, [I]),
         }
         for name, (res, args) in sig.items():
@@ -240,6 +242,14 @@ class Context:
         _check(_lib().jfnk_time_operator(self.h, int(which), _ptr(U), _ptr(y), int(reps), ms, _stream(stream)),
                "jfnk_time_operator")
         return ms[0], ms[1]
+
+    def jfnk_autotune(self, U, y, reps=3, stream=None):
+        best = (C.c_int * 3)()
+        ms = (C.c_double * 2)()
+        _check(_lib().jfnk_autotune(self.h, _ptr(U), _ptr(y), int(reps), best, ms, _stream(stream)),
+               "jfnk_autotune")
+        return {"tile_faces": best[0], "tile_volume": best[1], "tile_fv": best[2],
+                "dg_ms": ms[0], "precond_ms": ms[1]}
 
     def fv_levels(self):
         n = _lib().jfnk_fv_levels(self.h)

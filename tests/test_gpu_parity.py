@@ -290,3 +290,26 @@ def test_norm2_entry_point():
         ctx.norm2(x, out, n=n)
         ref = float(np.linalg.norm(x.cpu().numpy()[:n])) if n else 0.0
         assert abs(out.item() - ref) <= 1e-14 * max(ref, 1.0)
+
+
+
+def test_launch_tiles_do_not_change_results_and_autotune_picks_valid_shapes():
+    w = synth.scaled(W1, 12, 6, k=3, fv_levels=4)
+    from tests._common import oracle_dg as od
+    dg = od(w)
+    U0 = initial_state(w, dg)
+    outs = []
+    for tf, tv, tfv in ((128, 2, 128), (64, 1, 64), (256, 2, 256)):
+        ctx = gpu_context(w, precond_prec=32, tile_faces=tf, tile_volume=tv, tile_fv=tfv)
+        U = to_gpu(U0)
+        ctx.implicit_step(U, w.dt, scheme=1)
+        outs.append(to_cpu(U))
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    ctx = gpu_context(w, precond_prec=32)
+    y = to_gpu(synth.random_perturbation(dg.shape[1:], 3))
+    best = ctx.jfnk_autotune(to_gpu(U0), y, reps=2)
+    assert best["tile_faces"] in (64, 128, 256) and best["tile_volume"] in (1, 2)
+    assert best["tile_fv"] in (64, 128, 256) and best["dg_ms"] > 0 and best["precond_ms"] > 0
+    U = to_gpu(U0)
+    ctx.implicit_step(U, w.dt, scheme=1)
+    assert np.array_equal(outs[0], to_cpu(U))
