@@ -123,7 +123,9 @@ def make_context(w, prec, **kw):
     import paper_2505_24504_gb300 as P
     g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
     ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
-    o = P.Opts.defaults(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec, **kw)
+    kwargs = dict(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec)
+    kwargs.update(kw)
+    o = P.Opts.defaults(**kwargs)
     return P.Context(g, w.k, ph, o)
 
 

@@ -149,7 +149,8 @@ size_t workspace(const jfnk_grid *g, int k, const jfnk_opts *o, const jfnk_physi
     if (prec != 64) b += 4 * (4 + (visc ? 6 : 0)) * (fx + fz);
     b += 8 * N * 9;                        // DG work vectors
     b += 8 * N * (size_t)(m + 1);          // V
-    b += sS * N * (size_t)m;               // Z
+    const bool mg_on = o->mg_key[0] != 0;
+    b += ((prec == 64 || !mg_on) ? 8 : 4) * N * (size_t)m;   // Z
     b += sS * N * 6;                       // pz, pz2, pd, pr, pin, pout
     b += 8 * (size_t)g->nx * g->nz;        // dtau_dg
     int NX[JF_MAXLEV], NZ[JF_MAXLEV], fac[JF_MAXLEV];
@@ -369,8 +370,11 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     A_(c->Ulin, 8 * N);
     const int m = o.gmres_restart;
     const size_t sS = c->prec == 64 ? 8 : 4;
+    // FGMRES stores z_j = Q^-1 v_j in the preconditioner's precision; without a
+    // preconditioner z_j = v_j is copied in FP64
+    const size_t sZ = (c->prec == 64 || !c->mg_on) ? 8 : 4;
     A_(c->V, 8 * N * (size_t)(m + 1));
-    A_(c->Z, sS * N * (size_t)m);
+    A_(c->Z, sZ * N * (size_t)m);
     A_(c->pz, sS * N);
     A_(c->pz2, sS * N);
     A_(c->pd, sS * N);

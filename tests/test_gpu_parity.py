@@ -235,11 +235,13 @@ def test_implicit_step_parity(case, scheme):
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
 
 
-def test_implicit_step_unpreconditioned_parity():
+@pytest.mark.parametrize("prec", [64, 32])
+def test_implicit_step_unpreconditioned_parity(prec):
+    # no preconditioner: FGMRES keeps z_j = v_j in FP64 whatever precond_prec says
     w = synth.scaled(W1, 10, 5)
     from tests._common import oracle_dg as od
     dg = od(w)
-    ctx = gpu_context(w, mg_key="")
+    ctx = gpu_context(w, mg_key="", precond_prec=prec)
     U0 = initial_state(w, dg)
     U = to_gpu(U0)
     st = ctx.implicit_step(U, w.dt, scheme=0)
