@@ -119,14 +119,18 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def make_context(w, prec, **kw):
+def make_args(w, prec, **kw):
     import paper_2505_24504_gb300 as P
     g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
     ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
     kwargs = dict(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec)
     kwargs.update(kw)
-    o = P.Opts.defaults(**kwargs)
-    return P.Context(g, w.k, ph, o)
+    return g, w.k, ph, P.Opts.defaults(**kwargs)
+
+
+def make_context(w, prec, **kw):
+    import paper_2505_24504_gb300 as P
+    return P.Context(*make_args(w, prec, **kw))
 
 
 def initial_state(ctx, w):
@@ -475,6 +479,15 @@ def main():
             "volume_kernel": {"achieved": ach_v, "frac": ach_v / peak, "launch_ms": vm,
                               "flop_per_launch": FLOPS_NODE * nodes}}
 
+    # ---- phase breakdown of one more step (events at the solver's own syncs) ----
+    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1), U0)
+    Up = U0.clone()
+    ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
+    stp = ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
+    phases = {"precond_ms": stp.t_precond_ms, "fd_product_ms": stp.t_jv_ms, "orthogonalisation_ms": stp.t_orth_ms,
+              "newton_residual_linearise_ms": stp.t_newton_ms}
+    ctx_p.close()
+
     # ---- the plain FP64 single-instance form ----------------------------------
     U64 = U0.clone()
     kp = args.plain_steps or max(2, args.steps // 3)
@@ -491,6 +504,7 @@ def main():
         "plain_fp64": {"value": plain, "unit": "implicit steps/s", "dof_per_s": plain * w.n_unknowns,
                        "ms_per_step": ms64 / kp},
         "iterations_per_step": {"newton": newton, "gmres": gmres},
+        "phases_per_step": phases,
         "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
                    "newton_tol": w.newton_tol, "mg_key": w.mg_key, "fv_levels": w.fv_levels,
                    "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",

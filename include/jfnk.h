@@ -101,6 +101,7 @@ typedef struct {
     int tile_faces;      /* threads per block of the DG face kernel: 64, 128, 256 (0: 128) */
     int tile_volume;     /* elements per DG volume block: 1 = ~64 threads, 2 = ~128 (0: 2) */
     int tile_fv;         /* threads per block of the FV cell kernels: 64, 128, 256 (0: 128) */
+    int profile;         /* 1: time the phases of implicit_step with CUDA events (jfnk_stats) */
 } jfnk_opts;
 
 /* Counters of one implicit_step (Sec. 4.2 counts linear iterations and
@@ -114,6 +115,10 @@ typedef struct {
     int fv_calls;        /* FV operator evaluations on all levels */
     double res0;         /* |G(U^0)| of the last stage */
     double res_final;    /* |G| at exit of the last stage */
+    /* device time by phase (ms), filled when opts.profile = 1, else 0:
+     * preconditioner applications, FD products, Gram-Schmidt + norms,
+     * Newton residuals + linearisations */
+    double t_precond_ms, t_jv_ms, t_orth_ms, t_newton_ms;
 } jfnk_stats;
 
 void jfnk_default_opts(jfnk_opts *opts);

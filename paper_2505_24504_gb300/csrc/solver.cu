@@ -16,6 +16,31 @@ namespace {
 struct Stats {
     int newton_its = 0, gmres_its = 0;
     double res0 = 0, res_final = 0;
+    double t_pre = 0, t_jv = 0, t_orth = 0, t_newton = 0;
+};
+
+// Phase timing with events recorded on the solver's stream; elapsed times are
+// read after the synchronisations the solver does anyway.
+struct Phases {
+    bool on = false;
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    explicit Phases(bool enable) : on(enable) {
+        if (on)
+            for (auto &x : e)
+                if (cudaEventCreate(&x) != cudaSuccess) on = false;
+    }
+    ~Phases() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    void mark(int i, cudaStream_t s) {
+        if (on) cudaEventRecord(e[i], s);
+    }
+    double ms(int a, int b) {
+        float m = 0.f;
+        if (on && cudaEventElapsedTime(&m, e[a], e[b]) == cudaSuccess) return m;
+        return 0.0;
+    }
 };
 
 // z_j of the flexible basis as an FP64 pointer (converted for FP32 storage)
@@ -49,7 +74,8 @@ int read_norm(jfnk_ctx *c, const double *x, double *out, cudaStream_t s) {
 
 // Solve G'(U) x = b from x = 0 until the residual estimate <= tol_abs.
 int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x, double tol_abs, int *its,
-           cudaStream_t s) {
+           cudaStream_t s, Stats &st) {
+    Phases ph(c->opts.profile != 0);
     const size_t N = c->N;
     const int m = c->opts.gmres_restart;
     const int maxit = c->opts.gmres_max;
@@ -74,6 +100,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
         for (int j = 0; j < m; ++j) {
             double *vj = V + (size_t)j * N, *w = V + (size_t)(j + 1) * N;
             int rc;
+            ph.mark(0, s);
             if (c->mg_on) {
                 JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s));
             } else {
@@ -81,7 +108,9 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
             }
             const double *zj = z_as_double(c, j, c->w1, s, &rc);
             JF_RET(rc);
+            ph.mark(1, s);
             JF_RET(apply_jv(c, U, adt, zj, w, s));
+            ph.mark(2, s);
             // classical Gram-Schmidt, second pass only when the first lost more
             // than half of |w| (decided on the device)
             JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
@@ -92,8 +121,12 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
             JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, s, c->scal + S_FLAG));
             JF_RET(red_dot(c, w, w, N, c->scal + S_NORM, RED_SQRT, s));
             JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
+            ph.mark(3, s);
             JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
             JF_CK(cudaStreamSynchronize(s));
+            st.t_pre += ph.ms(0, 1);
+            st.t_jv += ph.ms(1, 2);
+            st.t_orth += ph.ms(2, 3);
             const double *hp = c->h_pinned;
             for (int i = 0; i <= j; ++i) H[i][j] = hp[S_H + i] + hp[S_H2 + i];
             H[j + 1][j] = hp[S_NORM];
@@ -176,17 +209,24 @@ int newton(jfnk_ctx *c, double *U, double adt, Stats &st, cudaStream_t s) {
             eta = fmin(eta, o.ew_eta_max);
             eta = fmax(eta, 0.5 * o.newton_tol * n0 / nk);
         }
+        Phases ph(c->opts.profile != 0);
+        ph.mark(0, s);
         if (c->mg_on) JF_RET(mg_linearize(c, U, adt, s));
+        ph.mark(1, s);
         JF_RET(blas_scale(-1.0, c->G, c->G, c->N, s));
         int its = 0;
-        int rc = fgmres(c, U, adt, c->G, c->dU, eta * nk, &its, s);
+        int rc = fgmres(c, U, adt, c->G, c->dU, eta * nk, &its, s, st);
         st.gmres_its += its;
         if (rc != JFNK_OK && rc != JFNK_ENOTCONV) return rc;
         JF_RET(blas_axpby(1.0, U, 1.0, c->dU, U, c->N, s));
         ++st.newton_its;
         nk_prev = nk;
         eta_prev = eta;
-        JF_RET(eval_G(c, U, adt, &nk, s));
+        ph.mark(2, s);
+        JF_RET(eval_G(c, U, adt, &nk, s));   // synchronises
+        ph.mark(3, s);
+        cudaEventSynchronize(ph.e[3]);
+        st.t_newton += ph.ms(0, 1) + ph.ms(2, 3);
         st.res_final = nk;
         if (!isfinite(nk)) return JFNK_ENAN;
     }
@@ -237,6 +277,10 @@ extern "C" int implicit_step(jfnk_ctx *c, double *U, double dt, int scheme, jfnk
         stats->fv_calls = (int)c->fv_calls;
         stats->res0 = st.res0;
         stats->res_final = st.res_final;
+        stats->t_precond_ms = st.t_pre;
+        stats->t_jv_ms = st.t_jv;
+        stats->t_orth_ms = st.t_orth;
+        stats->t_newton_ms = st.t_newton;
     }
     return rc;
 }

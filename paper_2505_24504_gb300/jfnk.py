@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("fv_levels", C.c_int), ("massfix", C.c_int), ("precond_prec", C.c_int),
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
-                ("tile_fv", C.c_int)]
+                ("tile_fv", C.c_int), ("profile", C.c_int)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -54,7 +54,9 @@ class Opts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("stages", C.c_int), ("newton_its", C.c_int), ("gmres_its", C.c_int),
-                ("dg_calls", C.c_int), ("fv_calls", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
+                ("dg_calls", C.c_int), ("fv_calls", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
+                ("t_precond_ms", C.c_double), ("t_jv_ms", C.c_double), ("t_orth_ms", C.c_double),
+                ("t_newton_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
