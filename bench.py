@@ -419,8 +419,9 @@ def main():
     c0 = make_context(w, 32)
     U = initial_state(c0, w)
     U0 = U.clone()
-    ctx, tiles = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U0)
     c0.close()
+    # preconditioner schedule (smoothing counts / cycle) and launch shapes from the autotuner
+    ctx, tiles = autotune.tuned_schedule_context(*make_args(w, 32), U0, w.dt, w.scheme)
     n0 = P.jfnk.launch_count()
     with Clocks(local) as clk:
         ms, stats = time_steps(ctx, U, w, args.steps, args.warmup, dist, flush)
@@ -480,7 +481,7 @@ def main():
                               "flop_per_launch": FLOPS_NODE * nodes}}
 
     # ---- phase breakdown of one more step (events at the solver's own syncs) ----
-    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1), U0)
+    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1, mg_key=tiles["mg_key"]), U0)
     Up = U0.clone()
     ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
     stp = ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
@@ -506,9 +507,10 @@ def main():
         "iterations_per_step": {"newton": newton, "gmres": gmres},
         "phases_per_step": phases,
         "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
-                   "newton_tol": w.newton_tol, "mg_key": w.mg_key, "fv_levels": w.fv_levels,
+                   "newton_tol": w.newton_tol, "mg_key": tiles["mg_key"], "fv_levels": w.fv_levels,
                    "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",
                    "tiles": {k: tiles[k] for k in ("tile_faces", "tile_volume", "tile_fv")},
+                   "mg_key_tuned": tiles["mg_key"], "schedule_trials_ms": tiles["schedule_trials_ms"],
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "gpu_launches": int(launches),

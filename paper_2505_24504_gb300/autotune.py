@@ -73,3 +73,55 @@ def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CAC
         cache[key] = entry
         save(cache, path)
     return ctx, dict(entry, cached=False)
+
+
+SCHEDULES = ("mg111111V", "mg112211V", "mg111122V", "mg112222V", "mg001111V", "mg002211V")
+
+
+def schedule_key(grid, k, phys, opts, dt) -> str:
+    return "|".join([_gpu_name(), "schedule", f"k{k}", f"{grid.nx}x{grid.nz}", f"p{grid.periodic_x}",
+                     "visc" if phys.mu != 0.0 else "euler", f"prec{opts.precond_prec}", f"dt{dt:.6g}"])
+
+
+def tuned_schedule_context(grid, k, phys, opts, U, dt, scheme, candidates=SCHEDULES, path: str = DEFAULT_CACHE):
+    """A context with the fastest preconditioner key among `candidates` for this
+    shape and time step (one timed implicit step per candidate on a copy of U,
+    after one untimed step), launch shapes tuned per key.  Cached."""
+    import copy
+
+    import torch
+    skey = schedule_key(grid, k, phys, opts, dt)
+    with _LOCK:
+        entry = load(path).get(skey)
+    if entry is None:
+        trials = {}
+        for key in candidates:
+            o = copy.copy(opts)
+            o.mg_key = key.encode()
+            ctx, _ = tuned_context(grid, k, phys, o, U, path=path)
+            Uc = U.clone()
+            ctx.implicit_step(Uc, dt, scheme=scheme)
+            s = torch.cuda.current_stream()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            st = ctx.implicit_step(Uc, dt, scheme=scheme, raise_on_error=False)
+            e1.record(s)
+            e1.synchronize()
+            if st.status == 0:
+                trials[key] = e0.elapsed_time(e1)
+            ctx.close()
+            del Uc
+        best = min(trials, key=trials.get)
+        entry = {"mg_key": best, "trial_ms": trials}
+        with _LOCK:
+            cache = load(path)
+            cache[skey] = entry
+            save(cache, path)
+        cached = False
+    else:
+        cached = True
+    o = copy.copy(opts)
+    o.mg_key = entry["mg_key"].encode()
+    ctx, tiles = tuned_context(grid, k, phys, o, U, path=path)
+    return ctx, dict(tiles, mg_key=entry["mg_key"], schedule_trials_ms=entry["trial_ms"], schedule_cached=cached)

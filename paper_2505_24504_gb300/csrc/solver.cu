@@ -225,8 +225,10 @@ int newton(jfnk_ctx *c, double *U, double adt, Stats &st, cudaStream_t s) {
         ph.mark(2, s);
         JF_RET(eval_G(c, U, adt, &nk, s));   // synchronises
         ph.mark(3, s);
-        cudaEventSynchronize(ph.e[3]);
-        st.t_newton += ph.ms(0, 1) + ph.ms(2, 3);
+        if (ph.on) {
+            cudaEventSynchronize(ph.e[3]);
+            st.t_newton += ph.ms(0, 1) + ph.ms(2, 3);
+        }
         st.res_final = nk;
         if (!isfinite(nk)) return JFNK_ENAN;
     }
