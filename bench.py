@@ -486,7 +486,8 @@ def main():
     ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
     stp = ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
     phases = {"precond_ms": stp.t_precond_ms, "fd_product_ms": stp.t_jv_ms, "orthogonalisation_ms": stp.t_orth_ms,
-              "newton_residual_linearise_ms": stp.t_newton_ms}
+              "newton_residual_linearise_ms": stp.t_newton_ms, "gmres_its": stp.gmres_its,
+              "second_gram_schmidt_passes": stp.reorth}
     ctx_p.close()
 
     # ---- the plain FP64 single-instance form ----------------------------------

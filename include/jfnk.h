@@ -119,6 +119,7 @@ typedef struct {
      * preconditioner applications, FD products, Gram-Schmidt + norms,
      * Newton residuals + linearisations */
     double t_precond_ms, t_jv_ms, t_orth_ms, t_newton_ms;
+    int reorth;          /* Arnoldi steps that needed the second Gram-Schmidt pass */
 } jfnk_stats;
 
 void jfnk_default_opts(jfnk_opts *opts);

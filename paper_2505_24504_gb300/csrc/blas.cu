@@ -148,6 +148,69 @@ __global__ void k_axpby(double a, const double *x, double b, const double *y, do
         z[i] = a * x[i] + (y ? b * y[i] : 0.0);
 }
 
+// w += sign * sum_j h_j V_j and per-block partial sums of the updated w^2
+// (about 8 elements per thread, like the dot kernels)
+template <int NVMAX>
+__global__ void __launch_bounds__(RB) k_mupdate_norm(const double *V, int nv, size_t ldv, const double *h,
+                                                     double *w, size_t n, double sign, const double *flag,
+                                                     double *part) {
+    if (flag && *flag == 0.0) return;
+    __shared__ double sh[NVMAX];
+    if (threadIdx.x < nv) sh[threadIdx.x] = sign * h[threadIdx.x];
+    __syncthreads();
+    double acc2 = 0.0;
+    const size_t stride = (size_t)gridDim.x * RB;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+        double a = w[i];
+        for (int j = 0; j < nv; ++j) a = fma(sh[j], V[(size_t)j * ldv + i], a);
+        w[i] = a;
+        acc2 = fma(a, a, acc2);
+    }
+    acc2 = block_sum(acc2);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc2;
+}
+
+// After the first pass: w1sq = sum of partials, nrm = sqrt(w1sq) and the
+// reorthogonalisation flag (|w1| < |w0|/sqrt(2), |w0|^2 = |w1|^2 + |h|^2).
+// After the second pass (flag given): nrm = sqrt(sum) only if that pass ran.
+__global__ void __launch_bounds__(RB) k_final_gs(const double *part, int nb, const double *h, int nv,
+                                                 const double *flag_in, double *w1sq, double *nrm,
+                                                 double *flag_out) {
+    if (flag_in && *flag_in == 0.0) return;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += RB) acc += part[i];
+    acc = block_sum(acc);
+    __shared__ double tot;
+    if (threadIdx.x == 0) tot = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double hh = 0.0;
+        if (!flag_in)
+            for (int i = threadIdx.x; i < nv; i += 32) hh += h[i] * h[i];
+        hh = warp_sum(hh);
+        if (threadIdx.x == 0) {
+            *nrm = sqrt(tot);
+            if (!flag_in) {
+                *w1sq = tot;
+                *flag_out = (tot < 0.5 * (tot + hh)) ? 1.0 : 0.0;
+            }
+        }
+    }
+}
+
+// y = (double) x and per-block partial sums of x^2 (for eps of the FD product)
+__global__ void __launch_bounds__(RB) k_f2d_norm(const float *x, double *y, size_t n, double *part) {
+    double acc = 0.0;
+    const size_t stride = (size_t)gridDim.x * RB;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+        const double v = (double)x[i];
+        y[i] = v;
+        acc = fma(v, v, acc);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
 struct YV {
     double y[MAXV];
 };
@@ -297,6 +360,38 @@ __global__ void k_reortho_flag(const double *w1sq, const double *h, int nv, doub
 
 int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag, cudaStream_t s) {
     k_reortho_flag<<<1, 32, 0, s>>>(w1sq, h, nv, flag);
+    jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
+                      double sign, const double *flag_in, double *w1sq, double *nrm, double *flag_out,
+                      cudaStream_t s) {
+    if (nv > MAXV) {   // long bases: plain updates, then the norm pass
+        JF_RET(blas_mupdate(c, V, nv, ldv, h, w, n, sign, s, flag_in));
+        const int nb = nblocks_red(c, n);
+        k_dot_partial<double><<<nb, RB, 0, s>>>(w, w, n, c->partial);
+        jf_launched();
+        k_final_gs<<<1, RB, 0, s>>>(c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
+        jf_launched();
+        JF_CK(cudaGetLastError());
+        return JFNK_OK;
+    }
+    const int nb = nblocks_red(c, n);
+    k_mupdate_norm<MAXV><<<nb, RB, 0, s>>>(V, nv, ldv, h, w, n, sign, flag_in, c->partial);
+    jf_launched();
+    k_final_gs<<<1, RB, 0, s>>>(c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
+    jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s) {
+    const int nb = nblocks_red(c, n);
+    k_f2d_norm<<<nb, RB, 0, s>>>(x, y, n, c->partial);
+    jf_launched();
+    k_final<<<1, RB, 0, s>>>(c->partial, nb, eps_out, RED_EPS);
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
                                                typename OutT<T>::type *symz) {
     typedef typename OutT<T>::type O;
     __shared__ PowTab spt;
-    load_powtab(&spt, K.pt);
+    if (IN != 2) load_powtab(&spt, K.pt);   // the FP32 tangent power needs no table
     Loader<T, IN> ld = ld0;
     ld.prepare();
     __syncthreads();
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     __shared__ O sDx[NP1][NP1], sDz[NP1][NP1];
     __shared__ double sDn[NP1][NP1];
     __shared__ O sl[8][NP1];
-    load_powtab(&spt, K.pt);
+    if (IN != 2) load_powtab(&spt, K.pt);
     Loader<T, IN> ld = ld0;
     ld.prepare();
     if (threadIdx.x < NP) {

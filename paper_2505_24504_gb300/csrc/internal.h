@@ -158,6 +158,10 @@ int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w,
 int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h_dev, double *w, size_t n, double sign,
                  cudaStream_t s, const double *flag = nullptr);
 int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag, cudaStream_t s);
+int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
+                      double sign, const double *flag_in, double *w1sq, double *nrm, double *flag_out,
+                      cudaStream_t s);
+int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s);
 int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);
 int blas_zcomb(const void *Z, int prec32, int nz, size_t n, const double *yv, double *x, cudaStream_t s);

@@ -17,6 +17,7 @@ struct Stats {
     int newton_its = 0, gmres_its = 0;
     double res0 = 0, res_final = 0;
     double t_pre = 0, t_jv = 0, t_orth = 0, t_newton = 0;
+    int reortho = 0;
 };
 
 // Phase timing with events recorded on the solver's stream; elapsed times are
@@ -43,17 +44,22 @@ struct Phases {
     }
 };
 
-// z_j of the flexible basis as an FP64 pointer (converted for FP32 storage)
-const double *z_as_double(jfnk_ctx *c, int j, double *tmp, cudaStream_t s, int *rc) {
+// z_j of the flexible basis as an FP64 pointer; FP32 storage is converted and
+// eps of the FD product computed in the same pass (*eps_ready = true)
+const double *z_as_double(jfnk_ctx *c, int j, double *tmp, cudaStream_t s, int *rc, bool *eps_ready) {
     *rc = JFNK_OK;
+    *eps_ready = false;
     if (c->prec == 64 || !c->mg_on) return (const double *)c->Z + (size_t)j * c->N;
-    *rc = blas_copy_f2d((const float *)c->Z + (size_t)j * c->N, tmp, c->N, s);
+    *rc = blas_f2d_eps(c, (const float *)c->Z + (size_t)j * c->N, tmp, c->N, c->scal + S_EPS, s);
+    *eps_ready = true;
     return tmp;
 }
 
-// w = G'(U) y with eps = sqrt(eps_mach)/|y| computed on the device
-int apply_jv(jfnk_ctx *c, const double *U, double adt, const double *y, double *w, cudaStream_t s) {
-    JF_RET(red_dot(c, y, y, c->N, c->scal + S_EPS, RED_EPS, s));
+// w = G'(U) y with eps = sqrt(eps_mach)/|y| computed on the device (skipped
+// when the caller already wrote eps to S_EPS)
+int apply_jv(jfnk_ctx *c, const double *U, double adt, const double *y, double *w, cudaStream_t s,
+             bool eps_ready = false) {
+    if (!eps_ready) JF_RET(red_dot(c, y, y, c->N, c->scal + S_EPS, RED_EPS, s));
     DGArgs a = {};
     a.U = U;
     a.y = y;
@@ -106,20 +112,21 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
             } else {
                 JF_CK(cudaMemcpyAsync((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
             }
-            const double *zj = z_as_double(c, j, c->w1, s, &rc);
+            bool eps_ready = false;
+            const double *zj = z_as_double(c, j, c->w1, s, &rc, &eps_ready);
             JF_RET(rc);
             ph.mark(1, s);
-            JF_RET(apply_jv(c, U, adt, zj, w, s));
+            JF_RET(apply_jv(c, U, adt, zj, w, s, eps_ready));
             ph.mark(2, s);
-            // classical Gram-Schmidt, second pass only when the first lost more
-            // than half of |w| (decided on the device)
+            // classical Gram-Schmidt; the update kernel also reduces |w|^2, and a
+            // second pass runs only when the first lost more than half of |w|
+            // (decided on the device)
             JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
-            JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, s));
-            JF_RET(red_dot(c, w, w, N, c->scal + S_W1, RED_SUM, s));
-            JF_RET(blas_reortho_flag(c->scal + S_W1, c->scal + S_H, j + 1, c->scal + S_FLAG, s));
+            JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, nullptr, c->scal + S_W1,
+                                     c->scal + S_NORM, c->scal + S_FLAG, s));
             JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H2, s, c->scal + S_FLAG));
-            JF_RET(blas_mupdate(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, s, c->scal + S_FLAG));
-            JF_RET(red_dot(c, w, w, N, c->scal + S_NORM, RED_SQRT, s));
+            JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, c->scal + S_FLAG, nullptr,
+                                     c->scal + S_NORM, nullptr, s));
             JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
             ph.mark(3, s);
             JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
@@ -128,7 +135,8 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
             st.t_jv += ph.ms(1, 2);
             st.t_orth += ph.ms(2, 3);
             const double *hp = c->h_pinned;
-            for (int i = 0; i <= j; ++i) H[i][j] = hp[S_H + i] + hp[S_H2 + i];
+            if (hp[S_FLAG] != 0.0) ++st.reortho;
+            for (int i = 0; i <= j; ++i) H[i][j] = hp[S_H + i] + (hp[S_FLAG] != 0.0 ? hp[S_H2 + i] : 0.0);
             H[j + 1][j] = hp[S_NORM];
             if (!isfinite(H[j + 1][j])) return JFNK_ENAN;
             for (int i = 0; i < j; ++i) {
@@ -283,6 +291,7 @@ extern "C" int implicit_step(jfnk_ctx *c, double *U, double dt, int scheme, jfnk
         stats->t_jv_ms = st.t_jv;
         stats->t_orth_ms = st.t_orth;
         stats->t_newton_ms = st.t_newton;
+        stats->reorth = st.reortho;
     }
     return rc;
 }

@@ -56,7 +56,7 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("stages", C.c_int), ("newton_its", C.c_int), ("gmres_its", C.c_int),
                 ("dg_calls", C.c_int), ("fv_calls", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
                 ("t_precond_ms", C.c_double), ("t_jv_ms", C.c_double), ("t_orth_ms", C.c_double),
-                ("t_newton_ms", C.c_double)]
+                ("t_newton_ms", C.c_double), ("reorth", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
