@@ -215,7 +215,7 @@ size_t jfnk_workspace_bytes(const jfnk_grid *g, int k, const jfnk_opts *opts) {
 
 void jfnk_destroy(jfnk_ctx *c) {
     if (!c) return;
-    if (c->mg_graph_valid) cudaGraphExecDestroy(c->mg_graph);
+    jf_invalidate_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     Allocs *a = allocs_of(c);
     if (a) {
@@ -619,6 +619,7 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
     if (!c || !U || !y || !best || !ms || reps < 1) return JFNK_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int keep_f = c->opts.tile_faces, keep_v = c->opts.tile_volume, keep_fv = c->opts.tile_fv;
+    jf_invalidate_graphs(c);   // captured graphs hold the old launch shapes
     double best_dg = 1e300;
     int bf = keep_f, bv = keep_v;
     const int fs[3] = {64, 128, 256}, vs[2] = {1, 2};
@@ -684,6 +685,7 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
         }
     }
     c->opts.tile_fv = bfv;
+    jf_invalidate_graphs(c);
     best[0] = bf;
     best[1] = bv;
     best[2] = bfv;

@@ -96,6 +96,15 @@ struct jfnk_ctx {
     unsigned long long graph_launches;   // kernels in the graph
     long long graph_dg_calls, graph_fv_calls;
     void *pin, *pout;                    // fixed input / output of the graph
+    int mg_graph_gen;                    // incremented at every capture of the preconditioner
+    int capturing;                       // 1 while an Arnoldi step is being captured
+    // one graph per Arnoldi step index j (preconditioner child graph, FD
+    // product, Gram-Schmidt, normalisation, Hessenberg column copy)
+    cudaGraphExec_t arn_graph[64];
+    int arn_valid[64], arn_gen[64];
+    double arn_adt;
+    unsigned long long arn_launches[64];
+    long long arn_dg_calls[64], arn_fv_calls[64];
     size_t alloc_bytes;
     void *allocs;        // list of this context's allocations (api.cu)
     // optional per-launch timing of the DG kernels (jfnk_time_operator)
@@ -172,6 +181,8 @@ int blas_scale(double a, const double *x, double *y, size_t n, cudaStream_t s);
 // preconditioner (mg.cu)
 int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s);
 int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s);
+int mg_graph_prepare(jfnk_ctx *c);
+void jf_invalidate_graphs(jfnk_ctx *c);
 int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s);
 int transfer_to_fv64(jfnk_ctx *c, const double *u, double *v, cudaStream_t s);
 int transfer_to_dg64(jfnk_ctx *c, const double *v, double *u, int accumulate, cudaStream_t s);

@@ -927,15 +927,29 @@ int capture(jfnk_ctx *c) {
     }
     c->mg_graph_valid = 1;
     c->mg_graph_adt = c->mg_adt;
+    c->mg_graph_gen++;
     return JFNK_OK;
 }
 }  // namespace
+
+// Drop every captured graph (launch shapes or buffers changed).
+void jf_invalidate_graphs(jfnk_ctx *c) {
+    if (c->mg_graph_valid) {
+        cudaGraphExecDestroy(c->mg_graph);
+        c->mg_graph_valid = 0;
+    }
+    for (int i = 0; i < 64; ++i)
+        if (c->arn_valid[i]) {
+            cudaGraphExecDestroy(c->arn_graph[i]);
+            c->arn_valid[i] = 0;
+        }
+}
 
 int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s) {
     const size_t sS = c->prec == 64 ? 8 : 4;
     if (c->prec == 64) JF_CK(cudaMemcpyAsync(c->pin, r, 8 * c->N, cudaMemcpyDeviceToDevice, s));
     else JF_RET(blas_copy_d2f(r, (float *)c->pin, c->N, s));   // FP32 preconditioner: r enters in FP32
-    if (c->opts.use_graphs) {
+    if (c->opts.use_graphs && !c->capturing) {
         if (!c->mg_graph_valid || c->mg_graph_adt != c->mg_adt) JF_RET(capture(c));
         JF_CK(cudaGraphLaunch(c->mg_graph, s));
         jf_launched((unsigned)c->graph_launches);

@@ -78,6 +78,92 @@ int read_norm(jfnk_ctx *c, const double *x, double *out, cudaStream_t s) {
     return JFNK_OK;
 }
 
+// Device work of Arnoldi step j: z_j = Q^-1 v_j, w = G'(U) z_j into v_{j+1},
+// Gram-Schmidt (second pass decided on the device), normalisation, and the
+// copy of the Hessenberg column to pinned host memory.  No host decisions, so
+// it can be captured.
+int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStream_t s, Phases *ph) {
+    const size_t N = c->N;
+    double *V = c->V;
+    double *vj = V + (size_t)j * N, *w = V + (size_t)(j + 1) * N;
+    int rc;
+    if (ph) ph->mark(0, s);
+    if (c->mg_on) {
+        JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s));
+    } else {
+        JF_CK(cudaMemcpyAsync((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
+    }
+    bool eps_ready = false;
+    const double *zj = z_as_double(c, j, c->w1, s, &rc, &eps_ready);
+    JF_RET(rc);
+    if (ph) ph->mark(1, s);
+    JF_RET(apply_jv(c, U, adt, zj, w, s, eps_ready));
+    if (ph) ph->mark(2, s);
+    // classical Gram-Schmidt; the update kernel also reduces |w|^2, and a
+    // second pass runs only when the first lost more than half of |w|
+    // (decided on the device)
+    JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
+    JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, nullptr, c->scal + S_W1,
+                             c->scal + S_NORM, c->scal + S_FLAG, s));
+    JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H2, s, c->scal + S_FLAG));
+    JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, c->scal + S_FLAG, nullptr,
+                             c->scal + S_NORM, nullptr, s));
+    JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
+    if (ph) ph->mark(3, s);
+    JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
+    return JFNK_OK;
+}
+
+// Arnoldi step j, replayed from a graph captured per j (pointers are all
+// context-owned: U is the context's copy of the Newton iterate).
+int arnoldi_step(jfnk_ctx *c, const double *U, double adt, int j, cudaStream_t s, Phases &ph) {
+    const bool graphs = c->opts.use_graphs && !ph.on && U == c->Ulin && j < 64;
+    if (!graphs) return arnoldi_step_work(c, U, adt, j, s, ph.on ? &ph : nullptr);
+    if (c->arn_adt != adt) {
+        for (int i = 0; i < 64; ++i)
+            if (c->arn_valid[i]) {
+                cudaGraphExecDestroy(c->arn_graph[i]);
+                c->arn_valid[i] = 0;
+            }
+        c->arn_adt = adt;
+    }
+    if (!c->arn_valid[j]) {
+        if (!c->cap_stream) JF_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        const unsigned long long n0 = t_jf_launches;
+        const long long d0 = c->dg_calls, f0 = c->fv_calls;
+        JF_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c->capturing = 1;   // the preconditioner's kernels are captured inline
+        const int rc = arnoldi_step_work(c, U, adt, j, c->cap_stream, nullptr);
+        c->capturing = 0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        c->arn_launches[j] = t_jf_launches - n0;
+        __atomic_fetch_sub(&g_jf_launches, c->arn_launches[j], __ATOMIC_RELAXED);
+        t_jf_launches = n0;
+        c->arn_dg_calls[j] = c->dg_calls - d0;
+        c->arn_fv_calls[j] = c->fv_calls - f0;
+        c->dg_calls = d0;
+        c->fv_calls = f0;
+        if (rc != JFNK_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc != JFNK_OK ? rc : JFNK_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->arn_graph[j], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            return JFNK_ECUDA;
+        }
+        c->arn_valid[j] = 1;
+    }
+    JF_CK(cudaGraphLaunch(c->arn_graph[j], s));
+    jf_launched((unsigned)c->arn_launches[j]);
+    c->dg_calls += c->arn_dg_calls[j];
+    c->fv_calls += c->arn_fv_calls[j];
+    return JFNK_OK;
+}
+
 // Solve G'(U) x = b from x = 0 until the residual estimate <= tol_abs.
 int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x, double tol_abs, int *its,
            cudaStream_t s, Stats &st) {
@@ -104,32 +190,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
         int jd = 0;
         bool conv = false;
         for (int j = 0; j < m; ++j) {
-            double *vj = V + (size_t)j * N, *w = V + (size_t)(j + 1) * N;
-            int rc;
-            ph.mark(0, s);
-            if (c->mg_on) {
-                JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s));
-            } else {
-                JF_CK(cudaMemcpyAsync((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
-            }
-            bool eps_ready = false;
-            const double *zj = z_as_double(c, j, c->w1, s, &rc, &eps_ready);
-            JF_RET(rc);
-            ph.mark(1, s);
-            JF_RET(apply_jv(c, U, adt, zj, w, s, eps_ready));
-            ph.mark(2, s);
-            // classical Gram-Schmidt; the update kernel also reduces |w|^2, and a
-            // second pass runs only when the first lost more than half of |w|
-            // (decided on the device)
-            JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
-            JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, nullptr, c->scal + S_W1,
-                                     c->scal + S_NORM, c->scal + S_FLAG, s));
-            JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H2, s, c->scal + S_FLAG));
-            JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, c->scal + S_FLAG, nullptr,
-                                     c->scal + S_NORM, nullptr, s));
-            JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
-            ph.mark(3, s);
-            JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
+            JF_RET(arnoldi_step(c, U, adt, j, s, ph));
             JF_CK(cudaStreamSynchronize(s));
             st.t_pre += ph.ms(0, 1);
             st.t_jv += ph.ms(1, 2);
@@ -219,11 +280,13 @@ int newton(jfnk_ctx *c, double *U, double adt, Stats &st, cudaStream_t s) {
         }
         Phases ph(c->opts.profile != 0);
         ph.mark(0, s);
+        // the context's copy of U^k: the captured Arnoldi graphs hold this pointer
         if (c->mg_on) JF_RET(mg_linearize(c, U, adt, s));
+        else JF_CK(cudaMemcpyAsync(c->Ulin, U, 8 * c->N, cudaMemcpyDeviceToDevice, s));
         ph.mark(1, s);
         JF_RET(blas_scale(-1.0, c->G, c->G, c->N, s));
         int its = 0;
-        int rc = fgmres(c, U, adt, c->G, c->dU, eta * nk, &its, s, st);
+        int rc = fgmres(c, c->Ulin, adt, c->G, c->dU, eta * nk, &its, s, st);
         st.gmres_its += its;
         if (rc != JFNK_OK && rc != JFNK_ENOTCONV) return rc;
         JF_RET(blas_axpby(1.0, U, 1.0, c->dU, U, c->N, s));
