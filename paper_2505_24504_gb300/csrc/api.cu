@@ -15,6 +15,7 @@ void jf_background(const jfnk_physics *ph, double z, double U[4], double dU[4]);
 double jf_insert_coef(const jfnk_physics *ph, double z);
 
 unsigned long long g_jf_launches = 0;
+std::mutex g_jf_device_mu;
 thread_local unsigned long long t_jf_launches = 0;
 
 namespace {
@@ -213,7 +214,15 @@ size_t jfnk_workspace_bytes(const jfnk_grid *g, int k, const jfnk_opts *opts) {
     return workspace(g, k, &o, nullptr, nullptr);
 }
 
+static void destroy_unlocked(jfnk_ctx *c);
+
 void jfnk_destroy(jfnk_ctx *c) {
+    if (!c) return;
+    std::lock_guard<std::mutex> lock(g_jf_device_mu);
+    destroy_unlocked(c);
+}
+
+static void destroy_unlocked(jfnk_ctx *c) {
     if (!c) return;
     jf_invalidate_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -226,7 +235,16 @@ void jfnk_destroy(jfnk_ctx *c) {
     free(c);
 }
 
+static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_opts *opts,
+                         jfnk_ctx **out);
+
 int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_opts *opts, jfnk_ctx **out) {
+    std::unique_lock<std::mutex> lock(g_jf_device_mu);
+    return create_locked(g, k, ph, opts, out);
+}
+
+static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_opts *opts,
+                         jfnk_ctx **out) {
     if (!out) return JFNK_EINVAL;
     *out = nullptr;
     JF_RET(check_args(g, k, ph));
@@ -270,7 +288,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     c->prec = o.precond_prec;
     int rc = parse_key(c, o.mg_key);
     if (rc) {
-        jfnk_destroy(c);
+        destroy_unlocked(c);
         return rc;
     }
     const double R = ph->cp - ph->cv;
@@ -286,7 +304,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     do {                                     \
         rc = dalloc(c, &(p), (bytes));       \
         if (rc) {                            \
-            jfnk_destroy(c);                 \
+            destroy_unlocked(c);                 \
             return rc;                       \
         }                                    \
     } while (0)
@@ -338,7 +356,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
             cudaMemcpy(c->dubh, duh.data(), 8 * duh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(c->prow, pr.data(), 8 * pr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(c->theta_row, tr.data(), 8 * tr.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            jfnk_destroy(c);
+            destroy_unlocked(c);
             return JFNK_ECUDA;
         }
     }
@@ -395,7 +413,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
             cudaMemcpy(b2.data(), c->dubv, 8 * b2.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(b3.data(), c->ubh, 8 * b3.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(b4.data(), c->dubh, 8 * b4.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            jfnk_destroy(c);
+            destroy_unlocked(c);
             return JFNK_ECUDA;
         }
         for (size_t i = 0; i < b1.size(); ++i) {
@@ -410,7 +428,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
             cudaMemcpy(c->dubvf, a2.data(), 4 * a2.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(c->ubhf, a3.data(), 4 * a3.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(c->dubhf, a4.data(), 4 * a4.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            jfnk_destroy(c);
+            destroy_unlocked(c);
             return JFNK_ECUDA;
         }
     }
@@ -446,7 +464,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
         std::vector<float> ubf(ub.begin(), ub.end());
         if (cudaMemcpy(L.ub, ub.data(), 8 * ub.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(L.ubf, ubf.data(), 4 * ubf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            jfnk_destroy(c);
+            destroy_unlocked(c);
             return JFNK_ECUDA;
         }
     }
@@ -457,7 +475,7 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
         void *h = nullptr;
         if (cudaMallocHost(&h, 8 * (size_t)S_COUNT) != cudaSuccess) {
             cudaGetLastError();
-            jfnk_destroy(c);
+            destroy_unlocked(c);
             return JFNK_ENOMEM;
         }
         allocs_of(c)->host.push_back(h);
@@ -465,13 +483,13 @@ int jfnk_create(const jfnk_grid *g, int k, const jfnk_physics *ph, const jfnk_op
     }
 #undef A_
     if (cudaMemset(c->scal, 0, 8 * (size_t)S_COUNT) != cudaSuccess) {
-        jfnk_destroy(c);
+        destroy_unlocked(c);
         return JFNK_ECUDA;
     }
     rc = dg_setup_background(c);
     if (!rc) rc = fv_setup_background(c);
     if (rc) {
-        jfnk_destroy(c);
+        destroy_unlocked(c);
         return rc;
     }
     *out = c;

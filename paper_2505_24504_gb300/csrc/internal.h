@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/jfnk.h"
 #include "physics.cuh"
 
@@ -124,6 +126,12 @@ inline void jf_launched(unsigned n = 1) {
     __atomic_fetch_add(&g_jf_launches, (unsigned long long)n, __ATOMIC_RELAXED);
     t_jf_launches += n;
 }
+
+// Device-wide synchronisation (context creation and destruction: cudaMalloc,
+// synchronous copies, cudaDeviceSynchronize, cudaFree) is invalid while any
+// stream of the device is being captured, so captures and these calls take
+// this process-wide lock.
+extern std::mutex g_jf_device_mu;
 
 // ---- kernels / launchers (implemented in the .cu files) ----
 int dg_setup_background(jfnk_ctx *c);

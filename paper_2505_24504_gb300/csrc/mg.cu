@@ -900,6 +900,7 @@ int capture(jfnk_ctx *c) {
         cudaGraphExecDestroy(c->mg_graph);
         c->mg_graph_valid = 0;
     }
+    std::lock_guard<std::mutex> lock(g_jf_device_mu);   // no device-wide sync during capture
     if (!c->cap_stream) JF_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     const unsigned long long n0 = t_jf_launches;
     const long long d0 = c->dg_calls, f0 = c->fv_calls;

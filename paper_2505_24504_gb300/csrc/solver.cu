@@ -128,6 +128,7 @@ int arnoldi_step(jfnk_ctx *c, const double *U, double adt, int j, cudaStream_t s
         c->arn_adt = adt;
     }
     if (!c->arn_valid[j]) {
+        std::lock_guard<std::mutex> lock(g_jf_device_mu);   // no device-wide sync during capture
         if (!c->cap_stream) JF_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         const unsigned long long n0 = t_jf_launches;
         const long long d0 = c->dg_calls, f0 = c->fv_calls;

@@ -137,8 +137,9 @@ class Server:
         self._busy.add(sid)
         return ctx
 
-    def run(self, arrivals):
-        """Replay (arrival_time_s, sid) requests in real time; returns a Report."""
+    def run(self, arrivals, timeout_s: float = 600.0):
+        """Replay (arrival_time_s, sid) requests in real time; returns a Report.
+        Raises RuntimeError if the workers do not finish within timeout_s."""
         import torch
         reqs = sorted(arrivals)
         pending = collections.deque()
@@ -175,7 +176,15 @@ class Server:
                                 return
                             rec = pick()
                             if rec is not None:
-                                ctx = self._acquire(rec.sid)
+                                try:
+                                    ctx = self._acquire(rec.sid)
+                                except Exception as exc:   # admission failed: record, never hang
+                                    rec.status = getattr(exc, "code", -3)
+                                    rec.start = rec.end = time.perf_counter() - t0
+                                    state["done"] += 1
+                                    records.append(rec)
+                                    self._lock.notify_all()
+                                    continue
                                 state["inflight"] += 1
                                 state["maxc"] = max(state["maxc"], state["inflight"])
                                 break
@@ -185,11 +194,14 @@ class Server:
                             self._lock.wait(timeout=wait if wait is not None else 0.05)
                     st = self.states[rec.sid]
                     rec.start = time.perf_counter() - t0
-                    s = ctx.implicit_step(st.U, st.dt, scheme=st.scheme, raise_on_error=False)
-                    stream.synchronize()
+                    try:
+                        s = ctx.implicit_step(st.U, st.dt, scheme=st.scheme, raise_on_error=False)
+                        stream.synchronize()
+                        rec.status = s.status
+                        rec.gmres_its = s.gmres_its
+                    except Exception as exc:   # a failed request must not stop the loop
+                        rec.status = getattr(exc, "code", -3)
                     rec.end = time.perf_counter() - t0
-                    rec.status = s.status
-                    rec.gmres_its = s.gmres_its
                     with self._lock:
                         st.steps_done += 1
                         self._busy.discard(rec.sid)
@@ -201,8 +213,12 @@ class Server:
         threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
         for t in threads:
             t.start()
+        deadline = time.perf_counter() + timeout_s
         for t in threads:
-            t.join()
+            t.join(timeout=max(0.0, deadline - time.perf_counter()))
+        if any(t.is_alive() for t in threads):
+            raise RuntimeError(f"serving loop did not finish within {timeout_s} s "
+                               f"({state['done']} of {total} requests done)")
         wall = time.perf_counter() - t0
         return Report(records=records, wall_s=wall, peak_bytes=self.peak, contexts_created=self.created,
                       contexts_evicted=self.evicted, max_concurrent=state["maxc"])

@@ -23,6 +23,7 @@ def _members():
     return ms, states
 
 
+@pytest.mark.timeout(600)
 @pytest.mark.parametrize("prec", [64, 32])
 def test_batch_step_bitwise_equals_alone(prec):
     import paper_2505_24504_gb300 as P
@@ -48,6 +49,7 @@ def test_batch_step_bitwise_equals_alone(prec):
     batch.close()
 
 
+@pytest.mark.timeout(600)
 def test_serving_mix_equals_alone_under_eviction():
     import paper_2505_24504_gb300 as P
     from paper_2505_24504_gb300.serve import Server, StateSpec
@@ -64,7 +66,7 @@ def test_serving_mix_equals_alone_under_eviction():
     arr = synth.poisson_arrivals(400.0, 0.06, seed=7)
     rng = np.random.default_rng(3)
     reqs = [(float(t), int(rng.integers(0, len(ms)))) for t in arr]
-    rep = srv.run(reqs)
+    rep = srv.run(reqs, timeout_s=300.0)
     srv.close()
     summ = rep.summary()
     assert summ["requests"] == len(reqs) and summ["failed"] == 0
