@@ -481,7 +481,8 @@ def main():
                               "flop_per_launch": FLOPS_NODE * nodes}}
 
     # ---- phase breakdown of one more step (events at the solver's own syncs) ----
-    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1, mg_key=tiles["mg_key"]), U0)
+    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1, mg_key=tiles["mg_key"],
+                                                 sigma_fv=tiles["sigma_fv"], sigma_dg=tiles["sigma_dg"]), U0)
     Up = U0.clone()
     ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
     stp = ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
@@ -511,7 +512,8 @@ def main():
                    "newton_tol": w.newton_tol, "mg_key": tiles["mg_key"], "fv_levels": w.fv_levels,
                    "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",
                    "tiles": {k: tiles[k] for k in ("tile_faces", "tile_volume", "tile_fv")},
-                   "mg_key_tuned": tiles["mg_key"], "schedule_trials_ms": tiles["schedule_trials_ms"],
+                   "mg_key_tuned": tiles["mg_key"], "sigma_fv": tiles["sigma_fv"], "sigma_dg": tiles["sigma_dg"],
+                   "schedule_trials_ms": tiles["schedule_trials_ms"],
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "gpu_launches": int(launches),

@@ -75,7 +75,10 @@ def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CAC
     return ctx, dict(entry, cached=False)
 
 
-SCHEDULES = ("mg111111V", "mg112211V", "mg111122V", "mg112222V", "mg001111V", "mg002211V")
+SCHEDULES = ("mg111111V", "mg112211V", "mg113311V", "mg112222V", "mg122211V", "mg001111V", "mg002211V",
+             "mg112212V")
+SIGMA_FV = (0.7, 0.85, 1.0, 1.15)
+SIGMA_DG = (0.7, 1.0, 1.3)
 
 
 def schedule_key(grid, k, phys, opts, dt) -> str:
@@ -83,45 +86,64 @@ def schedule_key(grid, k, phys, opts, dt) -> str:
                      "visc" if phys.mu != 0.0 else "euler", f"prec{opts.precond_prec}", f"dt{dt:.6g}"])
 
 
-def tuned_schedule_context(grid, k, phys, opts, U, dt, scheme, candidates=SCHEDULES, path: str = DEFAULT_CACHE):
-    """A context with the fastest preconditioner key among `candidates` for this
-    shape and time step (one timed implicit step per candidate on a copy of U,
-    after one untimed step), launch shapes tuned per key.  Cached."""
-    import copy
-
+def _trial(grid, k, phys, opts, U, dt, scheme, path):
+    """Device time of one implicit step (after one untimed step) on a copy of U; None on failure."""
     import torch
+    ctx, _ = tuned_context(grid, k, phys, opts, U, path=path)
+    Uc = U.clone()
+    try:
+        st0 = ctx.implicit_step(Uc, dt, scheme=scheme, raise_on_error=False)
+        if st0.status != 0:
+            return None
+        s = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = ctx.implicit_step(Uc, dt, scheme=scheme, raise_on_error=False)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) if st.status == 0 else None
+    finally:
+        ctx.close()
+        del Uc
+
+
+def tuned_schedule_context(grid, k, phys, opts, U, dt, scheme, candidates=SCHEDULES, path: str = DEFAULT_CACHE):
+    """A context with the fastest preconditioner schedule for this shape and time
+    step: the mg key among `candidates` (pseudo-time factors 1), then sigma_fv and
+    sigma_dg by coordinate search.  One timed implicit step per trial on a copy of
+    U; launch shapes tuned per key; everything cached.  The converged answer does
+    not depend on these choices (the Newton tolerance decides it)."""
+    import copy
     skey = schedule_key(grid, k, phys, opts, dt)
     with _LOCK:
         entry = load(path).get(skey)
+    cached = entry is not None
     if entry is None:
         trials = {}
-        for key in candidates:
+
+        def run(key, sfv, sdg):
             o = copy.copy(opts)
             o.mg_key = key.encode()
-            ctx, _ = tuned_context(grid, k, phys, o, U, path=path)
-            Uc = U.clone()
-            ctx.implicit_step(Uc, dt, scheme=scheme)
-            s = torch.cuda.current_stream()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            st = ctx.implicit_step(Uc, dt, scheme=scheme, raise_on_error=False)
-            e1.record(s)
-            e1.synchronize()
-            if st.status == 0:
-                trials[key] = e0.elapsed_time(e1)
-            ctx.close()
-            del Uc
-        best = min(trials, key=trials.get)
-        entry = {"mg_key": best, "trial_ms": trials}
+            o.sigma_fv = sfv
+            o.sigma_dg = sdg
+            t = _trial(grid, k, phys, o, U, dt, scheme, path)
+            trials[f"{key}/{sfv}/{sdg}"] = t
+            return t if t is not None else float("inf")
+
+        best_key = min(candidates, key=lambda kk: run(kk, 1.0, 1.0))
+        best_fv = min(SIGMA_FV, key=lambda sv: trials.get(f"{best_key}/{sv}/1.0") or run(best_key, sv, 1.0))
+        best_dg = min(SIGMA_DG, key=lambda sd: trials.get(f"{best_key}/{best_fv}/{sd}") or run(best_key, best_fv, sd))
+        entry = {"mg_key": best_key, "sigma_fv": best_fv, "sigma_dg": best_dg,
+                 "trial_ms": {kk: v for kk, v in trials.items() if v is not None}}
         with _LOCK:
             cache = load(path)
             cache[skey] = entry
             save(cache, path)
-        cached = False
-    else:
-        cached = True
     o = copy.copy(opts)
     o.mg_key = entry["mg_key"].encode()
+    o.sigma_fv = entry["sigma_fv"]
+    o.sigma_dg = entry["sigma_dg"]
     ctx, tiles = tuned_context(grid, k, phys, o, U, path=path)
-    return ctx, dict(tiles, mg_key=entry["mg_key"], schedule_trials_ms=entry["trial_ms"], schedule_cached=cached)
+    return ctx, dict(tiles, mg_key=entry["mg_key"], sigma_fv=entry["sigma_fv"], sigma_dg=entry["sigma_dg"],
+                     schedule_trials_ms=entry["trial_ms"], schedule_cached=cached)

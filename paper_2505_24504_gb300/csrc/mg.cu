@@ -111,22 +111,11 @@ JF_D void visc2(const T UL[4], const T UR[4], double mu, double id, T V[4]) {
     for (int v = 1; v < 4; ++v) V[v] = c * (UR[v] * irR - UL[v] * irL);
 }
 
-// One thread per cell of an NX x NZ level.
-template <class T, int IN, int MODE, bool VISC>
-__global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
-                                            const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
-                                            const double *fu, double adt, typename SOf<T>::type *out) {
-    typedef typename SOf<T>::type S;
-    __shared__ PowTab spt;
-    if (IN != 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
-    FLoad<T, IN> ld = ld0;
-    ld.prepare();
-    __syncthreads();
+// f_low (or its tangent) at one cell (I, Jz): HLLC^pert on the four faces,
+// gravity source, two-point viscous flux.
+template <class T, int IN, bool VISC>
+JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size_t c, int I, int Jz, T f[4]) {
     const int NX = K.NX, NZ = K.NZ;
-    const size_t n1 = (size_t)NX * NZ;
-    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n1) return;
-    const int I = (int)(c % NX), Jz = (int)(c / NX);
     const bool sub = (IN != 2);
     T U[4], Un[4][4];   // own state and the W, E, S, N neighbours
     int nb[4] = {-1, -1, -1, -1};
@@ -148,11 +137,10 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
             Un[q][v] = nb[q] >= 0 ? ld(v, (size_t)nb[q], nI[q], nJ[q]) + bgs<T>(K.ub, K.ubf, v * NZ + nJ[q]) : U[v];
     }
     T HW[4], HE[4], HS[4], HN[4];
-    face_flux<T, 0>(Un[0], U, nb[0] < 0, false, nb[0] < 0 ? K.hbxw : K.hbx, NZ, Jz, sub, K, &spt, HW);
-    face_flux<T, 0>(U, Un[1], false, nb[1] < 0, nb[1] < 0 ? K.hbxw + 4 * NZ : K.hbx, NZ, Jz, sub, K, &spt, HE);
-    face_flux<T, 1>(Un[2], U, nb[2] < 0, false, K.hbz, NZ + 1, Jz, sub, K, &spt, HS);
-    face_flux<T, 1>(U, Un[3], false, nb[3] < 0, K.hbz, NZ + 1, Jz + 1, sub, K, &spt, HN);
-    T f[4];
+    face_flux<T, 0>(Un[0], U, nb[0] < 0, false, nb[0] < 0 ? K.hbxw : K.hbx, NZ, Jz, sub, K, spt, HW);
+    face_flux<T, 0>(U, Un[1], false, nb[1] < 0, nb[1] < 0 ? K.hbxw + 4 * NZ : K.hbx, NZ, Jz, sub, K, spt, HE);
+    face_flux<T, 1>(Un[2], U, nb[2] < 0, false, K.hbz, NZ + 1, Jz, sub, K, spt, HS);
+    face_flux<T, 1>(U, Un[3], false, nb[3] < 0, K.hbz, NZ + 1, Jz + 1, sub, K, spt, HN);
     const T iHx = mk(K.iHx, T{}), iHz = mk(K.iHz, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v) f[v] = -((HE[v] - HW[v]) * iHx + (HN[v] - HS[v]) * iHz);
@@ -168,6 +156,32 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
 #pragma unroll
         for (int v = 1; v < 4; ++v) f[v] = f[v] + (VE[v] - VW[v]) * iHx + (VN[v] - VS[v]) * iHz;
     }
+}
+
+// g'(u) x at one cell and variable from the operator value f (FD quotient or tangent)
+template <class T, int IN, class S>
+JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, double adt, double eps) {
+    if (IN == 1) return (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)oval(f) - fu[gi]) / eps);
+    return x - (S)adt * (S)oval(f);
+}
+
+// One thread per cell of an NX x NZ level.
+template <class T, int IN, int MODE, bool VISC>
+__global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
+                                            const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
+                                            const double *fu, double adt, typename SOf<T>::type *out) {
+    typedef typename SOf<T>::type S;
+    __shared__ PowTab spt;
+    if (IN != 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
+    FLoad<T, IN> ld = ld0;
+    ld.prepare();
+    __syncthreads();
+    const size_t n1 = (size_t)K.NX * K.NZ;
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n1) return;
+    const int I = (int)(c % K.NX), Jz = (int)(c / K.NX);
+    T f[4];
+    fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
     const double eps = ld.step();
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -176,16 +190,55 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
             out[gi] = (S)oval(f[v]);
         } else {
             const S x = (S)ld.dir(v, c, I, Jz);
-            S gx;
-            if (IN == 1)
-                gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)oval(f[v]) - fu[gi]) / eps);
-            else
-                gx = x - (S)adt * (S)oval(f[v]);
+            const S gx = gprime_of<T, IN, S>(ld, x, f[v], fu, gi, adt, eps);
             if (MODE == FV_SMOOTH)
                 out[gi] = x + dtau[c] * (b[gi] - gx);
             else
                 out[gi] = gx - b[gi];
         }
+    }
+}
+
+// Defect and restriction in one pass: one thread per coarse cell computes the
+// defect g'x - b of its fac x fac children and writes the mean to b_c; when x_c
+// is given, also the coarse level's first pseudo-time step x_c = dtau_c b_c.
+template <class T, int IN, bool VISC>
+__global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *b,
+                                                            const double *fu, double adt, int fac,
+                                                            typename SOf<T>::type *bc, typename SOf<T>::type *xc,
+                                                            const typename SOf<T>::type *dtau_c) {
+    typedef typename SOf<T>::type S;
+    __shared__ PowTab spt;
+    if (IN != 2) load_pt(&spt, K.pt);
+    FLoad<T, IN> ld = ld0;
+    ld.prepare();
+    __syncthreads();
+    const int NXc = K.NX / fac, NZc = K.NZ / fac;
+    const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
+    const size_t cc = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cc >= nc) return;
+    const int Ic = (int)(cc % NXc), Jc = (int)(cc / NXc);
+    const double eps = ld.step();
+    S acc[4] = {0, 0, 0, 0};
+    for (int jj = 0; jj < fac; ++jj)
+        for (int ii = 0; ii < fac; ++ii) {
+            const int I = Ic * fac + ii, Jz = Jc * fac + jj;
+            const size_t c = (size_t)Jz * K.NX + I;
+            T f[4];
+            fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const size_t gi = (size_t)v * n1 + c;
+                const S x = (S)ld.dir(v, c, I, Jz);
+                acc[v] += gprime_of<T, IN, S>(ld, x, f[v], fu, gi, adt, eps) - b[gi];
+            }
+        }
+    const S inv = (S)1 / (S)(fac * fac);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const S bv = acc[v] * inv;
+        bc[(size_t)v * nc + cc] = bv;
+        if (xc) xc[(size_t)v * nc + cc] = dtau_c[cc] * bv;
     }
 }
 
@@ -648,6 +701,45 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     return JFNK_OK;
 }
 
+// defect g'x - b on level l restricted to level l+1 (b_{l+1}, and x_{l+1} = dtau b
+// when xc is given)
+int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *bc, void *xc, const void *dtc,
+                       cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    FVLev &C = c->lev[l + 1];
+    FVK K = make_fvk(c, l);
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    const size_t nc = (size_t)C.NX * C.NZ;
+    const bool visc = c->phys.mu != 0.0;
+    const int tb = c->opts.tile_fv;
+    const unsigned g = nblk(nc, tb);
+    c->fv_calls++;
+    if (c->prec == 64) {
+        double *epsp = c->scal + S_EPSFV + l;
+        JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPS, s));
+        FLoad<D64, 1> ld{(const double *)L.u, (const double *)x, epsp, n1, 0.0};
+        if (visc)
+            k_fv_defect_restrict<D64, 1, true><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
+                                                                c->mg_adt, L.fac, (double *)bc, (double *)xc,
+                                                                (const double *)dtc);
+        else
+            k_fv_defect_restrict<D64, 1, false><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
+                                                                 c->mg_adt, L.fac, (double *)bc, (double *)xc,
+                                                                 (const double *)dtc);
+    } else {
+        FLoad<TL32, 2> ld{(const float *)L.u, (const float *)x, n1};
+        if (visc)
+            k_fv_defect_restrict<TL32, 2, true><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
+                                                                 (float *)bc, (float *)xc, (const float *)dtc);
+        else
+            k_fv_defect_restrict<TL32, 2, false><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
+                                                                  (float *)bc, (float *)xc, (const float *)dtc);
+    }
+    jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
 inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, const void *b, void *out,
                                cudaStream_t s) {
     if (c->prec == 64)
@@ -689,16 +781,17 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     JF_RET(smooth(pre));
     if (l < c->nlev - 1) {
         FVLev &C = c->lev[l + 1];
+        const bool fuse = c->mid_pre >= 1;
         if (zero) {
             k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
             jf_launched();
+            k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
+                                                           fuse ? (S *)C.x : nullptr, (const S *)C.dtau);
+            jf_launched();
         } else {
-            JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
+            // defect and restriction (and the coarse first step) in one pass
+            JF_RET(fv_defect_restrict(c, l, L.x, L.b, C.b, fuse ? C.x : nullptr, C.dtau, s));
         }
-        const bool fuse = c->mid_pre >= 1;
-        k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
-                                                       fuse ? (S *)C.x : nullptr, (const S *)C.dtau);
-        jf_launched();
         bool vz = true, fd = fuse;
         for (int cyc = 0; cyc < c->cycles; ++cyc) {
             JF_RET(mg_cycle_t<S>(c, l + 1, vz, fd, s));
