@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--ensemble-steps", type=int, default=2)
     p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
     p.add_argument("--viscous-steps", type=int, default=3, help="timed steps of the viscous workload (0: skip)")
+    p.add_argument("--schedule", default=None, metavar="KEY",
+                   help="use this mg key instead of searching the schedule (profiler runs)")
     p.add_argument("--mg-sweep", action="store_true",
                    help="also sweep the preconditioner key (none, mg001111V, mg111111V, mg111111W)")
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
@@ -421,7 +423,11 @@ def main():
     U0 = U.clone()
     c0.close()
     # preconditioner schedule (smoothing counts / cycle) and launch shapes from the autotuner
-    ctx, tiles = autotune.tuned_schedule_context(*make_args(w, 32), U0, w.dt, w.scheme)
+    if args.schedule:
+        ctx, tiles = autotune.tuned_context(*make_args(w, 32, mg_key=args.schedule), U0)
+        tiles = dict(tiles, mg_key=args.schedule, sigma_fv=1.0, sigma_dg=1.0, schedule_trials_ms={})
+    else:
+        ctx, tiles = autotune.tuned_schedule_context(*make_args(w, 32), U0, w.dt, w.scheme)
     n0 = P.jfnk.launch_count()
     with Clocks(local) as clk:
         ms, stats = time_steps(ctx, U, w, args.steps, args.warmup, dist, flush)

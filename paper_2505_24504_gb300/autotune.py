@@ -75,8 +75,8 @@ def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CAC
     return ctx, dict(entry, cached=False)
 
 
-SCHEDULES = ("mg111111V", "mg112211V", "mg113311V", "mg112222V", "mg122211V", "mg001111V", "mg002211V",
-             "mg112212V")
+SCHEDULES = ("mg111111V", "mg112211V", "mg122211V", "mg132211V", "mg123311V", "mg222211V", "mg133311V",
+             "mg122222V", "mg001111V", "mg112222V")
 SIGMA_FV = (0.7, 0.85, 1.0, 1.15)
 SIGMA_DG = (0.7, 1.0, 1.3)
 
