@@ -497,6 +497,18 @@ def main():
               "second_gram_schmidt_passes": stp.reorth}
     ctx_p.close()
 
+    # ---- BF16 numerics on the coarsest FV level (precond_prec = 16), same schedule ----
+    c16, _ = autotune.tuned_context(*make_args(w, 16, mg_key=tiles["mg_key"], sigma_fv=tiles["sigma_fv"],
+                                               sigma_dg=tiles["sigma_dg"]), U0)
+    U16 = U0.clone()
+    U32 = U0.clone()
+    ms16, st16 = time_steps(c16, U16, w, 2, 1, None, flush)
+    _, _ = time_steps(ctx, U32, w, 2, 1, None, flush)
+    bf16 = {"steps_per_s": 2 / (ms16 / 1e3), "gmres_per_step": sum(x["gmres_its"] for x in st16) / 2,
+            "rel_diff_vs_fp32_form": float(torch.linalg.norm(U16 - U32) / torch.linalg.norm(U32 - U0)),
+            "note": "relative to the 3-step state change; both converge to the 1e-8 Newton tolerance"}
+    c16.close()
+
     # ---- the plain FP64 single-instance form ----------------------------------
     U64 = U0.clone()
     kp = args.plain_steps or max(2, args.steps // 3)
@@ -514,6 +526,7 @@ def main():
                        "ms_per_step": ms64 / kp},
         "iterations_per_step": {"newton": newton, "gmres": gmres},
         "phases_per_step": phases,
+        "bf16_coarsest": bf16,
         "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
                    "newton_tol": w.newton_tol, "mg_key": tiles["mg_key"], "fv_levels": w.fv_levels,
                    "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",

@@ -18,6 +18,8 @@
 //             in one CUDA graph.
 #include <string.h>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace {
@@ -76,6 +78,13 @@ template <> struct FLoad<TL32, 2> {
     }
 };
 enum { FV_RES = 0, FV_SMOOTH = 1, FV_DEFECT = 2 };
+
+// BF16 storage numerics on the coarsest level (precond_prec = 16): values are
+// rounded to bfloat16 whenever they are written there
+template <class S>
+JF_D S store_round(S v, int bf16) {
+    return bf16 ? (S)__bfloat162float(__float2bfloat16_rn((float)v)) : v;
+}
 
 template <class T> struct SOf;
 template <> struct SOf<D64> { typedef double type; };
@@ -169,7 +178,8 @@ JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, 
 template <class T, int IN, int MODE, bool VISC>
 __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
-                                            const double *fu, double adt, typename SOf<T>::type *out) {
+                                            const double *fu, double adt, typename SOf<T>::type *out,
+                                            int bf16 = 0) {
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
     if (IN != 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
             const S x = (S)ld.dir(v, c, I, Jz);
             const S gx = gprime_of<T, IN, S>(ld, x, f[v], fu, gi, adt, eps);
             if (MODE == FV_SMOOTH)
-                out[gi] = x + dtau[c] * (b[gi] - gx);
+                out[gi] = store_round<S>(x + dtau[c] * (b[gi] - gx), bf16);
             else
                 out[gi] = gx - b[gi];
         }
@@ -206,7 +216,7 @@ template <class T, int IN, bool VISC>
 __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *b,
                                                             const double *fu, double adt, int fac,
                                                             typename SOf<T>::type *bc, typename SOf<T>::type *xc,
-                                                            const typename SOf<T>::type *dtau_c) {
+                                                            const typename SOf<T>::type *dtau_c, int bf16) {
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
     if (IN != 2) load_pt(&spt, K.pt);
@@ -236,9 +246,9 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     const S inv = (S)1 / (S)(fac * fac);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        const S bv = acc[v] * inv;
+        const S bv = store_round<S>(acc[v] * inv, bf16);
         bc[(size_t)v * nc + cc] = bv;
-        if (xc) xc[(size_t)v * nc + cc] = dtau_c[cc] * bv;
+        if (xc) xc[(size_t)v * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
     }
 }
 
@@ -480,7 +490,7 @@ __global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
 // R plus the coarse level's first pseudo-time step from zero: b_c = R r and,
 // when x_c is given, x_c = dtau_c b_c
 template <class S>
-__global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc, const S *dtau_c) {
+__global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc, const S *dtau_c, int bf16 = 0) {
     const int NXc = NXf / fac, NZc = NZf / fac;
     const size_t nc = (size_t)NXc * NZc;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -492,9 +502,9 @@ __global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc
     S acc = 0;
     for (int jj = 0; jj < fac; ++jj)
         for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
-    const S bv = acc / (S)(fac * fac);
+    const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
     bc[t] = bv;
-    if (xc) xc[t] = dtau_c[c] * bv;
+    if (xc) xc[t] = store_round<S>(dtau_c[c] * bv, bf16);
 }
 
 // x = (zero ? 0 : x) - P v
@@ -690,9 +700,10 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     FLoad<TL32, 2> ld{(const float *)L.u, x, n1};
     const float *dt = (const float *)L.dtau;
     const double adt = c->mg_adt;
+    const int bf = (c->prec == 16 && l == c->nlev - 1) ? 1 : 0;   // BF16 coarsest level
     if (mode == FV_SMOOTH) {
-        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
-        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out, bf); jf_launched(); }
+        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out, bf); jf_launched(); }
     } else {
         if (visc) { k_fv<TL32, 2, FV_DEFECT, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
         else { k_fv<TL32, 2, FV_DEFECT, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
@@ -721,19 +732,20 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
         if (visc)
             k_fv_defect_restrict<D64, 1, true><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
                                                                 c->mg_adt, L.fac, (double *)bc, (double *)xc,
-                                                                (const double *)dtc);
+                                                                (const double *)dtc, 0);
         else
             k_fv_defect_restrict<D64, 1, false><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
                                                                  c->mg_adt, L.fac, (double *)bc, (double *)xc,
-                                                                 (const double *)dtc);
+                                                                 (const double *)dtc, 0);
     } else {
         FLoad<TL32, 2> ld{(const float *)L.u, (const float *)x, n1};
+        const int bf = (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0;   // BF16 coarsest level
         if (visc)
             k_fv_defect_restrict<TL32, 2, true><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
-                                                                 (float *)bc, (float *)xc, (const float *)dtc);
+                                                                 (float *)bc, (float *)xc, (const float *)dtc, bf);
         else
             k_fv_defect_restrict<TL32, 2, false><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
-                                                                  (float *)bc, (float *)xc, (const float *)dtc);
+                                                                  (float *)bc, (float *)xc, (const float *)dtc, bf);
     }
     jf_launched();
     JF_CK(cudaGetLastError());
@@ -786,7 +798,8 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
             jf_launched();
             k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
-                                                           fuse ? (S *)C.x : nullptr, (const S *)C.dtau);
+                                                           fuse ? (S *)C.x : nullptr, (const S *)C.dtau,
+                                                           (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0);
             jf_launched();
         } else {
             // defect and restriction (and the coarse first step) in one pass
@@ -965,7 +978,9 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
             if (c->prec == 64)
                 k_restrict<double><<<nblk(L.n, 256), 256, 0, s>>>((const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
             else
-                k_restrict<float><<<nblk(L.n, 256), 256, 0, s>>>((const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u);
+                k_restrict_b<float><<<nblk(L.n, 256), 256, 0, s>>>((const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u,
+                                                                   nullptr, nullptr,
+                                                                   (c->prec == 16 && l == c->nlev - 1) ? 1 : 0);
             jf_launched();
         }
         if (c->prec == 64) {

@@ -251,7 +251,7 @@ def test_implicit_step_unpreconditioned_parity(prec):
     assert st.gmres_its > 0
 
 
-@pytest.mark.parametrize("prec", [32])
+@pytest.mark.parametrize("prec", [32, 16])
 def test_implicit_step_fp32_preconditioner_same_answer(case, prec):
     # the preconditioner changes the iteration, not the converged answer
     w, _, dg = case
