@@ -77,7 +77,9 @@ typedef struct {
  *  precond_prec 64: preconditioner in FP64 with finite-difference products
  *               exactly as the paper; 32: preconditioner (DG smoothing,
  *               transfers, all FV levels) in FP32 with exact tangent-linear
- *               products; 16: as 32 with the coarsest FV level stored in bf16.
+ *               products; 16: as 32 with every vector written on the coarsest
+ *               FV level (state, iterate, right-hand side) rounded to bfloat16
+ *               (the numerics of bf16 storage; arithmetic stays FP32).
  *               The Newton residual, the outer FD Jv, the background
  *               subtraction and GMRES stay FP64 in every mode.
  *  sigma_fv, sigma_dg  pseudo-time CFL factors of the smoothers (Sec. 3.5).
