@@ -324,7 +324,7 @@ def whole_job_rate(units_per_rank, ms_max, world):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None):
+def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None, mg_key=None):
     """The FP64 oracle as it stands on the host cores: one Newton iteration of
     the first SDIRK2 stage (residual, linearisation, GMRES iterations equal to
     the workload's mean per Newton iteration).  Returns (seconds per step
@@ -342,7 +342,7 @@ def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None):
     its = budget_its or max(1, int(round(gmres_per_step / max(newton_per_step, 1))))
     t0 = time.perf_counter()
     G, fU = dg.G(U, adt, U)
-    mg = Multigrid(dg, w.fv_levels, w.mg_key)
+    mg = Multigrid(dg, w.fv_levels, mg_key or w.mg_key)
     mg.linearize(U, adt, fU)
     t1 = time.perf_counter()
     A = lambda y: dg.jv(U, fU, y, adt)
@@ -351,9 +351,9 @@ def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None):
     t_newton = t1 - t0
     t_it = (t2 - t1) / max(done, 1)
     per_step = newton_per_step * t_newton + gmres_per_step * t_it
-    desc = (f"oracle (numpy FP64, 1 thread): 1 residual + linearisation + {done} preconditioned FGMRES "
-            f"iterations of workload 2's first Newton step, scaled to {newton_per_step} Newton / "
-            f"{gmres_per_step} GMRES iterations per SDIRK2 step")
+    desc = (f"oracle (numpy FP64, 1 thread, {mg_key or w.mg_key}): 1 residual + linearisation + {done} "
+            f"preconditioned FGMRES iterations of workload 2's first Newton step, scaled to "
+            f"{newton_per_step} Newton / {gmres_per_step} GMRES iterations per SDIRK2 step")
     return per_step, desc, t2 - t0
 
 
@@ -553,7 +553,7 @@ def main():
         line["serving"] = run_serving(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        per_step, desc, _ = oracle_sample(w, int(round(newton)), int(round(gmres)))
+        per_step, desc, _ = oracle_sample(w, int(round(newton)), int(round(gmres)), mg_key=tiles["mg_key"])
         line["cpu_baseline"] = {"value": 1.0 / per_step, "unit": "implicit steps/s", "cores": 1,
                                 "kind": "oracle", "sample": desc}
     if rank == 0:

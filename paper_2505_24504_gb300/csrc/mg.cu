@@ -794,9 +794,15 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     if (l < c->nlev - 1) {
         FVLev &C = c->lev[l + 1];
         const bool fuse = c->mid_pre >= 1;
-        if (zero) {
-            k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
-            jf_launched();
+        if (zero || c->prec == 64) {
+            // FP64: separate defect and restriction (one thread per fine cell keeps the
+            // FP64-bound defect kernel occupied)
+            if (zero) {
+                k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
+                jf_launched();
+            } else {
+                JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
+            }
             k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
                                                            fuse ? (S *)C.x : nullptr, (const S *)C.dtau,
                                                            (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0);
