@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--ensemble-steps", type=int, default=2)
     p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
     p.add_argument("--viscous-steps", type=int, default=3, help="timed steps of the viscous workload (0: skip)")
+    p.add_argument("--igw-steps", type=int, default=5, help="timed steps of the inertia gravity workload (0: skip)")
     p.add_argument("--schedule", default=None, metavar="KEY",
                    help="use this mg key instead of searching the schedule (profiler runs)")
     p.add_argument("--mg-sweep", action="store_true",
@@ -124,7 +125,7 @@ class Clocks:
 def make_args(w, prec, **kw):
     import paper_2505_24504_gb300 as P
     g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
-    ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
+    ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, w.ubg, 0.0, w.N_bv)
     kwargs = dict(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol, precond_prec=prec)
     kwargs.update(kw)
     return g, w.k, ph, P.Opts.defaults(**kwargs)
@@ -258,10 +259,23 @@ def run_serving(seconds, rate=200.0):
 
 def run_viscous(steps):
     """Viscous density current (mu = 75 m^2/s, Q2 256x32, SDIRK2, dt = 1 s), FP32 preconditioner."""
+    return run_case(synth.DENSITY_CURRENT_Q2_256x32, steps)
+
+
+def run_inertia_gravity(steps):
+    """Inertia gravity wave (constant N, mean flow, periodic x; Q3 80x3, SDIRK2, dt = 25 s),
+    FP32 preconditioner, with the interpolation transfer and with the L2 projection."""
+    w = synth.INERTIA_GRAVITY_Q3_80x3
+    out = run_case(w, steps)
+    out["transfer_l2"] = {k: v for k, v in run_case(w, steps, transfer_l2=1).items() if k != "workload"}
+    return out
+
+
+def run_case(w, steps, **opt):
+    """Timed SDIRK2 steps of a secondary workload with tuned launch tiles."""
     import torch
     from paper_2505_24504_gb300 import autotune
-    w = synth.DENSITY_CURRENT_Q2_256x32
-    c0 = make_context(w, 32)
+    c0 = make_context(w, 32, **opt)
     U = initial_state(c0, w)
     ctx, _ = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U)
     c0.close()
@@ -545,6 +559,8 @@ def main():
     ctx64.close()
     if args.viscous_steps > 0:
         line["viscous"] = run_viscous(args.viscous_steps)
+    if args.igw_steps > 0:
+        line["inertia_gravity"] = run_inertia_gravity(args.igw_steps)
     if args.mg_sweep:
         line["mg_sweep"] = run_mg_sweep()
     if args.ensemble > 0:

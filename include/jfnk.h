@@ -59,11 +59,15 @@ typedef struct {
  * (mu = 0: Euler).  background 0: isentropic atmosphere theta = theta0,
  * T = theta0 - g z / c_p, p = p0 (T/theta0)^(c_p/R) (Sec. 4.2, 4.3);
  * background 1: uniform state rho = p0/(R theta0), theta = theta0, wind
- * (ubg, wbg) (meant for g = 0). */
+ * (ubg, wbg) (meant for g = 0); background 2: constant Brunt-Vaisala
+ * frequency N_bv with surface temperature theta0 and mean flow ubg (Sec. 4.1):
+ * theta = theta0 exp(z/H), T = theta0 (alpha - (alpha-1) exp(z/H)),
+ * p = p0 exp(c_p/R (ln(T/theta0) - z/H)), H = g/N^2, alpha = g H/(c_p theta0). */
 typedef struct {
     double cp, cv, g, p0, theta0, mu;
     int background;
     double ubg, wbg;
+    double N_bv;
 } jfnk_physics;
 
 /* Solver options.  Defaults (jfnk_default_opts) follow Sec. 3.1 and Sec. 4:
@@ -74,6 +78,9 @@ typedef struct {
  *               steps, cycle V or W.  "" disables the preconditioner.
  *  fv_levels    number of FV levels (subgrid first, then agglomeration).
  *  massfix      1: transfer with the mass fix of eq. (transfer-mass-fix).
+ *  transfer_l2  1: transfer by L2 projection onto the subcells (subcell averages
+ *               of the DG polynomial, mass conservative, no mass fix) and its
+ *               inverse, instead of interpolation at the subcell centres.
  *  precond_prec 64: preconditioner in FP64 with finite-difference products
  *               exactly as the paper; 32: preconditioner (DG smoothing,
  *               transfers, all FV levels) in FP32 with exact tangent-linear
@@ -97,6 +104,7 @@ typedef struct {
     char mg_key[16];
     int fv_levels;
     int massfix;
+    int transfer_l2;
     int precond_prec;
     double sigma_fv, sigma_dg, c_ip;
     int use_graphs;

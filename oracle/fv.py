@@ -160,12 +160,14 @@ def prolong(v, fac):
 
 
 class Transfer:
-    """T^mf (DG -> FV subgrid) and its inverse with mass fix."""
+    """T^mf (DG -> FV subgrid) and its inverse with mass fix; with l2=True the L2
+    projection onto the subcells (mass conservative, no mass fix) and its inverse."""
 
-    def __init__(self, dg: DG):
+    def __init__(self, dg: DG, l2=False):
         self.dg = dg
         self.t = dg.t
         self.area = dg.hx * dg.hz
+        self.l2 = l2
 
     def _mass_dg(self, u):
         # exact integral of the DG polynomial per element and variable
@@ -179,18 +181,18 @@ class Transfer:
         """T^mf_E u = T_E u - (m_E(T_E u) - m_E(u))/|E| (eq. transfer-mass-fix), as an
         FV array (4, nz(k+1), nx(k+1)) with subcell (j, i) of element (ez, ex) at
         row ez(k+1)+j, column ex(k+1)+i."""
-        V = self.t.V
+        V = self.t.P if self.l2 else self.t.V
         Tu = np.einsum('jb,ia,vzxba->vzxji', V, V, u)
-        if massfix:
+        if massfix and not self.l2:
             Tu = Tu - ((self._mass_fv(Tu) - self._mass_dg(u)) / self.area)[..., None, None]
         return self._blocks_to_grid(Tu)
 
     def to_dg(self, v, massfix=True):
         """Inverse interpolation then mass fix: T^-1 v - (m_E(T^-1 v) - m_E(v))/|E|."""
-        Vi = self.t.Vinv
+        Vi = self.t.Pinv if self.l2 else self.t.Vinv
         vb = self._grid_to_blocks(v)
         u = np.einsum('bj,ai,vzxji->vzxba', Vi, Vi, vb)
-        if massfix:
+        if massfix and not self.l2:
             u = u - ((self._mass_dg(u) - self._mass_fv(vb)) / self.area)[..., None, None]
         return u
 
@@ -208,14 +210,14 @@ class Multigrid:
     """Q^-1 = T^-1 q^-1 T with DG pre/post smoothing (Sec. 3.2-3.5)."""
 
     def __init__(self, dg: DG, levels: int, mg_key="mg111111V", sigma_fv=1.0, sigma_dg=1.0,
-                 massfix=True):
+                 massfix=True, l2=False):
         self.dg = dg
         self.key = parse_mg_key(mg_key)
         sizes, facs = hierarchy(dg.nx, dg.nz, dg.k, levels)
         self.sizes, self.facs = sizes, facs
         # self.levels[0] is the finest grid
         self.levels = [FVLevel(X, Z, dg.x0, dg.x1, dg.z0, dg.z1, dg.ph, dg.px) for X, Z in sizes]
-        self.T = Transfer(dg)
+        self.T = Transfer(dg, l2=l2)
         self.sigma_fv, self.sigma_dg = sigma_fv, sigma_dg
         self.massfix = massfix
         self.stats = dict(dg_calls=0, fv_calls=[0] * len(sizes))

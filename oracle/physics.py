@@ -10,7 +10,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-ISENTROPIC, UNIFORM = 0, 1
+ISENTROPIC, UNIFORM, CONST_N = 0, 1, 2
 
 
 @dataclass
@@ -22,8 +22,9 @@ class Physics:
     theta0: float = 300.0
     mu: float = 0.0            # kinematic viscosity, F_v = mu rho (0, grad u, grad w, grad theta)
     background: int = ISENTROPIC
-    ubg: float = 0.0           # uniform background velocity (UNIFORM only)
+    ubg: float = 0.0           # background wind: UNIFORM (ubg, wbg); CONST_N mean flow ubg
     wbg: float = 0.0
+    N_bv: float = 0.01         # Brunt-Vaisala frequency (CONST_N)
     convective: bool = True    # test aid: False drops F_c and H_c (pure SIPG diffusion)
 
     @property
@@ -68,9 +69,35 @@ def background(z, ph: Physics):
         U[1] = rho * ph.ubg
         U[2] = rho * ph.wbg
         U[3] = rho * ph.theta0
+    elif ph.background == CONST_N:
+        # Sec. 4.1: theta = T0 exp(z/H), T = T0 (alpha - (alpha-1) exp(z/H)),
+        # p = p0 exp(c_p/R (ln(T/T0) - z/H)), H = g/N^2, alpha = g H / (c_p T0); wind ubg
+        p, th, T, H, alpha = _const_n(z, ph)
+        rho = p / (R * T)
+        ez = np.exp(z / H)
+        dT = -ph.theta0 * (alpha - 1.0) * ez / H
+        dp = -rho * ph.g
+        drho = (dp * T - p * dT) / (R * T * T)
+        dth = th / H
+        U[0] = rho
+        U[1] = rho * ph.ubg
+        U[3] = rho * th
+        dU[0] = drho
+        dU[1] = drho * ph.ubg
+        dU[3] = drho * th + rho * dth
     else:
         raise ValueError("unknown background")
     return U, dU
+
+
+def _const_n(z, ph: Physics):
+    H = ph.g / ph.N_bv ** 2
+    alpha = ph.g * H / (ph.cp * ph.theta0)
+    ez = np.exp(z / H)
+    th = ph.theta0 * ez
+    T = ph.theta0 * (alpha - (alpha - 1.0) * ez)
+    p = ph.p0 * np.exp(ph.cp / ph.R * (np.log(T / ph.theta0) - z / H))
+    return p, th, T, H, alpha
 
 
 def background_pressure_theta(z, ph: Physics):
@@ -81,6 +108,9 @@ def background_pressure_theta(z, ph: Physics):
         T = ph.theta0 - z * ph.g / ph.cp
         p = ph.p0 * (T / ph.theta0) ** (ph.cp / R)
         return p, np.full_like(z, ph.theta0), np.zeros_like(z), np.zeros_like(z)
+    if ph.background == CONST_N:
+        p, th, _, _, _ = _const_n(z, ph)
+        return p, th, np.full_like(z, ph.ubg), np.zeros_like(z)
     rho = ph.p0 / (R * ph.theta0)
     p = pressure(rho * ph.theta0 * np.ones_like(z), ph)
     return p, np.full_like(z, ph.theta0), np.full_like(z, ph.ubg), np.full_like(z, ph.wbg)

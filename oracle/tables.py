@@ -65,6 +65,23 @@ def midpoint_weights(k: int):
     return G, np.linalg.solve(A, rhs)
 
 
+def subcell_averages(nodes, k):
+    """P[i, a] = mean of l_a over subcell i of [-1,1] (k+1 equal subcells): the L2
+    projection of the DG polynomial onto the FV subcells (Sec. 3.2.1)."""
+    from numpy.polynomial import polynomial as Pn
+    nodes = np.asarray(nodes, dtype=np.float64)
+    n = len(nodes)
+    edges = -1.0 + 2.0 * np.arange(n + 1) / n
+    P = np.zeros((n, n))
+    for a in range(n):
+        others = np.delete(nodes, a)
+        coef = Pn.polyfromroots(others) / np.prod(nodes[a] - others)   # l_a in monomials
+        anti = Pn.polyint(coef)
+        for i in range(n):
+            P[i, a] = (Pn.polyval(edges[i + 1], anti) - Pn.polyval(edges[i], anti)) / (edges[i + 1] - edges[i])
+    return P
+
+
 class Tables:
     """All 1D tables for order k."""
 
@@ -85,3 +102,6 @@ class Tables:
         self.Vinv = np.linalg.inv(self.V)
         # modified Newton-Cotes weights on [0,1] at (2i+1)/(2(k+1))
         self.G01, self.omega = midpoint_weights(k)
+        # L2 projection onto the subcells (subcell averages) and its inverse
+        self.P = subcell_averages(self.xi, k)
+        self.Pinv = np.linalg.inv(self.P)

@@ -13,6 +13,7 @@ void jf_build_tables(int k, DGTab *T);
 void jf_build_powtab(double gamma, PowTab *P);
 void jf_background(const jfnk_physics *ph, double z, double U[4], double dU[4]);
 double jf_insert_coef(const jfnk_physics *ph, double z);
+double jf_background_theta(const jfnk_physics *ph, double z);
 
 unsigned long long g_jf_launches = 0;
 std::mutex g_jf_device_mu;
@@ -105,7 +106,8 @@ int check_args(const jfnk_grid *g, int k, const jfnk_physics *p) {
     if (k < 1 || k > 4) return JFNK_EINVAL;
     if (g->nx < 1 || g->nz < 1 || !(g->x1 > g->x0) || !(g->z1 > g->z0)) return JFNK_EINVAL;
     if (!(p->cp > p->cv) || !(p->cv > 0) || !(p->p0 > 0) || !(p->theta0 > 0) || p->mu < 0) return JFNK_EINVAL;
-    if (p->background != 0 && p->background != 1) return JFNK_EINVAL;
+    if (p->background < 0 || p->background > 2) return JFNK_EINVAL;
+    if (p->background == 2 && !(p->N_bv > 0)) return JFNK_EINVAL;
     return JFNK_OK;
 }
 
@@ -183,6 +185,7 @@ void jfnk_default_opts(jfnk_opts *o) {
     strcpy(o->mg_key, "mg111111V");
     o->fv_levels = 3;
     o->massfix = 1;
+    o->transfer_l2 = 0;
     o->precond_prec = 64;
     o->sigma_fv = 1.0;
     o->sigma_dg = 1.0;
@@ -339,7 +342,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
                     dub[v * nrow + J] = dU[v];
                 }
                 pr[J] = jf_insert_coef(ph, z);
-                tr[J] = ph->theta0;
+                tr[J] = jf_background_theta(ph, z);
             }
         for (int j = 0; j < (int)nf; ++j) {
             double U[4], dU[4];
@@ -515,7 +518,7 @@ int jfnk_node_coords(const jfnk_ctx *c, double *x, double *z) {
 int jfnk_init_state(jfnk_ctx *c, const double *thp, double *U, void *stream) {
     if (!c || !thp || !U) return JFNK_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const double ubg = c->phys.background == 1 ? c->phys.ubg : 0.0;
+    const double ubg = c->phys.background >= 1 ? c->phys.ubg : 0.0;
     const double wbg = c->phys.background == 1 ? c->phys.wbg : 0.0;
     k_init_state<<<(unsigned)((c->npt + 255) / 256), 256, 0, s>>>(thp, c->prow, c->theta_row, c->ubv, ubg, wbg,
                                                                    c->grid.nx, c->grid.nz, c->np1, U); jf_launched();

@@ -23,6 +23,8 @@ struct DGTab {
     double lpw[5], lmw[5], dlpw[5], dlmw[5];   // the same divided by w_a
     double V[5][5];      // V[i][a] = l_a(c_i), subcell centre c_i = -1 + (2i+1)/(k+1)
     double Vinv[5][5];
+    double P[5][5];      // P[i][a] = mean of l_a over subcell i (L2 projection)
+    double Pinv[5][5];
     double om[5];        // modified Newton-Cotes weights on [0,1] at the subcell centres
 };
 

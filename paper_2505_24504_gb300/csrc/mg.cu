@@ -617,6 +617,13 @@ TK make_tk(jfnk_ctx *c) {
     K.NX = c->lev[0].NX;
     K.NZ = c->lev[0].NZ;
     K.tab = c->tab;
+    if (c->opts.transfer_l2) {   // L2 projection: subcell averages and their inverse
+        for (int i = 0; i < 5; ++i)
+            for (int a = 0; a < 5; ++a) {
+                K.tab.V[i][a] = c->tab.P[i][a];
+                K.tab.Vinv[i][a] = c->tab.Pinv[i][a];
+            }
+    }
     return K;
 }
 
@@ -627,10 +634,10 @@ int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s, So *x0 = nullptr, con
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
-        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
-        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
-        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix, x0, dtau0); jf_launched(); break;
+        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -644,10 +651,10 @@ int to_dg(jfnk_ctx *c, const Si *v, So *u, int acc, cudaStream_t s) {
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: k_to_dg<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
-        case 3: k_to_dg<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
-        case 4: k_to_dg<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
-        case 5: k_to_dg<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix, acc); jf_launched(); break;
+        case 2: k_to_dg<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 3: k_to_dg<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 4: k_to_dg<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 5: k_to_dg<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());

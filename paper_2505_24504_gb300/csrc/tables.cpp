@@ -92,6 +92,8 @@ static void invert(int n, LD A[5][5], LD Ai[5][5]) {
         for (int j = 0; j < n; ++j) Ai[i][j] = M[i][j + n];
 }
 
+static void subcell_average_table(const LD *x, int n, LD P[5][5]);
+
 void jf_build_tables(int k, DGTab *T) {
     memset(T, 0, sizeof(*T));
     const int n = k + 1;
@@ -138,10 +140,15 @@ void jf_build_tables(int k, DGTab *T) {
         for (int a = 0; a < n; ++a) V[i][a] = lag(x, n, a, ci);
     }
     invert(n, V, Vi);
+    LD Pa[5][5], Pi[5][5];
+    subcell_average_table(x, n, Pa);
+    invert(n, Pa, Pi);
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < n; ++a) {
             T->V[i][a] = (double)V[i][a];
             T->Vinv[i][a] = (double)Vi[i][a];
+            T->P[i][a] = (double)Pa[i][a];
+            T->Pinv[i][a] = (double)Pi[i][a];
         }
     // midpoint weights: integral over [0,1] of the Lagrange polynomial through
     // the centres G_j = (2j+1)/(2n), expanded in monomials
@@ -164,6 +171,32 @@ void jf_build_tables(int k, DGTab *T) {
         LD integ = 0.0L;
         for (int m = 0; m <= deg; ++m) integ += coef[m] / (m + 1);
         T->om[i] = (double)integ;
+    }
+}
+
+// P[i][a] = mean of l_a over subcell i of [-1,1]: the L2 projection onto the
+// subcells (Sec. 3.2.1), from the monomial expansion of l_a integrated exactly.
+static void subcell_average_table(const LD *x, int n, LD P[5][5]) {
+    for (int a = 0; a < n; ++a) {
+        LD coef[6] = {1.0L, 0, 0, 0, 0, 0};
+        int deg = 0;
+        for (int b = 0; b < n; ++b) {
+            if (b == a) continue;
+            const LD s = 1.0L / (x[a] - x[b]);
+            LD nc[6] = {0, 0, 0, 0, 0, 0};
+            for (int m = 0; m <= deg; ++m) {
+                nc[m + 1] += coef[m] * s;
+                nc[m] -= coef[m] * x[b] * s;
+            }
+            ++deg;
+            for (int m = 0; m <= deg; ++m) coef[m] = nc[m];
+        }
+        for (int i = 0; i < n; ++i) {
+            const LD lo = -1.0L + 2.0L * i / n, hi = -1.0L + 2.0L * (i + 1) / n;
+            LD acc = 0.0L;
+            for (int m = 0; m <= deg; ++m) acc += coef[m] * (powl(hi, m + 1) - powl(lo, m + 1)) / (m + 1);
+            P[i][a] = acc / (hi - lo);
+        }
     }
 }
 
@@ -201,6 +234,24 @@ void jf_background(const jfnk_physics *ph, double z, double U[4], double dU[4]) 
         U[3] = (double)(rho * th);
         dU[0] = (double)drho;
         dU[3] = (double)(drho * th);
+    } else if (ph->background == 2) {
+        const LD gg = ph->g, th0 = ph->theta0;
+        const LD H = gg / ((LD)ph->N_bv * ph->N_bv);
+        const LD alpha = gg * H / ((LD)ph->cp * th0);
+        const LD ez = expl((LD)z / H);
+        const LD th = th0 * ez;
+        const LD T = th0 * (alpha - (alpha - 1.0L) * ez);
+        const LD p = ph->p0 * expl((LD)ph->cp / R * (logl(T / th0) - (LD)z / H));
+        const LD rho = p / (R * T);
+        const LD dT = -th0 * (alpha - 1.0L) * ez / H;
+        const LD dp = -rho * gg;
+        const LD drho = (dp * T - p * dT) / (R * T * T);
+        U[0] = (double)rho;
+        U[1] = (double)(rho * ph->ubg);
+        U[3] = (double)(rho * th);
+        dU[0] = (double)drho;
+        dU[1] = (double)(drho * ph->ubg);
+        dU[3] = (double)(drho * th + rho * th / H);
     } else {
         const LD rho = (LD)ph->p0 / (R * ph->theta0);
         U[0] = (double)rho;
@@ -208,6 +259,15 @@ void jf_background(const jfnk_physics *ph, double z, double U[4], double dU[4]) 
         U[2] = (double)(rho * ph->wbg);
         U[3] = (double)(rho * ph->theta0);
     }
+}
+
+// theta~ of the environmental atmosphere at height z (insertion, eq. add-perturbation)
+double jf_background_theta(const jfnk_physics *ph, double z) {
+    if (ph->background == 2) {
+        const LD H = (LD)ph->g / ((LD)ph->N_bv * ph->N_bv);
+        return (double)((LD)ph->theta0 * expl((LD)z / H));
+    }
+    return ph->theta0;
 }
 
 // Coefficient p0^(R/c_p) p~^(1/gamma) / R of the pressure-preserving insertion
@@ -219,6 +279,11 @@ double jf_insert_coef(const jfnk_physics *ph, double z) {
     if (ph->background == 0) {
         const LD T = (LD)ph->theta0 - (LD)z * ph->g / ph->cp;
         p = ph->p0 * powl(T / ph->theta0, (LD)ph->cp / R);
+    } else if (ph->background == 2) {
+        const LD H = (LD)ph->g / ((LD)ph->N_bv * ph->N_bv);
+        const LD alpha = (LD)ph->g * H / ((LD)ph->cp * ph->theta0);
+        const LD T = (LD)ph->theta0 * (alpha - (alpha - 1.0L) * expl((LD)z / H));
+        p = ph->p0 * expl((LD)ph->cp / R * (logl(T / ph->theta0) - (LD)z / H));
     } else {
         p = ph->p0;   // uniform state rho = p0/(R theta0) has p = p0
     }

@@ -29,14 +29,14 @@ class Grid(C.Structure):
 class Physics(C.Structure):
     _fields_ = [("cp", C.c_double), ("cv", C.c_double), ("g", C.c_double), ("p0", C.c_double),
                 ("theta0", C.c_double), ("mu", C.c_double), ("background", C.c_int),
-                ("ubg", C.c_double), ("wbg", C.c_double)]
+                ("ubg", C.c_double), ("wbg", C.c_double), ("N_bv", C.c_double)]
 
 
 class Opts(C.Structure):
     _fields_ = [("newton_tol", C.c_double), ("newton_max", C.c_int), ("gmres_restart", C.c_int),
                 ("gmres_max", C.c_int), ("ew_gamma", C.c_double), ("ew_alpha", C.c_double),
                 ("ew_eta0", C.c_double), ("ew_eta_max", C.c_double), ("mg_key", C.c_char * 16),
-                ("fv_levels", C.c_int), ("massfix", C.c_int), ("precond_prec", C.c_int),
+                ("fv_levels", C.c_int), ("massfix", C.c_int), ("transfer_l2", C.c_int), ("precond_prec", C.c_int),
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
                 ("tile_fv", C.c_int), ("profile", C.c_int)]

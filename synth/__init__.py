@@ -42,6 +42,20 @@ class Bubble:
 
 
 @dataclass(frozen=True)
+class Wave:
+    """theta'(x,z) = theta_c sin(pi z/Z) / (1 + ((x-xc)/a)^2)  (Sec. 4.1 perturbation)."""
+    theta_c: float
+    xc: float
+    a: float
+    Z: float
+
+    def theta(self, x, z):
+        x = np.asarray(x, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        return self.theta_c * np.sin(np.pi * z / self.Z) / (1.0 + ((x - self.xc) / self.a) ** 2)
+
+
+@dataclass(frozen=True)
 class Workload:
     name: str
     nx: int
@@ -57,7 +71,7 @@ class Workload:
     p0: float
     theta0: float
     mu: float
-    bubble: Bubble
+    bubble: object               # Bubble or Wave: theta'(x, z)
     noise_amp: float = 0.0
     noise_seed: int = 0
     scheme: int = 1              # 0 backward Euler, 1 SDIRK2
@@ -68,7 +82,9 @@ class Workload:
     mg_key: str = "mg111111V"
     newton_tol: float = 1e-8
     periodic_x: bool = False
-    background: int = 0          # 0 isentropic, 1 uniform
+    background: int = 0          # 0 isentropic, 1 uniform, 2 constant Brunt-Vaisala frequency
+    ubg: float = 0.0             # mean flow of the environmental atmosphere (background 1, 2)
+    N_bv: float = 0.01           # Brunt-Vaisala frequency (background 2)
 
     @property
     def n_el(self) -> int:
@@ -136,6 +152,18 @@ DENSITY_CURRENT_Q2_256x32 = Workload(
     nx=256, nz=32, x0=0.0, x1=51200.0, z0=0.0, z1=6400.0, k=2,
     theta0=300.0, mu=75.0, bubble=Bubble(-15.0, 0.0, 3000.0, 4000.0, 2000.0),
     scheme=1, dt_fixed=1.0, steps=20, fv_levels=4, **PHYS_STRAKA)
+
+
+# Workload 4: non-hydrostatic inertia gravity wave (Sec. 4.1): [0,300km]x[0,10km],
+# periodic in x, constant N = 0.01/s, T0 = 250 K, mean flow 20 m/s,
+# theta' = 0.01 K sin(pi z/10km) / (1 + ((x-100km)/5km)^2); Q3 on 80x3 quads
+# (node spacing ~940 m in x), SDIRK2 at dt = 25 s, 3 MG levels.
+INERTIA_GRAVITY_Q3_80x3 = Workload(
+    name="inertia gravity Q3 80x3 (15,360 DOF), SDIRK2, dt=25s",
+    nx=80, nz=3, x0=0.0, x1=300000.0, z0=0.0, z1=10000.0, k=3,
+    theta0=250.0, mu=0.0, bubble=Wave(0.01, 100000.0, 5000.0, 10000.0),
+    scheme=1, dt_fixed=25.0, steps=120, fv_levels=3, periodic_x=True,
+    background=2, ubg=20.0, N_bv=0.01, **PHYS_ROBERT)
 
 
 def scaled(w: Workload, nx: int, nz: int, **kw) -> Workload:

@@ -10,7 +10,7 @@ from oracle.physics import Physics as OPhys
 
 def oracle_physics(w: synth.Workload, **kw):
     return OPhys(cp=w.cp, cv=w.cv, g=w.g, p0=w.p0, theta0=w.theta0, mu=w.mu,
-                 background=w.background, **kw)
+                 background=w.background, ubg=w.ubg, N_bv=w.N_bv, **kw)
 
 
 def oracle_dg(w: synth.Workload, c_ip=2.0):
@@ -20,7 +20,7 @@ def oracle_dg(w: synth.Workload, c_ip=2.0):
 def gpu_context(w: synth.Workload, **opt):
     import paper_2505_24504_gb300 as P
     g = P.Grid(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, int(w.periodic_x))
-    ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, 0.0, 0.0)
+    ph = P.Physics(w.cp, w.cv, w.g, w.p0, w.theta0, w.mu, w.background, w.ubg, 0.0, w.N_bv)
     kw = dict(fv_levels=w.fv_levels, mg_key=w.mg_key, newton_tol=w.newton_tol)
     kw.update(opt)
     return P.Context(g, w.k, ph, P.Opts.defaults(**kw))

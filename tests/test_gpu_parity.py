@@ -24,6 +24,7 @@ def _cases():
         "q3-periodic": synth.scaled(W1, 12, 6, k=3, periodic_x=True, fv_levels=4),
         "visc-q2-24x6": W3S,
         "visc-q3-10x4": synth.scaled(synth.DENSITY_CURRENT_Q2_256x32, 10, 4, k=3, x1=8000.0, fv_levels=3),
+        "igw-q3-20x3": synth.scaled(synth.INERTIA_GRAVITY_Q3_80x3, 20, 3),
     }
 
 
@@ -163,6 +164,22 @@ def test_transfers_parity(case):
     assert rel(to_cpu(back, dg.shape), u) <= 1e-13
 
 
+def test_transfers_l2_parity(case):
+    from oracle.fv import Transfer
+    w, _, dg = case
+    ctx = gpu_context(w, transfer_l2=1)
+    T = Transfer(dg, l2=True)
+    u = perturbed_state(w, dg, seed=21)
+    v = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.transfer_to_fv(to_gpu(u), v)
+    vref = T.to_fv(u)
+    assert rel(to_cpu(v, vref.shape), vref) <= 1e-14
+    back = torch.empty_like(v)
+    ctx.transfer_to_dg(v, back)
+    assert rel(to_cpu(back, dg.shape), T.to_dg(to_cpu(v, vref.shape))) <= 1e-14
+    assert rel(to_cpu(back, dg.shape), u) <= 1e-13
+
+
 def test_fv_residual_parity_every_level(case):
     from oracle.fv import Multigrid
     w, ctx, dg = case
@@ -233,6 +250,34 @@ def test_implicit_step_parity(case, scheme):
     ref = _oracle_step(w, dg, U0, scheme)
     assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
+
+
+@pytest.mark.parametrize("name", ["q3-11x6", "igw-q3-20x3"])
+def test_implicit_step_l2_transfer_parity(name):
+    from oracle.fv import Multigrid
+    from oracle.solver import implicit_step
+    w = _cases()[name]
+    dg = oracle_dg(w)
+    ctx = gpu_context(w, transfer_l2=1)
+    U0 = initial_state(w, dg)
+    U = to_gpu(U0)
+    st = ctx.implicit_step(U, w.dt, scheme=1)
+    assert st.status == 0
+    ref = implicit_step(dg, U0, w.dt, scheme=1, tol=w.newton_tol,
+                        precond=Multigrid(dg, w.fv_levels, w.mg_key, l2=True))
+    got = to_cpu(U, dg.shape)
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
+
+
+def test_inertia_gravity_steady_with_wind_and_periodic():
+    # zero perturbation: the implicit step of the stratified atmosphere with mean
+    # flow leaves U' = 0 exactly (well balanced, periodic x)
+    w = synth.scaled(synth.INERTIA_GRAVITY_Q3_80x3, 20, 3)
+    ctx = gpu_context(w)
+    U = torch.zeros(ctx.N, dtype=torch.float64, device="cuda")
+    st = ctx.implicit_step(U, w.dt, scheme=1)
+    assert st.status == 0
+    assert torch.count_nonzero(U).item() == 0
 
 
 @pytest.mark.parametrize("prec", [64, 32])

@@ -179,3 +179,12 @@ def test_sipg_heat_equation_order(k, order):
             U = implicit_step(dg, U, T / nt, scheme=1, tol=1e-12)
         errs.append(np.sqrt(np.sum(dg.mass_weights() * (U[3] - E(T)) ** 2)))
     assert np.log2(errs[0] / errs[1]) > order
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_well_balanced_bitwise_constant_n_with_wind(k):
+    # Sec. 4.1 environment: constant N, mean flow 20 m/s, periodic in x
+    from oracle.physics import CONST_N
+    ph = Physics(cp=1005.0, cv=717.95, g=9.80665, p0=1e5, theta0=250.0, background=CONST_N, ubg=20.0, N_bv=0.01)
+    dg = DG(6, 3, 0.0, 30000.0, 0.0, 10000.0, k, ph, periodic_x=True)
+    assert np.all(dg.rhs(dg.zeros()) == 0.0)

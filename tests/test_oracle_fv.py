@@ -160,3 +160,31 @@ def test_fv_other_hydrostatic_state_converges_to_balance():
         res.append(np.abs(f[2, 1:-1]).max())
     assert res[0] < 0.01 * ROBERT.g * 0.017
     assert np.log2(res[1] / res[2]) > 1.8
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_l2_transfer_gives_cell_averages_and_conserves_mass(k):
+    # Sec. 3.2.1: the L2 projection onto piecewise constants = subcell averages
+    dg = DG(2, 2, 0, 2000, 0, 2000, k, ROBERT)
+    T = Transfer(dg, l2=True)
+    n1 = k + 1
+    p = lambda x, z: 1 + (x / 2000) ** k + 2 * (z / 2000) ** (k - 1) * (x / 2000)
+    u = np.stack([p(dg.X, dg.Z)] * 4)
+    v = T.to_fv(u)
+    # exact averages of p over each subcell by Gauss-Legendre with k+2 points
+    from oracle.tables import gauss_legendre
+    g, wg = gauss_legendre(k + 2)
+    H = 1000.0 / n1
+    for J in range(2 * n1):
+        for I in range(2 * n1):
+            xs = (I + 0.5 * (1 + g)) * H
+            zs = (J + 0.5 * (1 + g)) * H
+            avg = 0.25 * np.sum(wg[:, None] * wg[None, :] * p(xs[None, :], zs[:, None]))
+            assert abs(v[0, J, I] - avg) <= 1e-12 * abs(avg)
+    ur = synth.random_perturbation(dg.shape[1:], 9)
+    vr = T.to_fv(ur)
+    cell = dg.hx * dg.hz / n1 ** 2
+    for var in range(4):
+        m_dg = np.sum(dg.mass_weights() * ur[var])
+        assert abs(cell * vr[var].sum() - m_dg) <= 1e-13 * np.sum(np.abs(dg.mass_weights() * ur[var]))
+    np.testing.assert_allclose(T.to_dg(vr), ur, atol=1e-11 * np.abs(ur).max())

@@ -117,3 +117,22 @@ def test_uniform_background_constant():
     assert np.all(dU == 0)
     np.testing.assert_allclose(U[1] / U[0], 0.5)
     np.testing.assert_allclose(pressure(U[3], ph), 1.0, rtol=1e-15)
+
+
+def test_constant_n_background_hydrostatic_and_stratified():
+    from oracle.physics import CONST_N
+    ph = Physics(cp=1005.0, cv=717.95, g=9.80665, p0=1e5, theta0=250.0, background=CONST_N, ubg=20.0, N_bv=0.01)
+    z = np.linspace(100, 9900, 40)
+    U, dU = background(z, ph)
+    h = 1e-2
+    Up, _ = background(z + h, ph)
+    Um, _ = background(z - h, ph)
+    dpdz = (pressure(Up[3], ph) - pressure(Um[3], ph)) / (2 * h)
+    np.testing.assert_allclose(dpdz, -U[0] * ph.g, rtol=1e-7)
+    H = ph.g / ph.N_bv ** 2
+    np.testing.assert_allclose(U[3] / U[0], 250.0 * np.exp(z / H), rtol=1e-13)
+    # N^2 = g dln(theta)/dz
+    th = lambda zz: background(zz, ph)[0][3] / background(zz, ph)[0][0]
+    np.testing.assert_allclose(ph.g * (np.log(th(z + h)) - np.log(th(z - h))) / (2 * h), 1e-4, rtol=1e-6)
+    np.testing.assert_allclose(U[1] / U[0], 20.0)
+    np.testing.assert_allclose(dU, (Up - Um) / (2 * h), rtol=1e-6, atol=1e-12)
