@@ -94,8 +94,9 @@ typedef struct {
  *  use_graphs   1 (default): capture one preconditioner application in a CUDA
  *               graph on first use (and again when alpha_dt changes) and replay
  *               it; 0: launch the kernels one by one.  Same results either way.
- *  tile_*       launch shapes (results do not depend on them); jfnk_autotune
- *               picks them by timing. */
+ *  tile_*, fv_split_cells  launch shapes (results do not depend on them, except
+ *               fv_split_cells, which changes the summation order of the FV
+ *               operator at rounding level); jfnk_autotune picks them by timing. */
 typedef struct {
     double newton_tol;
     int newton_max;
@@ -111,6 +112,8 @@ typedef struct {
     int tile_faces;      /* threads per block of the DG face kernel: 64, 128, 256 (0: 128) */
     int tile_volume;     /* elements per DG volume block: 1 = ~64 threads, 2 = ~128 (0: 2) */
     int tile_fv;         /* threads per block of the FV cell kernels: 64, 128, 256 (0: 128) */
+    int fv_split_cells;  /* FV levels with fewer cells than this run four lanes per cell (one
+                            per face), larger levels one thread per cell (0: 65536) */
     int profile;         /* 1: time the phases of implicit_step with CUDA events (jfnk_stats) */
 } jfnk_opts;
 
@@ -270,9 +273,10 @@ int jfnk_time_operator(jfnk_ctx *ctx, int which, const double *U_dev, const doub
 
 /* Autotuner of the launch shapes: times every (tile_faces, tile_volume)
  * pair on `reps` FP64 FD products at state U with direction y (CUDA events on
- * `stream`), and every tile_fv on `reps` preconditioner applications
- * linearised at U (contexts with a preconditioner), keeps the fastest in the
- * context and writes them to best[0..2] (host) and their times in ms to
+ * `stream`), and every (tile_fv, fv_split_cells) pair on `reps` preconditioner
+ * applications linearised at U (contexts with a preconditioner), keeps the
+ * fastest in the context and writes them to best[0..3] = tile_faces,
+ * tile_volume, tile_fv, fv_split_cells (host) and their times in ms to
  * ms[0..1] (host; ms[1] = 0 without a preconditioner).  Results of every
  * call are independent of the shapes; only speed changes. */
 int jfnk_autotune(jfnk_ctx *ctx, const double *U_dev, const double *y_dev, int reps, int *best_host,

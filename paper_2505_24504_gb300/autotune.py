@@ -49,6 +49,7 @@ def apply(opts, entry) -> None:
     opts.tile_faces = int(entry["tile_faces"])
     opts.tile_volume = int(entry["tile_volume"])
     opts.tile_fv = int(entry["tile_fv"])
+    opts.fv_split_cells = int(entry.get("fv_split_cells", 0))
 
 
 def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CACHE, seed: int = 5):

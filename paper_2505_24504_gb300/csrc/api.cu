@@ -194,6 +194,7 @@ void jfnk_default_opts(jfnk_opts *o) {
     o->tile_faces = 128;
     o->tile_volume = 2;
     o->tile_fv = 128;
+    o->fv_split_cells = 0;
 }
 
 const char *jfnk_strerror(int code) {
@@ -474,6 +475,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     c->nb_red = 4096;
     A_(c->partial, 8 * (size_t)c->nb_red * 32);
     A_(c->scal, 8 * (size_t)S_COUNT);
+    A_(c->ticket, 256);
     {
         void *h = nullptr;
         if (cudaMallocHost(&h, 8 * (size_t)S_COUNT) != cudaSuccess) {
@@ -485,7 +487,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
         c->h_pinned = (double *)h;
     }
 #undef A_
-    if (cudaMemset(c->scal, 0, 8 * (size_t)S_COUNT) != cudaSuccess) {
+    if (cudaMemset(c->scal, 0, 8 * (size_t)S_COUNT) != cudaSuccess || cudaMemset(c->ticket, 0, 256) != cudaSuccess) {
         destroy_unlocked(c);
         return JFNK_ECUDA;
     }
@@ -640,6 +642,7 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
     if (!c || !U || !y || !best || !ms || reps < 1) return JFNK_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int keep_f = c->opts.tile_faces, keep_v = c->opts.tile_volume, keep_fv = c->opts.tile_fv;
+    const int keep_sp = c->opts.fv_split_cells;
     jf_invalidate_graphs(c);   // captured graphs hold the old launch shapes
     double best_dg = 1e300;
     int bf = keep_f, bv = keep_v;
@@ -664,7 +667,7 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
     c->opts.tile_faces = bf;
     c->opts.tile_volume = bv;
     double best_mg = 0.0;
-    int bfv = keep_fv;
+    int bfv = keep_fv, bsp = keep_sp;
     if (c->mg_on) {
         cudaEvent_t e0, e1;
         JF_CK(cudaEventCreate(&e0));
@@ -675,8 +678,12 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
         int rc = dg_apply(c, DG_RES, a, s);
         if (!rc) rc = mg_linearize(c, U, 1.0, s);
         best_mg = 1e300;
-        for (int t = 64; t <= 256 && rc == JFNK_OK; t *= 2) {
+        // split thresholds: never, between the level sizes a 2x2 hierarchy gives, always
+        const int sps[5] = {1, 4096, 16384, 65536, 1 << 30};
+        for (int it = 0; it < 15 && rc == JFNK_OK; ++it) {
+            const int t = 64 << (it % 3), sp = sps[it / 3];
             c->opts.tile_fv = t;
+            c->opts.fv_split_cells = sp;
             if (c->mg_graph_valid) {   // the graph holds the old launch shapes
                 cudaGraphExecDestroy(c->mg_graph);
                 c->mg_graph_valid = 0;
@@ -692,6 +699,7 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
             if (m / reps < best_mg) {
                 best_mg = m / reps;
                 bfv = t;
+                bsp = sp;
             }
         }
         cudaEventDestroy(e0);
@@ -702,14 +710,17 @@ int jfnk_autotune(jfnk_ctx *c, const double *U, const double *y, int reps, int *
         }
         if (rc) {
             c->opts.tile_fv = keep_fv;
+            c->opts.fv_split_cells = keep_sp;
             return rc;
         }
     }
     c->opts.tile_fv = bfv;
+    c->opts.fv_split_cells = bsp;
     jf_invalidate_graphs(c);
     best[0] = bf;
     best[1] = bv;
     best[2] = bfv;
+    best[3] = bsp;
     ms[0] = best_dg;
     ms[1] = c->mg_on ? best_mg : 0.0;
     return JFNK_OK;

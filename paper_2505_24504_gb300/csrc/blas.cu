@@ -8,6 +8,13 @@
 // without a host round trip.
 // Multi-dot (classical Gram-Schmidt): one pass over w reads w once for all
 // basis vectors, h_i = V_i . w for i < nv.
+// Single-launch reductions: each block writes its partials, then takes a ticket
+// from a per-context counter; the block that arrives last adds all partials in
+// block order (so the bits do not depend on which block that is), writes the
+// result and resets the counter.  Nothing waits on another block.
+// Gram-Schmidt twice (CGS2) in three passes over the basis: h1 = V^T w; then
+// w1 = w - V h1 fused with h2 = V^T w1 and |w1|^2; then, when the device-side
+// test asks for it, w2 = w1 - V h2 with |w2|^2.
 #include "internal.h"
 
 namespace {
@@ -36,6 +43,244 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;   // valid in thread 0
 }
 
+// true in the block that arrives last at the ticket (after its partials are visible)
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// fixed-order sum of part[0..nb) by one block (valid in thread 0)
+__device__ __forceinline__ double sum_partials(const double *part, int nb) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += RB) acc += __ldcg(part + i);
+    return block_sum(acc);
+}
+
+__device__ __forceinline__ double finish_op(double acc, int op) {
+    if (op == RED_SQRT) return sqrt(acc);
+    if (op == RED_EPS) return acc > 0.0 ? 1.4901161193847656e-08 / sqrt(acc) : 0.0;
+    if (op == RED_EPS32) return acc > 0.0 ? 3.4526698300124393e-04 / sqrt(acc) : 0.0;
+    return acc;
+}
+
+// x . y (op applied) in one launch
+template <class S>
+__global__ void __launch_bounds__(RB) k_dot1(const S *x, const S *y, size_t n, double *part, unsigned *ticket,
+                                             double *out, int op) {
+    double acc = 0.0, acc2 = 0.0;
+    const size_t stride = (size_t)gridDim.x * RB;
+    size_t i = (size_t)blockIdx.x * RB + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        const double a0 = (double)x[i], b0 = (double)y[i];
+        const double a1 = (double)x[i + stride], b1 = (double)y[i + stride];
+        acc = fma(a0, b0, acc);
+        acc2 = fma(a1, b1, acc2);
+    }
+    if (i < n) acc = fma((double)x[i], (double)y[i], acc);
+    acc = block_sum(acc + acc2);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (!last_block(ticket)) return;
+    const double t = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        *out = finish_op(t, op);
+        *ticket = 0u;
+    }
+}
+
+// ---- CGS2 passes (NV basis vectors, two elements per thread and step) -------
+// h[j] = sum over blocks of part[j * nb + b], one warp per vector, fixed order
+template <int NV>
+__device__ __forceinline__ void finish_multi(const double *part, int nb, double *h) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = wid; j < NV; j += RB / 32) {
+        double a = 0.0;
+        for (int b = lane; b < nb; b += 32) a += __ldcg(part + (size_t)j * nb + b);
+        a = warp_sum(a);
+        if (lane == 0) h[j] = a;
+    }
+}
+
+// Warp sums of NV per-lane values at about one FP64 add per value and lane:
+// each butterfly round over lane bit b keeps half of the remaining vectors
+// (lanes with bit b set keep the upper half) and adds the partner's copies, so
+// after log2(P) rounds lane L holds vector L >> (5 - log2 P) summed over its
+// group; the remaining rounds finish the sum within the group.  P = NV rounded
+// up to a power of two (at most 32); returns the value of that vector.
+template <int NV>
+__device__ __forceinline__ double warp_sum_scatter(const double (&a)[NV], int lane) {
+    constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+    constexpr int LP = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;
+    double v[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) v[k] = k < NV ? a[k] : 0.0;
+#pragma unroll
+    for (int r = 0; r < LP; ++r) {
+        const int half = P >> (r + 1);
+        const int bit = 4 - r;
+        const bool hi = (lane >> bit) & 1;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double keep = hi ? v[k + half] : v[k];
+            const double send = hi ? v[k] : v[k + half];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << bit);
+        }
+    }
+    double s = v[0];
+#pragma unroll
+    for (int bit = 4 - LP; bit >= 0; --bit) s += __shfl_xor_sync(0xffffffffu, s, 1 << bit);
+    return s;
+}
+
+// block sums of NV accumulators into part[j * nb + blockIdx.x]
+template <int NV>
+__device__ __forceinline__ void store_multi(const double (&acc)[NV], double *part) {
+    constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+    __shared__ double sw[NV][RB / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double v = warp_sum_scatter<NV>(acc, lane);
+    const int j = lane / (32 / P);
+    if (lane % (32 / P) == 0 && j < NV) sw[j][wid] = v;
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < RB / 32; ++q) r += sw[threadIdx.x][q];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+// pass 1: h = V^T w
+template <int NV>
+__global__ void __launch_bounds__(RB) k_gs_dot(const double *V, size_t ldv, const double *w, size_t n2,
+                                               double *part, unsigned *ticket, double *h) {
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const double2 *Vp[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Vp[j] = reinterpret_cast<const double2 *>(V + (size_t)j * ldv);
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
+        const double2 a = w2[i];
+        double2 v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] = fma(v[j].y, a.y, fma(v[j].x, a.x, acc[j]));
+    }
+    store_multi<NV>(acc, part);
+    if (!last_block(ticket)) return;
+    finish_multi<NV>(part, gridDim.x, h);
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// pass 2: w <- w - V h1, h2 = V^T w, w1sq = |w|^2, flag = (|w1| < |w0|/sqrt(2)),
+// nrm = |w| (final unless the third pass runs)
+template <int NV>
+__global__ void __launch_bounds__(RB) k_gs_update_dot(const double *V, size_t ldv, double *w, size_t n2,
+                                                      const double *h1, double *part, unsigned *ticket,
+                                                      double *h2, double *w1sq, double *nrm, double *flag) {
+    double2 *wv = reinterpret_cast<double2 *>(w);
+    const double2 *Vp[NV];
+    double c[NV], acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        Vp[j] = reinterpret_cast<const double2 *>(V + (size_t)j * ldv);
+        c[j] = -h1[j];
+        acc[j] = 0.0;
+    }
+    double sq = 0.0;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
+        double2 a = wv[i];
+        double2 v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            a.x = fma(c[j], v[j].x, a.x);
+            a.y = fma(c[j], v[j].y, a.y);
+        }
+        wv[i] = a;
+        sq = fma(a.y, a.y, fma(a.x, a.x, sq));
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] = fma(v[j].y, a.y, fma(v[j].x, a.x, acc[j]));
+    }
+    store_multi<NV>(acc, part);
+    const double bs = block_sum(sq);
+    if (threadIdx.x == 0) part[(size_t)NV * gridDim.x + blockIdx.x] = bs;
+    if (!last_block(ticket)) return;
+    finish_multi<NV>(part, gridDim.x, h2);
+    const double tot = sum_partials(part + (size_t)NV * gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+        double hh = 0.0;
+        for (int j = 0; j < NV; ++j) hh += h1[j] * h1[j];
+        *w1sq = tot;
+        const double nr = sqrt(tot);
+        nrm[0] = nr;
+        nrm[S_INV - S_NORM] = nr != 0.0 ? 1.0 / nr : 0.0;
+        *flag = (tot < 0.5 * (tot + hh)) ? 1.0 : 0.0;
+        *ticket = 0u;
+    }
+}
+
+// pass 3 (only when flag != 0): w <- w - V h2, nrm = |w|
+template <int NV>
+__global__ void __launch_bounds__(RB) k_gs_update_norm(const double *V, size_t ldv, double *w, size_t n2,
+                                                       const double *h2, const double *flag, double *part,
+                                                       unsigned *ticket, double *nrm) {
+    if (*flag == 0.0) return;
+    double2 *wv = reinterpret_cast<double2 *>(w);
+    const double2 *Vp[NV];
+    double c[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        Vp[j] = reinterpret_cast<const double2 *>(V + (size_t)j * ldv);
+        c[j] = -h2[j];
+    }
+    double sq = 0.0;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
+        double2 a = wv[i];
+        double2 v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            a.x = fma(c[j], v[j].x, a.x);
+            a.y = fma(c[j], v[j].y, a.y);
+        }
+        wv[i] = a;
+        sq = fma(a.y, a.y, fma(a.x, a.x, sq));
+    }
+    const double bs = block_sum(sq);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!last_block(ticket)) return;
+    const double tot = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(tot);
+        nrm[0] = nr;
+        nrm[S_INV - S_NORM] = nr != 0.0 ? 1.0 / nr : 0.0;
+        *ticket = 0u;
+    }
+}
+
+// v = w * inv (inv = 1/|w| from the Gram-Schmidt kernels), two elements per thread
+__global__ void k_scale_inv(const double *w, const double *inv, double *v, size_t n2) {
+    const double s = *inv;
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    double2 *v2 = reinterpret_cast<double2 *>(v);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        const double2 a = w2[i];
+        v2[i] = make_double2(a.x * s, a.y * s);
+    }
+}
+
 template <class S>
 __global__ void __launch_bounds__(RB) k_dot_partial(const S *x, const S *y, size_t n, double *part) {
     double acc = 0.0, acc2 = 0.0;
@@ -52,20 +297,8 @@ __global__ void __launch_bounds__(RB) k_dot_partial(const S *x, const S *y, size
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// op: RED_SUM -> sum; RED_SQRT -> sqrt(sum); RED_EPS -> sqrt(2^-52)/sqrt(sum) (0 if sum == 0);
-// RED_EPS32 -> sqrt(2^-23)/sqrt(sum)
-__global__ void __launch_bounds__(RB) k_final(const double *part, int nb, double *out, int op) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += RB) acc += part[i];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) {
-        double r = acc;
-        if (op == RED_SQRT) r = sqrt(acc);
-        if (op == RED_EPS) r = acc > 0.0 ? 1.4901161193847656e-08 / sqrt(acc) : 0.0;
-        if (op == RED_EPS32) r = acc > 0.0 ? 3.4526698300124393e-04 / sqrt(acc) : 0.0;
-        *out = r;
-    }
-}
+// op (single-launch reductions): RED_SUM -> sum; RED_SQRT -> sqrt(sum);
+// RED_EPS -> sqrt(2^-52)/sqrt(sum) (0 if sum == 0); RED_EPS32 -> sqrt(2^-23)/sqrt(sum)
 
 // h_j partials for NV basis vectors at once: accumulators are compile-time
 // indexed (registers), warp sums go through one shared-memory pass.
@@ -198,17 +431,35 @@ __global__ void __launch_bounds__(RB) k_final_gs(const double *part, int nb, con
     }
 }
 
-// y = (double) x and per-block partial sums of x^2 (for eps of the FD product)
-__global__ void __launch_bounds__(RB) k_f2d_norm(const float *x, double *y, size_t n, double *part) {
-    double acc = 0.0;
+// y = (double) x and eps = sqrt(2^-52)/|y| (for the FD product) in one launch
+__global__ void __launch_bounds__(RB) k_f2d_eps(const float *x, double *y, size_t n, double *part, unsigned *ticket,
+                                                double *eps) {
+    double acc = 0.0, acc2 = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
-    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    const size_t n4 = n / 4;   // float4 in, two double2 out (x, y 16-byte aligned)
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    double2 *y2 = reinterpret_cast<double2 *>(y);
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n4; i += stride) {
+        const float4 f = x4[i];
+        const double2 a = make_double2((double)f.x, (double)f.y), b = make_double2((double)f.z, (double)f.w);
+        y2[2 * i] = a;
+        y2[2 * i + 1] = b;
+        acc = fma(a.y, a.y, fma(a.x, a.x, acc));
+        acc2 = fma(b.y, b.y, fma(b.x, b.x, acc2));
+    }
+    for (size_t i = 4 * n4 + (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
         const double v = (double)x[i];
         y[i] = v;
         acc = fma(v, v, acc);
     }
-    acc = block_sum(acc);
+    acc = block_sum(acc + acc2);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (!last_block(ticket)) return;
+    const double t = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        *eps = finish_op(t, RED_EPS);
+        *ticket = 0u;
+    }
 }
 
 struct YV {
@@ -254,16 +505,42 @@ inline int nblocks_red(jfnk_ctx *c, size_t n) {
 
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    k_dot_partial<double><<<nb, RB, 0, s>>>(x, y, n, c->partial); jf_launched();
-    k_final<<<1, RB, 0, s>>>(c->partial, nb, out, op); jf_launched();
+    k_dot1<double><<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, out, op); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    k_dot_partial<float><<<nb, RB, 0, s>>>(x, y, n, c->partial); jf_launched();
-    k_final<<<1, RB, 0, s>>>(c->partial, nb, out, op); jf_launched();
+    k_dot1<float><<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, out, op); jf_launched();
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
+// CGS2 of w against V_0..V_{nv-1} (nv <= GS_FUSED_MAX; n even, V, w 16-byte
+// aligned), then w <- w / |w|: h1, h2, |w1|^2, the second-pass flag, |w| and
+// 1/|w| (nrm[S_INV - S_NORM]) land in device memory.
+template <int NV>
+static void cgs2_t(jfnk_ctx *c, const double *V, size_t ldv, double *w, size_t n, double *h1, double *h2,
+                   double *w1sq, double *nrm, double *flag, cudaStream_t s) {
+    const int nb = nblocks_red(c, n);
+    const size_t n2 = n / 2;
+    k_gs_dot<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
+    k_gs_update_dot<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
+    k_gs_update_norm<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
+    k_scale_inv<<<grid_for(n2), 256, 0, s>>>(w, nrm + (S_INV - S_NORM), w, n2);
+    jf_launched(4);
+}
+
+int blas_cgs2(jfnk_ctx *c, const double *V, int nv, size_t ldv, double *w, size_t n, double *h1, double *h2,
+              double *w1sq, double *nrm, double *flag, cudaStream_t s) {
+    if (nv < 1 || nv > GS_FUSED_MAX || (n & 1) || (ldv & 1)) return JFNK_EINVAL;
+    switch (nv) {
+#define JF_GS(K) case K: cgs2_t<K>(c, V, ldv, w, n, h1, h2, w1sq, nrm, flag, s); break;
+        JF_GS(1) JF_GS(2) JF_GS(3) JF_GS(4) JF_GS(5) JF_GS(6) JF_GS(7) JF_GS(8)
+        JF_GS(9) JF_GS(10) JF_GS(11) JF_GS(12) JF_GS(13) JF_GS(14) JF_GS(15) JF_GS(16)
+#undef JF_GS
+    }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -388,10 +665,9 @@ int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const do
 }
 
 int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s) {
+    if (((uintptr_t)x & 15) || ((uintptr_t)y & 15)) return JFNK_EINVAL;
     const int nb = nblocks_red(c, n);
-    k_f2d_norm<<<nb, RB, 0, s>>>(x, y, n, c->partial);
-    jf_launched();
-    k_final<<<1, RB, 0, s>>>(c->partial, nb, eps_out, RED_EPS);
+    k_f2d_eps<<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, eps_out);
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;

@@ -82,6 +82,7 @@ struct jfnk_ctx {
     FVLev lev[JF_MAXLEV];
     // reductions
     double *partial;     // scratch partial sums
+    unsigned *ticket;    // arrival counter of the single-launch reductions (0 between launches)
     int nb_red;          // partial-sum blocks
     double *scal;        // device scalars (norms, eps)
     double *h_pinned;    // host pinned scratch for Hessenberg columns
@@ -118,7 +119,7 @@ struct jfnk_ctx {
 };
 
 // device scalar slots in ctx->scal
-enum { S_NORM = 0, S_EPS = 1, S_W1 = 2, S_FLAG = 3, S_EPSFV = 8, S_NRM_FV = 24, S_H = 64, S_H2 = 128, S_COUNT = 256 };
+enum { S_NORM = 0, S_EPS = 1, S_W1 = 2, S_FLAG = 3, S_INV = 4, S_EPSDG = 5, S_EPSFV = 8, S_NRM_FV = 24, S_H = 64, S_H2 = 128, S_COUNT = 256 };
 
 // number of kernels this library has launched (diagnostic counter); the
 // thread-local twin lets a graph capture count only its own thread's launches
@@ -180,6 +181,9 @@ int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag,
 int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
                       double sign, const double *flag_in, double *w1sq, double *nrm, double *flag_out,
                       cudaStream_t s);
+constexpr int GS_FUSED_MAX = 16;   // basis vectors of the fused CGS2 kernels
+int blas_cgs2(jfnk_ctx *c, const double *V, int nv, size_t ldv, double *w, size_t n, double *h1, double *h2,
+              double *w1sq, double *nrm, double *flag, cudaStream_t s);
 int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s);
 int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);

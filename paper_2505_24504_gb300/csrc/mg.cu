@@ -120,8 +120,9 @@ JF_D void visc2(const T UL[4], const T UR[4], double mu, double id, T V[4]) {
     for (int v = 1; v < 4; ++v) V[v] = c * (UR[v] * irR - UL[v] * irL);
 }
 
-// f_low (or its tangent) at one cell (I, Jz): HLLC^pert on the four faces,
-// gravity source, two-point viscous flux.
+// f_low (or its tangent) at one cell (I, Jz) by one thread: HLLC^pert on the four
+// faces, gravity source, two-point viscous flux (large levels: enough cells to
+// fill the GPU, and fewer instructions per cell than the four-lane form).
 template <class T, int IN, bool VISC>
 JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size_t c, int I, int Jz, T f[4]) {
     const int NX = K.NX, NZ = K.NZ;
@@ -167,6 +168,114 @@ JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, si
     }
 }
 
+JF_D D64 shfl_x(D64 a, int m) { return D64{__shfl_xor_sync(0xffffffffu, a.x, m)}; }
+JF_D TL32 shfl_x(TL32 a, int m) {
+    return TL32{__shfl_xor_sync(0xffffffffu, a.v, m), __shfl_xor_sync(0xffffffffu, a.d, m)};
+}
+template <class T>
+JF_D void swap12(T U[4]) {
+    const T t = U[1];
+    U[1] = U[2];
+    U[2] = t;
+}
+
+// Sum over the four lanes of a group of per-lane vectors f[4], scattered so that
+// lane q ends up with component q (two shuffle rounds, three exchanges).
+template <class T>
+JF_D T reduce_scatter4(const T f[4], int q) {
+    const bool hi = (q & 2) != 0, lo = (q & 1) != 0;
+    const T k0 = hi ? f[2] : f[0], k1 = hi ? f[3] : f[1];
+    const T s0 = hi ? f[0] : f[2], s1 = hi ? f[1] : f[3];
+    const T g0 = k0 + shfl_x(s0, 2), g1 = k1 + shfl_x(s1, 2);
+    const T keep = lo ? g1 : g0, send = lo ? g0 : g1;
+    return keep + shfl_x(send, 1);
+}
+
+// f_low (or its tangent) at cell (I, Jz), computed by four lanes: lane q evaluates
+// face q (0 W, 1 E, 2 S, 3 N): HLLC^pert (background flux of the face row
+// subtracted), the two-point viscous flux, and lane 2 adds the gravity source.
+// z faces are evaluated in a frame with the two momentum components swapped, so
+// every lane runs the same x-direction HLLC (the arithmetic is that of the
+// z-direction flux, component for component).  Returns component q of f.
+// All four lanes of the group must be active (the reduction shuffles).
+template <class T, int IN, bool VISC>
+JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size_t c, int I, int Jz, int q) {
+    const int NX = K.NX, NZ = K.NZ;
+    const bool sub = (IN != 2);
+    const bool zf = q >= 2, right = (q & 1) != 0;
+    long nb = -1;
+    int nI = I, nJ = Jz;
+    if (q == 0) {
+        if (I > 0) { nb = (long)c - 1; nI = I - 1; }
+        else if (K.periodic) { nb = (long)c + NX - 1; nI = NX - 1; }
+    } else if (q == 1) {
+        if (I < NX - 1) { nb = (long)c + 1; nI = I + 1; }
+        else if (K.periodic) { nb = (long)c - (NX - 1); nI = 0; }
+    } else if (q == 2) {
+        if (Jz > 0) { nb = (long)c - NX; nJ = Jz - 1; }
+    } else {
+        if (Jz < NZ - 1) { nb = (long)c + NX; nJ = Jz + 1; }
+    }
+    const bool wall = nb < 0;
+    T U[4], N[4];
+    const T up0 = ld(0, c, I, Jz);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) U[v] = (v == 0 ? up0 : ld(v, c, I, Jz)) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        N[v] = wall ? U[v] : ld(v, (size_t)nb, nI, nJ) + bgs<T>(K.ub, K.ubf, v * NZ + nJ);
+    if (zf) {
+        swap12(U);
+        swap12(N);
+    }
+    if (wall) N[1] = -U[1];   // slip-wall ghost: normal momentum reversed
+    T H[4];
+    if (right) hllc<T, 0>(U, N, K.pc, spt, H);
+    else hllc<T, 0>(N, U, K.pc, spt, H);
+    T V[4];
+    if (VISC) {
+        if (wall) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) V[v] = mk(0.0, T{});
+        } else if (right) {
+            visc2(U, N, K.mu, zf ? K.iHz : K.iHx, V);
+        } else {
+            visc2(N, U, K.mu, zf ? K.iHz : K.iHx, V);
+        }
+    }
+    if (zf) {
+        swap12(H);
+        if (VISC) swap12(V);
+    }
+    if (sub) {
+        const double *hb;
+        size_t hs, hi;
+        if (!zf) {
+            hb = wall ? (right ? K.hbxw + 4 * NZ : K.hbxw) : K.hbx;
+            hs = NZ;
+            hi = Jz;
+        } else {
+            hb = K.hbz;
+            hs = NZ + 1;
+            hi = Jz + (right ? 1 : 0);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * hs + hi], T{});
+    }
+    const T ih = mk(zf ? K.iHz : K.iHx, T{});
+    T f[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        // W, S faces enter with +, E, N with - (f = -div H + div F_v)
+        T a = H[v] * ih;
+        if (VISC && v > 0) a = a - V[v] * ih;
+        f[v] = right ? -a : a;
+    }
+    T fq = reduce_scatter4(f, q);
+    if (q == 2) fq = fq - mk(K.g, T{}) * up0;   // -g rho' (tangent: -g x_rho)
+    return fq;
+}
+
 // g'(u) x at one cell and variable from the operator value f (FD quotient or tangent)
 template <class T, int IN, class S>
 JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, double adt, double eps) {
@@ -174,8 +283,9 @@ JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, 
     return x - (S)adt * (S)oval(f);
 }
 
-// One thread per cell of an NX x NZ level.
-template <class T, int IN, int MODE, bool VISC>
+// One thread (L = 1) or four lanes (L = 4, lane q owns variable q) per cell of
+// an NX x NZ level.
+template <class T, int IN, int MODE, bool VISC, int L>
 __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
                                             const double *fu, double adt, typename SOf<T>::type *out,
@@ -187,20 +297,26 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     ld.prepare();
     __syncthreads();
     const size_t n1 = (size_t)K.NX * K.NZ;
-    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n1) return;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = L == 4 ? (int)(t & 3) : 0;
+    const size_t cell = L == 4 ? (t >> 2) : t;
+    const bool live = cell < n1;
+    if (L == 1 && !live) return;
+    const size_t c = live ? cell : n1 - 1;   // idle lanes still join the shuffles
     const int I = (int)(c % K.NX), Jz = (int)(c / K.NX);
     T f[4];
-    fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
-    const double eps = ld.step();
+    if (L == 4) f[0] = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+    else fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
+    if (!live) return;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int k = 0; k < (L == 4 ? 1 : 4); ++k) {
+        const int v = L == 4 ? q : k;
         const size_t gi = (size_t)v * n1 + c;
         if (MODE == FV_RES) {
-            out[gi] = (S)oval(f[v]);
+            out[gi] = (S)oval(f[k]);
         } else {
             const S x = (S)ld.dir(v, c, I, Jz);
-            const S gx = gprime_of<T, IN, S>(ld, x, f[v], fu, gi, adt, eps);
+            const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, ld.step());
             if (MODE == FV_SMOOTH)
                 out[gi] = store_round<S>(x + dtau[c] * (b[gi] - gx), bf16);
             else
@@ -209,10 +325,13 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     }
 }
 
-// Defect and restriction in one pass: one thread per coarse cell computes the
-// defect g'x - b of its fac x fac children and writes the mean to b_c; when x_c
-// is given, also the coarse level's first pseudo-time step x_c = dtau_c b_c.
-template <class T, int IN, bool VISC>
+// Defect and restriction in one pass: the defect g'x - b of every child cell of
+// a coarse cell, averaged into b_c; when x_c is given, also the coarse level's
+// first pseudo-time step x_c = dtau_c b_c.  L = 1: one thread per coarse cell
+// loops over its fac x fac children.  L = 4, FAC2: 2 x 2 agglomeration with
+// sixteen lanes per coarse cell (four lanes per child, children summed by
+// shuffles); L = 4 otherwise: four lanes per coarse cell loop over the children.
+template <class T, int IN, bool VISC, int L, bool FAC2>
 __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *b,
                                                             const double *fu, double adt, int fac,
                                                             typename SOf<T>::type *bc, typename SOf<T>::type *xc,
@@ -225,31 +344,63 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     __syncthreads();
     const int NXc = K.NX / fac, NZc = K.NZ / fac;
     const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
-    const size_t cc = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cc >= nc) return;
-    const int Ic = (int)(cc % NXc), Jc = (int)(cc / NXc);
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double eps = ld.step();
-    S acc[4] = {0, 0, 0, 0};
-    for (int jj = 0; jj < fac; ++jj)
-        for (int ii = 0; ii < fac; ++ii) {
-            const int I = Ic * fac + ii, Jz = Jc * fac + jj;
-            const size_t c = (size_t)Jz * K.NX + I;
-            T f[4];
-            fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
+    if (L == 1) {
+        if (t >= nc) return;
+        const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
+        S acc[4] = {0, 0, 0, 0};
+        for (int jj = 0; jj < fac; ++jj)
+            for (int ii = 0; ii < fac; ++ii) {
+                const int I = Ic * fac + ii, Jz = Jc * fac + jj;
+                const size_t c = (size_t)Jz * K.NX + I;
+                T f[4];
+                fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const size_t gi = (size_t)v * n1 + c;
-                const S x = (S)ld.dir(v, c, I, Jz);
-                acc[v] += gprime_of<T, IN, S>(ld, x, f[v], fu, gi, adt, eps) - b[gi];
+                for (int v = 0; v < 4; ++v) {
+                    const size_t gi = (size_t)v * n1 + c;
+                    acc[v] += gprime_of<T, IN, S>(ld, (S)ld.dir(v, c, I, Jz), f[v], fu, gi, adt, eps) - b[gi];
+                }
             }
-        }
-    const S inv = (S)1 / (S)(fac * fac);
+        const S inv = (S)1 / (S)(fac * fac);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const S bv = store_round<S>(acc[v] * inv, bf16);
-        bc[(size_t)v * nc + cc] = bv;
-        if (xc) xc[(size_t)v * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
+        for (int v = 0; v < 4; ++v) {
+            const S bv = store_round<S>(acc[v] * inv, bf16);
+            bc[(size_t)v * nc + t] = bv;
+            if (xc) xc[(size_t)v * nc + t] = store_round<S>(dtau_c[t] * bv, bf16);
+        }
+        return;
     }
+    const int q = (int)(t & 3);
+    const size_t g = FAC2 ? (t >> 4) : (t >> 2);
+    const bool live = g < nc;
+    const size_t cc = live ? g : nc - 1;
+    const int Ic = (int)(cc % NXc), Jc = (int)(cc / NXc);
+    S acc = 0;
+    if (FAC2) {
+        const int ch = (int)((t >> 2) & 3);
+        const int I = 2 * Ic + (ch & 1), Jz = 2 * Jc + (ch >> 1);
+        const size_t c = (size_t)Jz * K.NX + I;
+        const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+        const size_t gi = (size_t)q * n1 + c;
+        const S d = gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, eps) - b[gi];
+        const S d2 = d + __shfl_xor_sync(0xffffffffu, d, 4);
+        acc = d2 + __shfl_xor_sync(0xffffffffu, d2, 8);
+        if (ch != 0) return;
+    } else {
+        for (int jj = 0; jj < fac; ++jj)
+            for (int ii = 0; ii < fac; ++ii) {
+                const int I = Ic * fac + ii, Jz = Jc * fac + jj;
+                const size_t c = (size_t)Jz * K.NX + I;
+                const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+                const size_t gi = (size_t)q * n1 + c;
+                acc += gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, eps) - b[gi];
+            }
+    }
+    if (!live) return;
+    const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
+    bc[(size_t)q * nc + cc] = bv;
+    if (xc) xc[(size_t)q * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
 }
 
 // FV pseudo-time step sizes: dtau = sigma / (1 + adt lambda), lambda = sum_faces
@@ -662,6 +813,18 @@ int to_dg(jfnk_ctx *c, const Si *v, So *u, int acc, cudaStream_t s) {
 }
 
 // ---- FV level products ----------------------------------------------------
+// four lanes per cell on levels with fewer cells than opts.fv_split_cells
+// (default 65536), one thread per cell above
+inline bool fv_four_lanes(const jfnk_ctx *c, size_t cells) {
+    const long long lim = c->opts.fv_split_cells > 0 ? c->opts.fv_split_cells : 65536;
+    return (long long)cells < lim;
+}
+#define JF_FV(T, IN, MODE, V, ...)                                                  \
+    do {                                                                            \
+        if (l4) k_fv<T, IN, MODE, V, 4><<<g, tb, 0, s>>>(__VA_ARGS__);             \
+        else k_fv<T, IN, MODE, V, 1><<<g, tb, 0, s>>>(__VA_ARGS__);                \
+        jf_launched();                                                              \
+    } while (0)
 // FV_RES: out = f_low(u) (FP64 only).  FV_SMOOTH / FV_DEFECT use the FD quotient
 // (prec 64, eps = sqrt(eps_mach)/|x| from an on-device norm) or the tangent (prec 32).
 int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, const double *b, double *out,
@@ -672,11 +835,12 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
     const bool visc = c->phys.mu != 0.0;
     c->fv_calls++;
     const int tb = c->opts.tile_fv;
-    const unsigned g = nblk(n1, tb);
+    const bool l4 = fv_four_lanes(c, n1);
+    const unsigned g = nblk((l4 ? 4 : 1) * n1, tb);
     if (mode == FV_RES) {
         FLoad<D64, 0> ld{u, n1};
-        if (visc) { k_fv<D64, 0, FV_RES, true><<<g, tb, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
-        else { k_fv<D64, 0, FV_RES, false><<<g, tb, 0, s>>>(K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); jf_launched(); }
+        if (visc) { JF_FV(D64, 0, FV_RES, true, K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); }
+        else { JF_FV(D64, 0, FV_RES, false, K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); }
     } else {
         double *epsp = c->scal + S_EPSFV + l;
         JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPS, s));
@@ -685,11 +849,11 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
         const double *fu = (const double *)L.fu;
         const double adt = c->mg_adt;
         if (mode == FV_SMOOTH) {
-            if (visc) { k_fv<D64, 1, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
-            else { k_fv<D64, 1, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            if (visc) { JF_FV(D64, 1, FV_SMOOTH, true, K, ld, x, b, dt, fu, adt, out); }
+            else { JF_FV(D64, 1, FV_SMOOTH, false, K, ld, x, b, dt, fu, adt, out); }
         } else {
-            if (visc) { k_fv<D64, 1, FV_DEFECT, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
-            else { k_fv<D64, 1, FV_DEFECT, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out); jf_launched(); }
+            if (visc) { JF_FV(D64, 1, FV_DEFECT, true, K, ld, x, b, dt, fu, adt, out); }
+            else { JF_FV(D64, 1, FV_DEFECT, false, K, ld, x, b, dt, fu, adt, out); }
         }
     }
     JF_CK(cudaGetLastError());
@@ -703,17 +867,18 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     const bool visc = c->phys.mu != 0.0;
     c->fv_calls++;
     const int tb = c->opts.tile_fv;
-    const unsigned g = nblk(n1, tb);
+    const bool l4 = fv_four_lanes(c, n1);
+    const unsigned g = nblk((l4 ? 4 : 1) * n1, tb);
     FLoad<TL32, 2> ld{(const float *)L.u, x, n1};
     const float *dt = (const float *)L.dtau;
     const double adt = c->mg_adt;
     const int bf = (c->prec == 16 && l == c->nlev - 1) ? 1 : 0;   // BF16 coarsest level
     if (mode == FV_SMOOTH) {
-        if (visc) { k_fv<TL32, 2, FV_SMOOTH, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out, bf); jf_launched(); }
-        else { k_fv<TL32, 2, FV_SMOOTH, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out, bf); jf_launched(); }
+        if (visc) { JF_FV(TL32, 2, FV_SMOOTH, true, K, ld, x, b, dt, nullptr, adt, out, bf); }
+        else { JF_FV(TL32, 2, FV_SMOOTH, false, K, ld, x, b, dt, nullptr, adt, out, bf); }
     } else {
-        if (visc) { k_fv<TL32, 2, FV_DEFECT, true><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
-        else { k_fv<TL32, 2, FV_DEFECT, false><<<g, tb, 0, s>>>(K, ld, x, b, dt, nullptr, adt, out); jf_launched(); }
+        if (visc) { JF_FV(TL32, 2, FV_DEFECT, true, K, ld, x, b, dt, nullptr, adt, out); }
+        else { JF_FV(TL32, 2, FV_DEFECT, false, K, ld, x, b, dt, nullptr, adt, out); }
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -730,30 +895,37 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     const size_t nc = (size_t)C.NX * C.NZ;
     const bool visc = c->phys.mu != 0.0;
     const int tb = c->opts.tile_fv;
-    const unsigned g = nblk(nc, tb);
+    const bool l4 = fv_four_lanes(c, n1);
+    const bool f2 = L.fac == 2;
+    const unsigned g = nblk((l4 ? (f2 ? 16 : 4) : 1) * nc, tb);   // lanes per coarse cell
     c->fv_calls++;
+#define JF_DR(T, IN, V, LN, F2, ...) k_fv_defect_restrict<T, IN, V, LN, F2><<<g, tb, 0, s>>>(__VA_ARGS__)
+#define JF_DR2(T, IN, V, ...)                                \
+    do {                                                     \
+        if (!l4) JF_DR(T, IN, V, 1, false, __VA_ARGS__);     \
+        else if (f2) JF_DR(T, IN, V, 4, true, __VA_ARGS__);  \
+        else JF_DR(T, IN, V, 4, false, __VA_ARGS__);         \
+    } while (0)
+#define JF_DR4(T, IN, ...)                                   \
+    do {                                                     \
+        if (visc) JF_DR2(T, IN, true, __VA_ARGS__);          \
+        else JF_DR2(T, IN, false, __VA_ARGS__);              \
+    } while (0)
     if (c->prec == 64) {
         double *epsp = c->scal + S_EPSFV + l;
         JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPS, s));
         FLoad<D64, 1> ld{(const double *)L.u, (const double *)x, epsp, n1, 0.0};
-        if (visc)
-            k_fv_defect_restrict<D64, 1, true><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
-                                                                c->mg_adt, L.fac, (double *)bc, (double *)xc,
-                                                                (const double *)dtc, 0);
-        else
-            k_fv_defect_restrict<D64, 1, false><<<g, tb, 0, s>>>(K, ld, (const double *)b, (const double *)L.fu,
-                                                                 c->mg_adt, L.fac, (double *)bc, (double *)xc,
-                                                                 (const double *)dtc, 0);
+        JF_DR4(D64, 1, K, ld, (const double *)b, (const double *)L.fu, c->mg_adt, L.fac, (double *)bc, (double *)xc,
+               (const double *)dtc, 0);
     } else {
         FLoad<TL32, 2> ld{(const float *)L.u, (const float *)x, n1};
         const int bf = (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0;   // BF16 coarsest level
-        if (visc)
-            k_fv_defect_restrict<TL32, 2, true><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
-                                                                 (float *)bc, (float *)xc, (const float *)dtc, bf);
-        else
-            k_fv_defect_restrict<TL32, 2, false><<<g, tb, 0, s>>>(K, ld, (const float *)b, nullptr, c->mg_adt, L.fac,
-                                                                  (float *)bc, (float *)xc, (const float *)dtc, bf);
+        JF_DR4(TL32, 2, K, ld, (const float *)b, nullptr, c->mg_adt, L.fac, (float *)bc, (float *)xc,
+               (const float *)dtc, bf);
     }
+#undef JF_DR4
+#undef JF_DR2
+#undef JF_DR
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -846,13 +1018,13 @@ int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2
         JF_CK(cudaGetLastError());
         return JFNK_OK;
     }
-    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPS + 1, RED_EPS, s));
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPS, s));
     DGArgs a = {};
     a.U = c->mg_U;
     a.y = z;
     a.fU = c->fU;
     a.r = r;
-    a.eps = c->scal + S_EPS + 1;
+    a.eps = c->scal + S_EPSDG;
     a.dtau = c->dtau_dg;
     a.adt = c->mg_adt;
     a.out0 = z2;
@@ -893,12 +1065,12 @@ int dg_defect(jfnk_ctx *c, const S *r, const S *z, S *d, cudaStream_t s);
 
 template <>
 int dg_defect<double>(jfnk_ctx *c, const double *r, const double *z, double *d, cudaStream_t s) {
-    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPS + 1, RED_EPS, s));
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPS, s));
     DGArgs a = {};
     a.U = c->mg_U;
     a.y = z;
     a.fU = c->fU;
-    a.eps = c->scal + S_EPS + 1;
+    a.eps = c->scal + S_EPSDG;
     a.adt = c->mg_adt;
     a.out0 = c->w2;
     JF_RET(dg_apply(c, DG_JV, a, s));

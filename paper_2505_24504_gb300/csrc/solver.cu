@@ -102,6 +102,13 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
     // classical Gram-Schmidt; the update kernel also reduces |w|^2, and a
     // second pass runs only when the first lost more than half of |w|
     // (decided on the device)
+    if (j + 1 <= GS_FUSED_MAX && (N & 1) == 0) {
+        JF_RET(blas_cgs2(c, V, j + 1, N, w, N, c->scal + S_H, c->scal + S_H2, c->scal + S_W1, c->scal + S_NORM,
+                         c->scal + S_FLAG, s));   // normalises w too
+        if (ph) ph->mark(3, s);
+        JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
+        return JFNK_OK;
+    }
     JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
     JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H, w, N, -1.0, nullptr, c->scal + S_W1,
                              c->scal + S_NORM, c->scal + S_FLAG, s));

@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("fv_levels", C.c_int), ("massfix", C.c_int), ("transfer_l2", C.c_int), ("precond_prec", C.c_int),
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
-                ("tile_fv", C.c_int), ("profile", C.c_int)]
+                ("tile_fv", C.c_int), ("fv_split_cells", C.c_int), ("profile", C.c_int)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -246,12 +246,12 @@ class Context:
         return ms[0], ms[1]
 
     def jfnk_autotune(self, U, y, reps=3, stream=None):
-        best = (C.c_int * 3)()
+        best = (C.c_int * 4)()
         ms = (C.c_double * 2)()
         _check(_lib().jfnk_autotune(self.h, _ptr(U), _ptr(y), int(reps), best, ms, _stream(stream)),
                "jfnk_autotune")
         return {"tile_faces": best[0], "tile_volume": best[1], "tile_fv": best[2],
-                "dg_ms": ms[0], "precond_ms": ms[1]}
+                "fv_split_cells": best[3], "dg_ms": ms[0], "precond_ms": ms[1]}
 
     def fv_levels(self):
         n = _lib().jfnk_fv_levels(self.h)

@@ -180,9 +180,12 @@ def test_transfers_l2_parity(case):
     assert rel(to_cpu(back, dg.shape), u) <= 1e-13
 
 
-def test_fv_residual_parity_every_level(case):
+@pytest.mark.parametrize("split", [1, 1 << 30])
+def test_fv_residual_parity_every_level(case, split):
+    # split 1: one thread per cell on every level; 1 << 30: four lanes per cell
     from oracle.fv import Multigrid
-    w, ctx, dg = case
+    w, _, dg = case
+    ctx = gpu_context(w, fv_split_cells=split)
     mg = Multigrid(dg, w.fv_levels, w.mg_key)
     assert ctx.fv_levels() == [(lev.NX, lev.NZ) for lev in mg.levels]
     for l, lev in enumerate(mg.levels):
@@ -208,13 +211,17 @@ def test_preconditioner_without_fd_products_is_tight(case):
     assert rel(to_cpu(z, dg.shape), mg.apply(r)) <= 1e-12
 
 
-def test_preconditioner_parity_at_fd_noise(case):
+@pytest.mark.parametrize("split", [0, 1])
+def test_preconditioner_parity_at_fd_noise(case, split):
     # every FD product g'x amplifies rounding of f_low by alpha dt / eps with
     # eps = sqrt(eps_mach)/|x|, so two correct implementations differ at that
     # noise level.  Measure the oracle's own noise (input perturbed at 1e-15) and
-    # require the GPU within a small multiple of it.
+    # require the GPU within a small multiple of it.  split 1: one thread per FV
+    # cell on every level (the default runs these small levels four lanes per cell).
     from oracle.fv import Multigrid
     w, ctx, dg = case
+    if split:
+        ctx = gpu_context(w, fv_split_cells=split)
     Up = perturbed_state(w, dg, seed=19)
     r = synth.random_perturbation(dg.shape[1:], 20)
     z = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
@@ -357,6 +364,25 @@ def test_launch_tiles_do_not_change_results_and_autotune_picks_valid_shapes():
     best = ctx.jfnk_autotune(to_gpu(U0), y, reps=2)
     assert best["tile_faces"] in (64, 128, 256) and best["tile_volume"] in (1, 2)
     assert best["tile_fv"] in (64, 128, 256) and best["dg_ms"] > 0 and best["precond_ms"] > 0
+    assert best["fv_split_cells"] >= 1
     U = to_gpu(U0)
     ctx.implicit_step(U, w.dt, scheme=1)
-    assert np.array_equal(outs[0], to_cpu(U))
+    # the lane split changes the FV summation order: same answer to the Newton tolerance
+    got = to_cpu(U)
+    assert np.linalg.norm(got - outs[0]) <= 1e-6 * np.linalg.norm(outs[0] - U0)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fv_lane_split_same_answer(prec):
+    # one thread per FV cell on every level vs four lanes per cell on every level
+    w = synth.scaled(W1, 12, 6, k=3, fv_levels=4)
+    dg = oracle_dg(w)
+    U0 = initial_state(w, dg)
+    outs = []
+    for split in (1, 1 << 30):
+        ctx = gpu_context(w, precond_prec=prec, fv_split_cells=split)
+        U = to_gpu(U0)
+        st = ctx.implicit_step(U, w.dt, scheme=1)
+        assert st.status == 0
+        outs.append(to_cpu(U))
+    assert np.linalg.norm(outs[0] - outs[1]) <= 1e-6 * np.linalg.norm(outs[0] - U0)
