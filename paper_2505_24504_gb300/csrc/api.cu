@@ -302,6 +302,10 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     c->pc.g = ph->g;
     c->pc.mu = ph->mu;
     c->pc.R_over_p0 = R / ph->p0;
+    c->pc.gammaf = (float)c->pc.gamma;
+    c->pc.p0f = (float)c->pc.p0;
+    c->pc.R_over_p0f = (float)c->pc.R_over_p0;
+    c->pc.muf = (float)c->pc.mu;
     jf_build_tables(k, &c->tab);
 
 #define A_(p, bytes)                         \
@@ -473,6 +477,16 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
         }
     }
     c->nb_red = 4096;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            cudaGetLastError();
+            destroy_unlocked(c);
+            return JFNK_ECUDA;
+        }
+        c->n_sm = nsm;
+    }
     A_(c->partial, 8 * (size_t)c->nb_red * 32);
     A_(c->scal, 8 * (size_t)S_COUNT);
     A_(c->ticket, 256);

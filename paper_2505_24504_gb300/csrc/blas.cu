@@ -431,29 +431,44 @@ __global__ void __launch_bounds__(RB) k_final_gs(const double *part, int nb, con
     }
 }
 
-// y = (double) x and eps = sqrt(2^-52)/|y| (for the FD product) in one launch
+// float -> double widening on the integer pipe, exact: binary64 re-biases the
+// binary32 exponent by 1023 - 127 = 896 and takes the 23 fraction bits as the
+// top of its 52 (IEEE 754 formats).  Zero, subnormal, infinite and NaN inputs
+// use the conversion instruction (an FP64-pipe operation, like the DFMA).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)r);
+}
+
+// y = (double) x and eps = sqrt(2^-52)/|y| (for the FD product) in one launch.
+// The squares are summed in FP32 within a thread (eps needs a few digits), the
+// per-thread partials in FP64.
 __global__ void __launch_bounds__(RB) k_f2d_eps(const float *x, double *y, size_t n, double *part, unsigned *ticket,
                                                 double *eps) {
-    double acc = 0.0, acc2 = 0.0;
+    float acc = 0.0f, acc2 = 0.0f;
     const size_t stride = (size_t)gridDim.x * RB;
     const size_t n4 = n / 4;   // float4 in, two double2 out (x, y 16-byte aligned)
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
     double2 *y2 = reinterpret_cast<double2 *>(y);
     for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n4; i += stride) {
         const float4 f = x4[i];
-        const double2 a = make_double2((double)f.x, (double)f.y), b = make_double2((double)f.z, (double)f.w);
-        y2[2 * i] = a;
-        y2[2 * i + 1] = b;
-        acc = fma(a.y, a.y, fma(a.x, a.x, acc));
-        acc2 = fma(b.y, b.y, fma(b.x, b.x, acc2));
+        y2[2 * i] = make_double2(f2d_bits(f.x), f2d_bits(f.y));
+        y2[2 * i + 1] = make_double2(f2d_bits(f.z), f2d_bits(f.w));
+        acc = fmaf(f.y, f.y, fmaf(f.x, f.x, acc));
+        acc2 = fmaf(f.w, f.w, fmaf(f.z, f.z, acc2));
     }
     for (size_t i = 4 * n4 + (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
-        const double v = (double)x[i];
-        y[i] = v;
-        acc = fma(v, v, acc);
+        const float f = x[i];
+        y[i] = f2d_bits(f);
+        acc = fmaf(f, f, acc);
     }
-    acc = block_sum(acc + acc2);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double tsum = block_sum((double)acc + (double)acc2);
+    if (threadIdx.x == 0) part[blockIdx.x] = tsum;
     if (!last_block(ticket)) return;
     const double t = sum_partials(part, gridDim.x);
     if (threadIdx.x == 0) {
@@ -466,12 +481,15 @@ struct YV {
     double y[MAXV];
 };
 
+__device__ __forceinline__ double widen(float f) { return f2d_bits(f); }
+__device__ __forceinline__ double widen(double d) { return d; }
+
 template <class S>
 __global__ void k_zcomb(const S *Z, int nz, size_t n, YV yv, double *x) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double acc = x[i];
-        for (int j = 0; j < nz; ++j) acc = fma(yv.y[j], (double)Z[(size_t)j * n + i], acc);
+        for (int j = 0; j < nz; ++j) acc = fma(yv.y[j], widen(Z[(size_t)j * n + i]), acc);
         x[i] = acc;
     }
 }
@@ -482,7 +500,7 @@ __global__ void k_d2f(const double *x, float *y, size_t n) {
 }
 __global__ void k_f2d(const float *x, double *y, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (double)x[i];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = f2d_bits(x[i]);
 }
 
 inline unsigned grid_for(size_t n) {
@@ -520,14 +538,31 @@ int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out,
 // CGS2 of w against V_0..V_{nv-1} (nv <= GS_FUSED_MAX; n even, V, w 16-byte
 // aligned), then w <- w / |w|: h1, h2, |w1|^2, the second-pass flag, |w| and
 // 1/|w| (nrm[S_INV - S_NORM]) land in device memory.
+// One wave: the SM count times the blocks of this kernel an SM holds (FP64-bound
+// kernels lose a partial second wave otherwise), fewer for short vectors.
+template <class F>
+static int one_wave(jfnk_ctx *c, F kernel, size_t n2) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, RB, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    size_t g = (size_t)c->n_sm * per_sm;
+    const size_t need = (n2 + RB - 1) / RB;
+    if (g > need) g = need;
+    if (g > (size_t)c->nb_red) g = c->nb_red;
+    return g < 1 ? 1 : (int)g;
+}
+
 template <int NV>
 static void cgs2_t(jfnk_ctx *c, const double *V, size_t ldv, double *w, size_t n, double *h1, double *h2,
                    double *w1sq, double *nrm, double *flag, cudaStream_t s) {
-    const int nb = nblocks_red(c, n);
     const size_t n2 = n / 2;
-    k_gs_dot<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
-    k_gs_update_dot<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
-    k_gs_update_norm<NV><<<nb, RB, 0, s>>>(V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
+    const int g1 = one_wave(c, k_gs_dot<NV>, n2), g2 = one_wave(c, k_gs_update_dot<NV>, n2),
+              g3 = one_wave(c, k_gs_update_norm<NV>, n2);
+    k_gs_dot<NV><<<g1, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
+    k_gs_update_dot<NV><<<g2, RB, 0, s>>>(V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
+    k_gs_update_norm<NV><<<g3, RB, 0, s>>>(V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
     k_scale_inv<<<grid_for(n2), 256, 0, s>>>(w, nrm + (S_INV - S_NORM), w, n2);
     jf_launched(4);
 }

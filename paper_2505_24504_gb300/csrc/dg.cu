@@ -22,6 +22,8 @@ namespace {
 struct DGK {
     int nx, nz, n_el, periodic;
     double two_hx, two_hz, g, mu, eta_x, eta_z;
+    float two_hxf, two_hzf, gf, eta_xf, eta_zf;   // float copies for the FP32 tangent
+    float tlp[5], tlm[5], tdlp[5], tdlm[5];       // trace tables l_a(+-1), l_a'(+-1) in float
     PhysC pc;
     const PowTab *pt;
     const double *ubv, *dubv, *fbx, *fbz, *hbx, *hbxw, *ubh, *dubh, *hbz;
@@ -117,17 +119,17 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
             for (int a = 0; a < NP1; ++a) {
                 const T uL = ld((size_t)v * N1 + (size_t)eL * NP + s * NP1 + a);
                 const T uR = ld((size_t)v * N1 + (size_t)eR * NP + s * NP1 + a);
-                aL = jfma(mk(K.tab.lp[a], T{}), uL, aL);
-                aR = jfma(mk(K.tab.lm[a], T{}), uR, aR);
+                aL = jfma(mkc(K.tab.lp[a], K.tlp[a], T{}), uL, aL);
+                aR = jfma(mkc(K.tab.lm[a], K.tlm[a], T{}), uR, aR);
                 if (VISC) {
-                    dL = jfma(mk(K.tab.dlp[a], T{}), uL, dL);
-                    dR = jfma(mk(K.tab.dlm[a], T{}), uR, dR);
+                    dL = jfma(mkc(K.tab.dlp[a], K.tdlp[a], T{}), uL, dL);
+                    dR = jfma(mkc(K.tab.dlm[a], K.tdlm[a], T{}), uR, dR);
                 }
             }
             trL[v] = aL;
             trR[v] = aR;
-            gL[v] = mk(K.two_hx, T{}) * dL;
-            gR[v] = mk(K.two_hx, T{}) * dR;
+            gL[v] = mkc(K.two_hx, K.two_hxf, T{}) * dL;
+            gR[v] = mkc(K.two_hx, K.two_hxf, T{}) * dR;
         }
         T UL[4], UR[4], Gh[4];
 #pragma unroll
@@ -154,15 +156,15 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
         for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
         if (VISC && !wallL && !wallR) {
             T FL[4], FR[4], Jp[4];
-            viscous(UL, gL, K.mu, FL);
-            viscous(UR, gR, K.mu, FR);
+            viscous(UL, gL, K.pc, FL);
+            viscous(UR, gR, K.pc, FR);
 #pragma unroll
             for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
 #pragma unroll
-            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + mk(K.eta_x, T{}) * Jp[v];
+            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + mkc(K.eta_x, K.eta_xf, T{}) * Jp[v];
             T AL[4], AR[4];
-            viscous(UL, Jp, K.mu, AL);
-            viscous(UR, Jp, K.mu, AR);
+            viscous(UL, Jp, K.pc, AL);
+            viscous(UR, Jp, K.pc, AR);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sL[c] = half * AL[c + 1];
@@ -196,17 +198,17 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
             for (int b = 0; b < NP1; ++b) {
                 const T uB = ld((size_t)v * N1 + (size_t)eB * NP + b * NP1 + s);
                 const T uT = ld((size_t)v * N1 + (size_t)eT * NP + b * NP1 + s);
-                aB = jfma(mk(K.tab.lp[b], T{}), uB, aB);
-                aT = jfma(mk(K.tab.lm[b], T{}), uT, aT);
+                aB = jfma(mkc(K.tab.lp[b], K.tlp[b], T{}), uB, aB);
+                aT = jfma(mkc(K.tab.lm[b], K.tlm[b], T{}), uT, aT);
                 if (VISC) {
-                    dB = jfma(mk(K.tab.dlp[b], T{}), uB, dB);
-                    dT = jfma(mk(K.tab.dlm[b], T{}), uT, dT);
+                    dB = jfma(mkc(K.tab.dlp[b], K.tdlp[b], T{}), uB, dB);
+                    dT = jfma(mkc(K.tab.dlm[b], K.tdlm[b], T{}), uT, dT);
                 }
             }
             trB[v] = aB;
             trT[v] = aT;
-            gB[v] = mk(K.two_hz, T{}) * dB + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
-            gT[v] = mk(K.two_hz, T{}) * dT + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
+            gB[v] = mkc(K.two_hz, K.two_hzf, T{}) * dB + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
+            gT[v] = mkc(K.two_hz, K.two_hzf, T{}) * dT + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
         }
         T UB[4], UT[4], Gh[4];
 #pragma unroll
@@ -232,15 +234,15 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
         for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
         if (VISC && !wallB && !wallT) {
             T FB[4], FT[4], Jp[4];
-            viscous(UB, gB, K.mu, FB);
-            viscous(UT, gT, K.mu, FT);
+            viscous(UB, gB, K.pc, FB);
+            viscous(UT, gT, K.pc, FT);
 #pragma unroll
             for (int v = 0; v < 4; ++v) Jp[v] = trB[v] - trT[v];
 #pragma unroll
-            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + mk(K.eta_z, T{}) * Jp[v];
+            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + mkc(K.eta_z, K.eta_zf, T{}) * Jp[v];
             T AB[4], AT[4];
-            viscous(UB, Jp, K.mu, AB);
-            viscous(UT, Jp, K.mu, AT);
+            viscous(UB, Jp, K.pc, AB);
+            viscous(UT, Jp, K.pc, AT);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sL[c] = half * AB[c + 1];
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     // weak-form derivative and lift tables with the 2/h factors folded in:
     // sDx = (2/hx) Dw, sDz = (2/hz) Dw; sl[0..3] x-lifts, sl[4..7] z-lifts
     __shared__ O sDx[NP1][NP1], sDz[NP1][NP1];
-    __shared__ double sDn[NP1][NP1];
+    __shared__ O sDn[NP1][NP1];
     __shared__ O sl[8][NP1];
     if (IN != 2) load_powtab(&spt, K.pt);
     Loader<T, IN> ld = ld0;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
         const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
         sDx[r][q] = (O)(K.two_hx * K.tab.Dw[r][q]);
         sDz[r][q] = (O)(K.two_hz * K.tab.Dw[r][q]);
-        sDn[r][q] = K.tab.Dn[r][q];
+        sDn[r][q] = (O)K.tab.Dn[r][q];
     }
     if (threadIdx.x < NP1) {
         const int q = threadIdx.x;
@@ -347,14 +349,14 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
                 T sx = mk(0.0, T{}), sz = mk(0.0, T{});
 #pragma unroll
                 for (int q = 0; q < NP1; ++q) {
-                    sx = jfma(mk(sDn[a][q], T{}), su[le][v][b * NP1 + q], sx);
-                    sz = jfma(mk(sDn[b][q], T{}), su[le][v][q * NP1 + a], sz);
+                    sx = jfma(T{sDn[a][q]}, su[le][v][b * NP1 + q], sx);
+                    sz = jfma(T{sDn[b][q]}, su[le][v][q * NP1 + a], sz);
                 }
-                dx[v] = mk(K.two_hx, T{}) * sx;
-                dz[v] = mk(K.two_hz, T{}) * sz + bgs<T>(K.dubv, K.dubvf, v * nrow + J);
+                dx[v] = mkc(K.two_hx, K.two_hxf, T{}) * sx;
+                dz[v] = mkc(K.two_hz, K.two_hzf, T{}) * sz + bgs<T>(K.dubv, K.dubvf, v * nrow + J);
             }
-            viscous(U, dx, K.mu, Gx);
-            viscous(U, dz, K.mu, Gz);
+            viscous(U, dx, K.pc, Gx);
+            viscous(U, dz, K.pc, Gz);
 #pragma unroll
             for (int v = 1; v < 4; ++v) {
                 Fx[v] = Fx[v] - Gx[v];
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     const O lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
     const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
     const double ceps = eps != 0.0 ? A.adt / eps : 0.0;   // adt / eps once per thread
+    const float adtf = (MODE == DG_TLJV || MODE == DG_TLSMOOTH) ? (float)A.adt : 0.0f;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         O f = 0;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
             f = fma(sDx[a][q], sg[0][le][v][b * NP1 + q], f);
             f = fma(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
         }
-        if (v == 2) f = fma(-(O)K.g, (O)outv(Up[0]), f);
+        if (v == 2) f = fma(-pick<O>(K.g, K.gf), (O)outv(Up[0]), f);
         f = fma(lmxa, phix[v * fsx + iL], f);
         f = fma(-lpxa, phix[v * fsx + iR], f);
         f = fma(lmzb, phiz[v * fsz + iB], f);
@@ -411,10 +414,10 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
             ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
         } else if (MODE == DG_TLJV) {
             const float z = A.yf[gi];
-            ((float *)A.out0)[gi] = z - (float)A.adt * (float)f;
+            ((float *)A.out0)[gi] = z - adtf * (float)f;
         } else {  // DG_TLSMOOTH
             const float z = A.yf[gi];
-            const float Jz = z - (float)A.adt * (float)f;
+            const float Jz = z - adtf * (float)f;
             ((float *)A.out0)[gi] = z + A.dtauf[e] * (A.rf[gi] - Jz);
         }
     }
@@ -470,6 +473,7 @@ DGK make_K(jfnk_ctx *c) {
     K.two_hz = 2.0 / c->hz;
     K.g = c->phys.g;
     K.mu = c->phys.mu;
+    K.gf = (float)K.g;
     const double n1 = c->np1;
     K.eta_x = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hx;
     K.eta_z = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hz;
@@ -489,6 +493,16 @@ DGK make_K(jfnk_ctx *c) {
     K.ubhf = c->ubhf;
     K.dubhf = c->dubhf;
     K.tab = c->tab;
+    K.two_hxf = (float)K.two_hx;
+    K.two_hzf = (float)K.two_hz;
+    K.eta_xf = (float)K.eta_x;
+    K.eta_zf = (float)K.eta_z;
+    for (int a = 0; a < 5; ++a) {
+        K.tlp[a] = (float)K.tab.lp[a];
+        K.tlm[a] = (float)K.tab.lm[a];
+        K.tdlp[a] = (float)K.tab.dlp[a];
+        K.tdlm[a] = (float)K.tab.dlm[a];
+    }
     return K;
 }
 

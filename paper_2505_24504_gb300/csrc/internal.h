@@ -84,6 +84,7 @@ struct jfnk_ctx {
     double *partial;     // scratch partial sums
     unsigned *ticket;    // arrival counter of the single-launch reductions (0 between launches)
     int nb_red;          // partial-sum blocks
+    int n_sm;            // streaming multiprocessors of the context's device
     double *scal;        // device scalars (norms, eps)
     double *h_pinned;    // host pinned scratch for Hessenberg columns
     // linearisation of the preconditioner (set by mg_linearize)

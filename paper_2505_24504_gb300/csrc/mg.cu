@@ -27,6 +27,8 @@ namespace {
 struct FVK {
     int NX, NZ, periodic;
     double iHx, iHz, g, mu;
+    double vcx, vcz;                     // mu / (2 H) of the two-point viscous flux
+    float iHxf, iHzf, gf, vcxf, vczf;    // float copies for the FP32 tangent
     PhysC pc;
     const PowTab *pt;
     const double *ub, *hbx, *hbxw, *hbz;
@@ -112,9 +114,9 @@ JF_D void face_flux(const T UL[4], const T UR[4], bool wallL, bool wallR, const 
 }
 
 template <class T>
-JF_D void visc2(const T UL[4], const T UR[4], double mu, double id, T V[4]) {
+JF_D void visc2(const T UL[4], const T UR[4], T coef, T V[4]) {
     const T irL = mk(1.0, T{}) / UL[0], irR = mk(1.0, T{}) / UR[0];
-    const T c = mk(0.5 * mu * id, T{}) * (UL[0] + UR[0]);
+    const T c = coef * (UL[0] + UR[0]);
     V[0] = mk(0.0, T{});
 #pragma unroll
     for (int v = 1; v < 4; ++v) V[v] = c * (UR[v] * irR - UL[v] * irL);
@@ -151,18 +153,19 @@ JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, si
     face_flux<T, 0>(U, Un[1], false, nb[1] < 0, nb[1] < 0 ? K.hbxw + 4 * NZ : K.hbx, NZ, Jz, sub, K, spt, HE);
     face_flux<T, 1>(Un[2], U, nb[2] < 0, false, K.hbz, NZ + 1, Jz, sub, K, spt, HS);
     face_flux<T, 1>(U, Un[3], false, nb[3] < 0, K.hbz, NZ + 1, Jz + 1, sub, K, spt, HN);
-    const T iHx = mk(K.iHx, T{}), iHz = mk(K.iHz, T{});
+    const T iHx = mkc(K.iHx, K.iHxf, T{}), iHz = mkc(K.iHz, K.iHzf, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v) f[v] = -((HE[v] - HW[v]) * iHx + (HN[v] - HS[v]) * iHz);
     const T up0 = ld(0, c, I, Jz);
-    f[2] = f[2] - mk(K.g, T{}) * up0;   // -g rho' (tangent: -g x_rho)
+    f[2] = f[2] - mkc(K.g, K.gf, T{}) * up0;   // -g rho' (tangent: -g x_rho)
     if (VISC) {
         T VW[4], VE[4], VS[4], VN[4];
         const T zero = mk(0.0, T{});
-        if (nb[0] >= 0) visc2(Un[0], U, K.mu, K.iHx, VW); else { for (int v = 0; v < 4; ++v) VW[v] = zero; }
-        if (nb[1] >= 0) visc2(U, Un[1], K.mu, K.iHx, VE); else { for (int v = 0; v < 4; ++v) VE[v] = zero; }
-        if (nb[2] >= 0) visc2(Un[2], U, K.mu, K.iHz, VS); else { for (int v = 0; v < 4; ++v) VS[v] = zero; }
-        if (nb[3] >= 0) visc2(U, Un[3], K.mu, K.iHz, VN); else { for (int v = 0; v < 4; ++v) VN[v] = zero; }
+        const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
+        if (nb[0] >= 0) visc2(Un[0], U, cx, VW); else { for (int v = 0; v < 4; ++v) VW[v] = zero; }
+        if (nb[1] >= 0) visc2(U, Un[1], cx, VE); else { for (int v = 0; v < 4; ++v) VE[v] = zero; }
+        if (nb[2] >= 0) visc2(Un[2], U, cz, VS); else { for (int v = 0; v < 4; ++v) VS[v] = zero; }
+        if (nb[3] >= 0) visc2(U, Un[3], cz, VN); else { for (int v = 0; v < 4; ++v) VN[v] = zero; }
 #pragma unroll
         for (int v = 1; v < 4; ++v) f[v] = f[v] + (VE[v] - VW[v]) * iHx + (VN[v] - VS[v]) * iHz;
     }
@@ -238,9 +241,9 @@ JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size
 #pragma unroll
             for (int v = 0; v < 4; ++v) V[v] = mk(0.0, T{});
         } else if (right) {
-            visc2(U, N, K.mu, zf ? K.iHz : K.iHx, V);
+            visc2(U, N, zf ? mkc(K.vcz, K.vczf, T{}) : mkc(K.vcx, K.vcxf, T{}), V);
         } else {
-            visc2(N, U, K.mu, zf ? K.iHz : K.iHx, V);
+            visc2(N, U, zf ? mkc(K.vcz, K.vczf, T{}) : mkc(K.vcx, K.vcxf, T{}), V);
         }
     }
     if (zf) {
@@ -262,7 +265,7 @@ JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size
 #pragma unroll
         for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * hs + hi], T{});
     }
-    const T ih = mk(zf ? K.iHz : K.iHx, T{});
+    const T ih = zf ? mkc(K.iHz, K.iHzf, T{}) : mkc(K.iHx, K.iHxf, T{});
     T f[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -272,15 +275,15 @@ JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size
         f[v] = right ? -a : a;
     }
     T fq = reduce_scatter4(f, q);
-    if (q == 2) fq = fq - mk(K.g, T{}) * up0;   // -g rho' (tangent: -g x_rho)
+    if (q == 2) fq = fq - mkc(K.g, K.gf, T{}) * up0;   // -g rho' (tangent: -g x_rho)
     return fq;
 }
 
 // g'(u) x at one cell and variable from the operator value f (FD quotient or tangent)
 template <class T, int IN, class S>
-JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, double adt, double eps) {
+JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, double adt, float adtf, double eps) {
     if (IN == 1) return (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)oval(f) - fu[gi]) / eps);
-    return x - (S)adt * (S)oval(f);
+    return x - (S)adtf * (S)oval(f);
 }
 
 // One thread (L = 1) or four lanes (L = 4, lane q owns variable q) per cell of
@@ -296,6 +299,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     FLoad<T, IN> ld = ld0;
     ld.prepare();
     __syncthreads();
+    const float adtf = IN == 2 ? (float)adt : 0.0f;
     const size_t n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = L == 4 ? (int)(t & 3) : 0;
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
             out[gi] = (S)oval(f[k]);
         } else {
             const S x = (S)ld.dir(v, c, I, Jz);
-            const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, ld.step());
+            const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, adtf, ld.step());
             if (MODE == FV_SMOOTH)
                 out[gi] = store_round<S>(x + dtau[c] * (b[gi] - gx), bf16);
             else
@@ -346,6 +350,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double eps = ld.step();
+    const float adtf = IN == 2 ? (float)adt : 0.0f;
     if (L == 1) {
         if (t >= nc) return;
         const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const size_t gi = (size_t)v * n1 + c;
-                    acc[v] += gprime_of<T, IN, S>(ld, (S)ld.dir(v, c, I, Jz), f[v], fu, gi, adt, eps) - b[gi];
+                    acc[v] += gprime_of<T, IN, S>(ld, (S)ld.dir(v, c, I, Jz), f[v], fu, gi, adt, adtf, eps) - b[gi];
                 }
             }
         const S inv = (S)1 / (S)(fac * fac);
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
         const size_t c = (size_t)Jz * K.NX + I;
         const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
         const size_t gi = (size_t)q * n1 + c;
-        const S d = gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, eps) - b[gi];
+        const S d = gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
         const S d2 = d + __shfl_xor_sync(0xffffffffu, d, 4);
         acc = d2 + __shfl_xor_sync(0xffffffffu, d2, 8);
         if (ch != 0) return;
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
                 const size_t c = (size_t)Jz * K.NX + I;
                 const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
                 const size_t gi = (size_t)q * n1 + c;
-                acc += gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, eps) - b[gi];
+                acc += gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
             }
     }
     if (!live) return;
@@ -415,8 +420,8 @@ JF_D double wave_speed_r<double>(const double U[4], int D, const PhysC &P, const
 template <>
 JF_D float wave_speed_r<float>(const float U[4], int D, const PhysC &P, const PowTab *) {
     const float ir = 1.0f / U[0];
-    const float p = (float)P.p0 * __powf((float)P.R_over_p0 * U[3], (float)P.gamma);
-    return fabsf(U[1 + D] * ir) + sqrtf((float)P.gamma * p * ir);
+    const float p = P.p0f * __powf(P.R_over_p0f * U[3], P.gammaf);
+    return fabsf(U[1 + D] * ir) + sqrtf(P.gammaf * p * ir);
 }
 
 template <class S>
@@ -431,7 +436,7 @@ __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) 
     const int I = (int)(c % NX), Jz = (int)(c / NX);
     auto st = [&](int i, int j, S U[4]) {
         const size_t cc = (size_t)j * NX + i;
-        for (int v = 0; v < 4; ++v) U[v] = u[(size_t)v * n1 + cc] + (S)K.ub[v * NZ + j];
+        for (int v = 0; v < 4; ++v) U[v] = u[(size_t)v * n1 + cc] + pick<S>(K.ub[v * NZ + j], K.ubf[v * NZ + j]);
     };
     S U[4], V[4];
     st(I, Jz, U);
@@ -749,6 +754,13 @@ FVK make_fvk(jfnk_ctx *c, int l) {
     K.iHz = 1.0 / L.Hz;
     K.g = c->phys.g;
     K.mu = c->phys.mu;
+    K.vcx = 0.5 * K.mu * K.iHx;
+    K.vcz = 0.5 * K.mu * K.iHz;
+    K.iHxf = (float)K.iHx;
+    K.iHzf = (float)K.iHz;
+    K.gf = (float)K.g;
+    K.vcxf = (float)K.vcx;
+    K.vczf = (float)K.vcz;
     K.pc = c->pc;
     K.pt = c->powtab;
     K.ub = L.ub;

@@ -75,15 +75,28 @@ JF_D TL32 mk(double v, TL32) { return TL32{(float)v, 0.0f}; }
 JF_D TL32 operator+(TL32 a, TL32 b) { return TL32{a.v + b.v, a.d + b.d}; }
 JF_D TL32 operator-(TL32 a, TL32 b) { return TL32{a.v - b.v, a.d - b.d}; }
 JF_D TL32 operator*(TL32 a, TL32 b) { return TL32{a.v * b.v, fmaf(a.v, b.d, a.d * b.v)}; }
+// The tangent feeds only the preconditioner: quotients and square roots use the
+// hardware approximations (reciprocal, reciprocal square root; a few ulp)
+// instead of the correctly rounded FP32 sequences.
+JF_D float frcp(float x) { return __fdividef(1.0f, x); }
 JF_D TL32 operator/(TL32 a, TL32 b) {
-    const float ib = 1.0f / b.v;
+    const float ib = frcp(b.v);
     const float q = a.v * ib;
     return TL32{q, (a.d - q * b.d) * ib};
 }
 JF_D TL32 operator-(TL32 a) { return TL32{-a.v, -a.d}; }
 JF_D TL32 jsqrt(TL32 a) {
-    const float s = sqrtf(a.v);
-    return TL32{s, s > 0.0f ? 0.5f * a.d / s : 0.0f};
+    if (!(a.v > 0.0f)) return TL32{0.0f, 0.0f};
+    const float r = rsqrtf(a.v);
+    return TL32{a.v * r, 0.5f * a.d * r};
 }
 JF_D double val(TL32 a) { return (double)a.v; }
 JF_D TL32 jfma(TL32 a, TL32 b, TL32 c) { return a * b + c; }
+
+// Constants held in both precisions: the FP32 tangent takes the float copy, so
+// no double-to-float conversion (an FP64-pipe instruction) runs per use.
+JF_D D64 mkc(double d, float, D64) { return D64{d}; }
+JF_D TL32 mkc(double, float f, TL32) { return TL32{f, 0.0f}; }
+template <class S> JF_D S pick(double d, float f);
+template <> JF_D double pick<double>(double d, float) { return d; }
+template <> JF_D float pick<float>(double, float f) { return f; }

@@ -9,6 +9,7 @@
 struct PhysC {
     double gamma, R, p0, g, mu;
     double R_over_p0;   // R / p0
+    float gammaf, p0f, R_over_p0f, muf;   // float copies for the FP32 tangent
 };
 
 // p = p0 (R rho theta / p0)^gamma  (the EOS implied by eq. add-perturbation)
@@ -16,9 +17,9 @@ JF_D D64 pressure(D64 E, const PhysC &P, const PowTab *pt) {
     return D64{__dmul_rn(P.p0, pow_gamma_tab(__dmul_rn(P.R_over_p0, E.x), pt))};
 }
 JF_D TL32 pressure(TL32 E, const PhysC &P, const PowTab *) {
-    const float x = (float)P.R_over_p0 * E.v;
-    const float p = (float)P.p0 * __powf(x, (float)P.gamma);
-    return TL32{p, (float)P.gamma * p / E.v * E.d};
+    const float x = P.R_over_p0f * E.v;
+    const float p = P.p0f * __powf(x, P.gammaf);
+    return TL32{p, P.gammaf * p * frcp(E.v) * E.d};
 }
 
 template <class T>
@@ -44,7 +45,7 @@ template <class T, int D>
 JF_D void hllc(const T UL[4], const T UR[4], const PhysC &P, const PowTab *pt, T H[4]) {
     constexpr int iN = 1 + D, iT = 2 - D;
     const T one = mk(1.0, T{});
-    const T gam = mk(P.gamma, T{});
+    const T gam = mkc(P.gamma, P.gammaf, T{});
     const T irL = one / UL[0], irR = one / UR[0];
     const T uL = UL[iN] * irL, uR = UR[iN] * irR;
     const T pL = pressure(UL[3], P, pt), pR = pressure(UR[3], P, pt);
@@ -94,8 +95,8 @@ JF_D void mirror(const T U[4], T G[4]) {
 // A(U) dU with A = mu [[0,0,0,0],[-u,1,0,0],[-w,0,1,0],[-theta,0,0,1]]:
 // mu rho (0, d u, d w, d theta) for dU the derivative of U along one direction.
 template <class T>
-JF_D void viscous(const T U[4], const T dU[4], double mu, T F[4]) {
-    const T m = mk(mu, T{});
+JF_D void viscous(const T U[4], const T dU[4], const PhysC &P, T F[4]) {
+    const T m = mkc(P.mu, P.muf, T{});
     const T ir = mk(1.0, T{}) / U[0];
     F[0] = mk(0.0, T{});
     F[1] = m * (dU[1] - (U[1] * ir) * dU[0]);

@@ -239,6 +239,24 @@ def test_preconditioner_parity_at_fd_noise(case, split):
     assert err <= 1e-2
 
 
+@pytest.mark.parametrize("prec", [32, 16])
+def test_fp32_preconditioner_close_to_oracle(case, prec):
+    # the FP32 form (exact tangents in FP32 instead of FP64 difference quotients)
+    # applies the same Q^-1: agreement to FP32 rounding and the oracle's FD noise,
+    # far below the O(1) error a wrong tangent term would give
+    from oracle.fv import Multigrid
+    w, _, dg = case
+    ctx = gpu_context(w, precond_prec=prec)
+    Up = perturbed_state(w, dg, seed=19)
+    r = synth.random_perturbation(dg.shape[1:], 20)
+    z = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.mg_precondition(to_gpu(Up), w.dt, to_gpu(r), z)
+    mg = Multigrid(dg, w.fv_levels, w.mg_key)
+    mg.linearize(Up, w.dt)
+    err = rel(to_cpu(z, dg.shape), mg.apply(r))
+    assert err <= (2e-3 if prec == 32 else 2e-2), err
+
+
 def _oracle_step(w, dg, U0, scheme, key=None, levels=None):
     from oracle.fv import Multigrid
     from oracle.solver import implicit_step
