@@ -151,7 +151,7 @@ size_t workspace(const jfnk_grid *g, int k, const jfnk_opts *o, const jfnk_physi
     b += 8 * (4 + (visc ? 6 : 0)) * (fx + fz);
     if (prec != 64) b += 4 * (4 + (visc ? 6 : 0)) * (fx + fz);
     b += 8 * N * 9;                        // DG work vectors
-    b += 8 * N * (size_t)(m + 1);          // V
+    b += 12 * N * (size_t)(m + 1);         // V and its float copy
     const bool mg_on = o->mg_key[0] != 0;
     b += ((prec == 64 || !mg_on) ? 8 : 4) * N * (size_t)m;   // Z
     b += sS * N * 6;                       // pz, pz2, pd, pr, pin, pout
@@ -400,6 +400,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     // preconditioner z_j = v_j is copied in FP64
     const size_t sZ = (c->prec == 64 || !c->mg_on) ? 8 : 4;
     A_(c->V, 8 * N * (size_t)(m + 1));
+    A_(c->V32, 4 * N * (size_t)(m + 1));
     A_(c->Z, sZ * N * (size_t)m);
     A_(c->pz, sS * N);
     A_(c->pz2, sS * N);

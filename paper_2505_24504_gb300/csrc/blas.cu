@@ -43,10 +43,12 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;   // valid in thread 0
 }
 
-// true in the block that arrives last at the ticket (after its partials are visible)
+// true in the block that arrives last at the ticket (after its partials are
+// visible).  Partials are written by threads of the first warp only, so only
+// that warp fences.
 __device__ __forceinline__ bool last_block(unsigned *ticket) {
     __shared__ bool last;
-    __threadfence();
+    if (threadIdx.x < 32) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -93,15 +95,36 @@ __global__ void __launch_bounds__(RB) k_dot1(const S *x, const S *y, size_t n, d
 }
 
 // ---- CGS2 passes (NV basis vectors, two elements per thread and step) -------
-// h[j] = sum over blocks of part[j * nb + b], one warp per vector, fixed order
+template <int NV>
+__device__ __forceinline__ double warp_sum_scatter(const double (&a)[NV], int lane);
+
+// h[j] = sum over blocks of part[j * nb + b] by the whole block, fixed order:
+// thread t sums the partials b = t mod RB of every vector (all loads of a round
+// issued together), then one warp-and-block reduction of the NV sums.
 template <int NV>
 __device__ __forceinline__ void finish_multi(const double *part, int nb, double *h) {
+    constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+    __shared__ double fw[NV][RB / 32];
+    double a[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) a[j] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += RB) {
+        double v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = __ldcg(part + (size_t)j * nb + b);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) a[j] += v[j];
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = wid; j < NV; j += RB / 32) {
-        double a = 0.0;
-        for (int b = lane; b < nb; b += 32) a += __ldcg(part + (size_t)j * nb + b);
-        a = warp_sum(a);
-        if (lane == 0) h[j] = a;
+    const double w = warp_sum_scatter<NV>(a, lane);
+    const int j = lane / (32 / P);
+    if (lane % (32 / P) == 0 && j < NV) fw[j][wid] = w;
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < RB / 32; ++q) r += fw[threadIdx.x][q];
+        h[threadIdx.x] = r;
     }
 }
 
@@ -269,16 +292,78 @@ __global__ void __launch_bounds__(RB) k_gs_update_norm(const double *V, size_t l
     }
 }
 
-// v = w * inv (inv = 1/|w| from the Gram-Schmidt kernels), two elements per thread
-__global__ void k_scale_inv(const double *w, const double *inv, double *v, size_t n2) {
+// double -> float by truncation of the fraction on the integer pipe (error below
+// one float ulp; enough for the first Gram-Schmidt pass): binary32 exponent =
+// binary64 exponent - 896, fraction = the top 23 of the 52 bits (IEEE 754
+// formats).  Values outside the normal float range use the conversion instruction.
+__device__ __forceinline__ float d2f_trunc(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126 || e > 127) return (float)d;
+    const unsigned r = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e + 127) << 23) |
+                       (unsigned)((b >> 29) & 0x7fffffu);
+    return __uint_as_float(r);
+}
+
+// v = w * inv (inv = 1/|w| from the Gram-Schmidt kernels), two elements per
+// thread; also the float copy of v used by the next first passes (v32 may be null)
+__global__ void k_scale_inv(const double *w, const double *inv, double *v, float *v32, size_t n2) {
     const double s = *inv;
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     double2 *v2 = reinterpret_cast<double2 *>(v);
+    float2 *f2 = reinterpret_cast<float2 *>(v32);
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
         const double2 a = w2[i];
-        v2[i] = make_double2(a.x * s, a.y * s);
+        const double2 o = make_double2(a.x * s, a.y * s);
+        v2[i] = o;
+        if (v32) f2[i] = make_float2(d2f_trunc(o.x), d2f_trunc(o.y));
     }
+}
+
+// pass 1 in FP32: h = V^T w from the float copy of the basis and w truncated to
+// float, FP32 sums within a block, FP64 across blocks.  Its error (a float ulp
+// of |w|) is removed by the FP64 second pass, which computes the remaining
+// projection of w - V h exactly as classical Gram-Schmidt twice does.
+template <int NV>
+__global__ void __launch_bounds__(RB) k_gs_dot32(const float *V32, size_t ldv, const double *w, size_t n2,
+                                                 double *part, unsigned *ticket, double *h) {
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const float2 *Vp[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) Vp[j] = reinterpret_cast<const float2 *>(V32 + (size_t)j * ldv);
+    float acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0f;
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
+        const double2 a = w2[i];
+        const float ax = d2f_trunc(a.x), ay = d2f_trunc(a.y);
+        float2 v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] = fmaf(v[j].y, ay, fmaf(v[j].x, ax, acc[j]));
+    }
+    __shared__ float sw[NV][RB / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        float v = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sw[j][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < RB / 32; ++q) r += (double)sw[threadIdx.x][q];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = r;
+    }
+    if (!last_block(ticket)) return;
+    finish_multi<NV>(part, gridDim.x, h);
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 template <class S>
@@ -538,8 +623,9 @@ int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out,
 // CGS2 of w against V_0..V_{nv-1} (nv <= GS_FUSED_MAX; n even, V, w 16-byte
 // aligned), then w <- w / |w|: h1, h2, |w1|^2, the second-pass flag, |w| and
 // 1/|w| (nrm[S_INV - S_NORM]) land in device memory.
-// One wave: the SM count times the blocks of this kernel an SM holds (FP64-bound
-// kernels lose a partial second wave otherwise), fewer for short vectors.
+// One wave: the SM count times the blocks of this kernel an SM holds, at most
+// three (FP64-bound kernels lose a partial second wave otherwise), fewer for
+// short vectors.
 template <class F>
 static int one_wave(jfnk_ctx *c, F kernel, size_t n2) {
     int per_sm = 0;
@@ -547,6 +633,7 @@ static int one_wave(jfnk_ctx *c, F kernel, size_t n2) {
         cudaGetLastError();
         per_sm = 1;
     }
+    if (per_sm > 3) per_sm = 3;   // fewer partials for the closing block to add
     size_t g = (size_t)c->n_sm * per_sm;
     const size_t need = (n2 + RB - 1) / RB;
     if (g > need) g = need;
@@ -555,23 +642,28 @@ static int one_wave(jfnk_ctx *c, F kernel, size_t n2) {
 }
 
 template <int NV>
-static void cgs2_t(jfnk_ctx *c, const double *V, size_t ldv, double *w, size_t n, double *h1, double *h2,
-                   double *w1sq, double *nrm, double *flag, cudaStream_t s) {
+static void cgs2_t(jfnk_ctx *c, const double *V, const float *V32, size_t ldv, double *w, float *w32, size_t n,
+                   double *h1, double *h2, double *w1sq, double *nrm, double *flag, cudaStream_t s) {
     const size_t n2 = n / 2;
-    const int g1 = one_wave(c, k_gs_dot<NV>, n2), g2 = one_wave(c, k_gs_update_dot<NV>, n2),
-              g3 = one_wave(c, k_gs_update_norm<NV>, n2);
-    k_gs_dot<NV><<<g1, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
+    const int g2 = one_wave(c, k_gs_update_dot<NV>, n2), g3 = one_wave(c, k_gs_update_norm<NV>, n2);
+    if (V32) {
+        const int g1 = one_wave(c, k_gs_dot32<NV>, n2);
+        k_gs_dot32<NV><<<g1, RB, 0, s>>>(V32, ldv, w, n2, c->partial, c->ticket, h1);
+    } else {
+        const int g1 = one_wave(c, k_gs_dot<NV>, n2);
+        k_gs_dot<NV><<<g1, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
+    }
     k_gs_update_dot<NV><<<g2, RB, 0, s>>>(V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
     k_gs_update_norm<NV><<<g3, RB, 0, s>>>(V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
-    k_scale_inv<<<grid_for(n2), 256, 0, s>>>(w, nrm + (S_INV - S_NORM), w, n2);
+    k_scale_inv<<<grid_for(n2), 256, 0, s>>>(w, nrm + (S_INV - S_NORM), w, w32, n2);
     jf_launched(4);
 }
 
-int blas_cgs2(jfnk_ctx *c, const double *V, int nv, size_t ldv, double *w, size_t n, double *h1, double *h2,
-              double *w1sq, double *nrm, double *flag, cudaStream_t s) {
+int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv, double *w, float *w32, size_t n,
+              double *h1, double *h2, double *w1sq, double *nrm, double *flag, cudaStream_t s) {
     if (nv < 1 || nv > GS_FUSED_MAX || (n & 1) || (ldv & 1)) return JFNK_EINVAL;
     switch (nv) {
-#define JF_GS(K) case K: cgs2_t<K>(c, V, ldv, w, n, h1, h2, w1sq, nrm, flag, s); break;
+#define JF_GS(K) case K: cgs2_t<K>(c, V, V32, ldv, w, w32, n, h1, h2, w1sq, nrm, flag, s); break;
         JF_GS(1) JF_GS(2) JF_GS(3) JF_GS(4) JF_GS(5) JF_GS(6) JF_GS(7) JF_GS(8)
         JF_GS(9) JF_GS(10) JF_GS(11) JF_GS(12) JF_GS(13) JF_GS(14) JF_GS(15) JF_GS(16)
 #undef JF_GS

@@ -72,6 +72,7 @@ struct jfnk_ctx {
     double *fU, *w1, *w2, *Ubs, *Un, *Usave, *G, *dU;
     // Krylov basis: V (m+1) N doubles, Z m N of the preconditioner's type
     double *V;
+    float *V32;          // float copy of V (first Gram-Schmidt pass)
     void *Z;
     // preconditioner DG vectors (type of the preconditioner)
     void *pz, *pz2, *pd, *pr;
@@ -183,8 +184,10 @@ int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const do
                       double sign, const double *flag_in, double *w1sq, double *nrm, double *flag_out,
                       cudaStream_t s);
 constexpr int GS_FUSED_MAX = 16;   // basis vectors of the fused CGS2 kernels
-int blas_cgs2(jfnk_ctx *c, const double *V, int nv, size_t ldv, double *w, size_t n, double *h1, double *h2,
-              double *w1sq, double *nrm, double *flag, cudaStream_t s);
+// V32 (optional): float copy of the basis (first pass in FP32); w32: where the
+// float copy of the normalised w goes (may be null)
+int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv, double *w, float *w32, size_t n,
+              double *h1, double *h2, double *w1sq, double *nrm, double *flag, cudaStream_t s);
 int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s);
 int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);

@@ -103,8 +103,8 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
     // second pass runs only when the first lost more than half of |w|
     // (decided on the device)
     if (j + 1 <= GS_FUSED_MAX && (N & 1) == 0) {
-        JF_RET(blas_cgs2(c, V, j + 1, N, w, N, c->scal + S_H, c->scal + S_H2, c->scal + S_W1, c->scal + S_NORM,
-                         c->scal + S_FLAG, s));   // normalises w too
+        JF_RET(blas_cgs2(c, V, c->V32, j + 1, N, w, c->V32 + (size_t)(j + 1) * N, N, c->scal + S_H, c->scal + S_H2,
+                         c->scal + S_W1, c->scal + S_NORM, c->scal + S_FLAG, s));   // normalises w too
         if (ph) ph->mark(3, s);
         JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
         return JFNK_OK;
@@ -191,6 +191,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
     while (*its < maxit) {
         JF_CK(cudaMemcpyAsync(c->scal + S_NORM, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
         JF_RET(blas_scale_copy(r, c->scal + S_NORM, V, N, s));
+        JF_RET(blas_copy_d2f(V, c->V32, N, s));
         JF_CK(cudaStreamSynchronize(s));   // beta lives on the host stack
         memset(H, 0, sizeof(H));
         for (int i = 0; i <= m; ++i) g[i] = 0.0;
