@@ -74,6 +74,7 @@ __device__ __forceinline__ double finish_op(double acc, int op) {
 template <class S>
 __global__ void __launch_bounds__(RB) k_dot1(const S *x, const S *y, size_t n, double *part, unsigned *ticket,
                                              double *out, int op) {
+    jf_pdl_enter();
     double acc = 0.0, acc2 = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
     size_t i = (size_t)blockIdx.x * RB + threadIdx.x;
@@ -181,6 +182,7 @@ __device__ __forceinline__ void store_multi(const double (&acc)[NV], double *par
 template <int NV>
 __global__ void __launch_bounds__(RB) k_gs_dot(const double *V, size_t ldv, const double *w, size_t n2,
                                                double *part, unsigned *ticket, double *h) {
+    jf_pdl_enter();
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *Vp[NV];
 #pragma unroll
@@ -209,6 +211,7 @@ template <int NV>
 __global__ void __launch_bounds__(RB) k_gs_update_dot(const double *V, size_t ldv, double *w, size_t n2,
                                                       const double *h1, double *part, unsigned *ticket,
                                                       double *h2, double *w1sq, double *nrm, double *flag) {
+    jf_pdl_enter();
     double2 *wv = reinterpret_cast<double2 *>(w);
     const double2 *Vp[NV];
     double c[NV], acc[NV];
@@ -257,6 +260,7 @@ template <int NV>
 __global__ void __launch_bounds__(RB) k_gs_update_norm(const double *V, size_t ldv, double *w, size_t n2,
                                                        const double *h2, const double *flag, double *part,
                                                        unsigned *ticket, double *nrm) {
+    jf_pdl_enter();
     if (*flag == 0.0) return;
     double2 *wv = reinterpret_cast<double2 *>(w);
     const double2 *Vp[NV];
@@ -308,6 +312,7 @@ __device__ __forceinline__ float d2f_trunc(double d) {
 // v = w * inv (inv = 1/|w| from the Gram-Schmidt kernels), two elements per
 // thread; also the float copy of v used by the next first passes (v32 may be null)
 __global__ void k_scale_inv(const double *w, const double *inv, double *v, float *v32, size_t n2) {
+    jf_pdl_enter();
     const double s = *inv;
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     double2 *v2 = reinterpret_cast<double2 *>(v);
@@ -328,6 +333,7 @@ __global__ void k_scale_inv(const double *w, const double *inv, double *v, float
 template <int NV>
 __global__ void __launch_bounds__(RB) k_gs_dot32(const float *V32, size_t ldv, const double *w, size_t n2,
                                                  double *part, unsigned *ticket, double *h) {
+    jf_pdl_enter();
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const float2 *Vp[NV];
 #pragma unroll
@@ -368,6 +374,7 @@ __global__ void __launch_bounds__(RB) k_gs_dot32(const float *V32, size_t ldv, c
 
 template <class S>
 __global__ void __launch_bounds__(RB) k_dot_partial(const S *x, const S *y, size_t n, double *part) {
+    jf_pdl_enter();
     double acc = 0.0, acc2 = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
     size_t i = (size_t)blockIdx.x * RB + threadIdx.x;
@@ -390,6 +397,7 @@ __global__ void __launch_bounds__(RB) k_dot_partial(const S *x, const S *y, size
 template <int NV>
 __global__ void __launch_bounds__(RB) k_mdot_partial(const double *V, size_t ldv, const double *w, size_t n,
                                                      double *part, const double *flag) {
+    jf_pdl_enter();
     if (flag && *flag == 0.0) {   // pass not needed: contribute zeros
         if (threadIdx.x < NV) part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = 0.0;
         return;
@@ -432,6 +440,7 @@ __global__ void __launch_bounds__(RB) k_mdot_partial(const double *V, size_t ldv
 }
 
 __global__ void __launch_bounds__(RB) k_mfinal(const double *part, int nb, double *out) {
+    jf_pdl_enter();
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += RB) acc += part[(size_t)blockIdx.x * nb + i];
     acc = block_sum(acc);
@@ -441,6 +450,7 @@ __global__ void __launch_bounds__(RB) k_mfinal(const double *part, int nb, doubl
 // w += sign * sum_j h_j V_j
 __global__ void k_mupdate(const double *V, int nv, size_t ldv, const double *h, double *w, size_t n,
                           double sign, const double *flag) {
+    jf_pdl_enter();
     if (flag && *flag == 0.0) return;
     __shared__ double sh[MAXV];
     if (threadIdx.x < nv) sh[threadIdx.x] = sign * h[threadIdx.x];
@@ -454,6 +464,7 @@ __global__ void k_mupdate(const double *V, int nv, size_t ldv, const double *h, 
 }
 
 __global__ void k_scale_copy(const double *w, const double *nrm, double *v, size_t n) {
+    jf_pdl_enter();
     const double s = *nrm;
     const double inv = s != 0.0 ? 1.0 / s : 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -461,6 +472,7 @@ __global__ void k_scale_copy(const double *w, const double *nrm, double *v, size
 }
 
 __global__ void k_axpby(double a, const double *x, double b, const double *y, double *z, size_t n) {
+    jf_pdl_enter();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         z[i] = a * x[i] + (y ? b * y[i] : 0.0);
@@ -472,6 +484,7 @@ template <int NVMAX>
 __global__ void __launch_bounds__(RB) k_mupdate_norm(const double *V, int nv, size_t ldv, const double *h,
                                                      double *w, size_t n, double sign, const double *flag,
                                                      double *part) {
+    jf_pdl_enter();
     if (flag && *flag == 0.0) return;
     __shared__ double sh[NVMAX];
     if (threadIdx.x < nv) sh[threadIdx.x] = sign * h[threadIdx.x];
@@ -494,6 +507,7 @@ __global__ void __launch_bounds__(RB) k_mupdate_norm(const double *V, int nv, si
 __global__ void __launch_bounds__(RB) k_final_gs(const double *part, int nb, const double *h, int nv,
                                                  const double *flag_in, double *w1sq, double *nrm,
                                                  double *flag_out) {
+    jf_pdl_enter();
     if (flag_in && *flag_in == 0.0) return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += RB) acc += part[i];
@@ -535,6 +549,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // per-thread partials in FP64.
 __global__ void __launch_bounds__(RB) k_f2d_eps(const float *x, double *y, size_t n, double *part, unsigned *ticket,
                                                 double *eps) {
+    jf_pdl_enter();
     float acc = 0.0f, acc2 = 0.0f;
     const size_t stride = (size_t)gridDim.x * RB;
     const size_t n4 = n / 4;   // float4 in, two double2 out (x, y 16-byte aligned)
@@ -571,6 +586,7 @@ __device__ __forceinline__ double widen(double d) { return d; }
 
 template <class S>
 __global__ void k_zcomb(const S *Z, int nz, size_t n, YV yv, double *x) {
+    jf_pdl_enter();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double acc = x[i];
@@ -580,10 +596,12 @@ __global__ void k_zcomb(const S *Z, int nz, size_t n, YV yv, double *x) {
 }
 
 __global__ void k_d2f(const double *x, float *y, size_t n) {
+    jf_pdl_enter();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
 }
 __global__ void k_f2d(const float *x, double *y, size_t n) {
+    jf_pdl_enter();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = f2d_bits(x[i]);
 }
@@ -608,14 +626,14 @@ inline int nblocks_red(jfnk_ctx *c, size_t n) {
 
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    k_dot1<double><<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, out, op); jf_launched();
+    jf_launch(k_dot1<double>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    k_dot1<float><<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, out, op); jf_launched();
+    jf_launch(k_dot1<float>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -648,14 +666,14 @@ static void cgs2_t(jfnk_ctx *c, const double *V, const float *V32, size_t ldv, d
     const int g2 = one_wave(c, k_gs_update_dot<NV>, n2), g3 = one_wave(c, k_gs_update_norm<NV>, n2);
     if (V32) {
         const int g1 = one_wave(c, k_gs_dot32<NV>, n2);
-        k_gs_dot32<NV><<<g1, RB, 0, s>>>(V32, ldv, w, n2, c->partial, c->ticket, h1);
+        jf_launch(k_gs_dot32<NV>, g1, RB, 0, s, V32, ldv, w, n2, c->partial, c->ticket, h1);
     } else {
         const int g1 = one_wave(c, k_gs_dot<NV>, n2);
-        k_gs_dot<NV><<<g1, RB, 0, s>>>(V, ldv, w, n2, c->partial, c->ticket, h1);
+        jf_launch(k_gs_dot<NV>, g1, RB, 0, s, V, ldv, w, n2, c->partial, c->ticket, h1);
     }
-    k_gs_update_dot<NV><<<g2, RB, 0, s>>>(V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
-    k_gs_update_norm<NV><<<g3, RB, 0, s>>>(V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
-    k_scale_inv<<<grid_for(n2), 256, 0, s>>>(w, nrm + (S_INV - S_NORM), w, w32, n2);
+    jf_launch(k_gs_update_dot<NV>, g2, RB, 0, s, V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
+    jf_launch(k_gs_update_norm<NV>, g3, RB, 0, s, V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
+    jf_launch(k_scale_inv, grid_for(n2), 256, 0, s, w, nrm + (S_INV - S_NORM), w, w32, n2);
     jf_launched(4);
 }
 
@@ -675,7 +693,7 @@ int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv
 template <int NV>
 void mdot_chunk(const double *V, size_t ldv, const double *w, size_t n, double *part, int nb, cudaStream_t s,
                 const double *flag) {
-    k_mdot_partial<NV><<<nb, RB, 0, s>>>(V, ldv, w, n, part, flag);
+    jf_launch(k_mdot_partial<NV>, nb, RB, 0, s, V, ldv, w, n, part, flag);
 }
 
 int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h,
@@ -704,7 +722,7 @@ int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w,
             default: mdot_chunk<16>(Vj, ldv, w, n, c->partial, nb, s, flag); break;
         }
         jf_launched();
-        k_mfinal<<<m, RB, 0, s>>>(c->partial, nb, h + j0); jf_launched();
+        jf_launch(k_mfinal, m, RB, 0, s, c->partial, nb, h + j0); jf_launched();
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -715,20 +733,20 @@ int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double 
     (void)c;
     for (int j0 = 0; j0 < nv; j0 += MAXV) {
         const int m = nv - j0 < MAXV ? nv - j0 : MAXV;
-        k_mupdate<<<grid_for(n), 256, 0, s>>>(V + (size_t)j0 * ldv, m, ldv, h + j0, w, n, sign, flag); jf_launched();
+        jf_launch(k_mupdate, grid_for(n), 256, 0, s, V + (size_t)j0 * ldv, m, ldv, h + j0, w, n, sign, flag); jf_launched();
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int blas_scale_copy(const double *w, const double *nrm, double *v, size_t n, cudaStream_t s) {
-    k_scale_copy<<<grid_for(n), 256, 0, s>>>(w, nrm, v, n); jf_launched();
+    jf_launch(k_scale_copy, grid_for(n), 256, 0, s, w, nrm, v, n); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s) {
-    k_axpby<<<grid_for(n), 256, 0, s>>>(a, x, b, y, z, n); jf_launched();
+    jf_launch(k_axpby, grid_for(n), 256, 0, s, a, x, b, y, z, n); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -743,9 +761,9 @@ int blas_zcomb(const void *Z, int prec32, int nzv, size_t n, const double *yv, d
         YV y;
         for (int j = 0; j < m; ++j) y.y[j] = yv[j0 + j];
         if (prec32)
-            k_zcomb<float><<<grid_for(n), 256, 0, s>>>((const float *)Z + (size_t)j0 * n, m, n, y, x);
+            jf_launch(k_zcomb<float>, grid_for(n), 256, 0, s, (const float *)Z + (size_t)j0 * n, m, n, y, x);
         else
-            k_zcomb<double><<<grid_for(n), 256, 0, s>>>((const double *)Z + (size_t)j0 * n, m, n, y, x);
+            jf_launch(k_zcomb<double>, grid_for(n), 256, 0, s, (const double *)Z + (size_t)j0 * n, m, n, y, x);
         jf_launched();
     }
     JF_CK(cudaGetLastError());
@@ -756,6 +774,7 @@ int blas_zcomb(const void *Z, int prec32, int nzv, size_t n, const double *yv, d
 // |w1|^2 of |w0|^2 = |w1|^2 + |h|^2; reorthogonalise when |w1| < |w0| / sqrt(2)
 // ("twice is enough").  flag = 1.0 or 0.0, decided on the device.
 __global__ void k_reortho_flag(const double *w1sq, const double *h, int nv, double *flag) {
+    jf_pdl_enter();
     double hh = 0.0;
     for (int i = threadIdx.x; i < nv; i += 32) hh += h[i] * h[i];
     hh = warp_sum(hh);
@@ -763,7 +782,7 @@ __global__ void k_reortho_flag(const double *w1sq, const double *h, int nv, doub
 }
 
 int blas_reortho_flag(const double *w1sq, const double *h, int nv, double *flag, cudaStream_t s) {
-    k_reortho_flag<<<1, 32, 0, s>>>(w1sq, h, nv, flag);
+    jf_launch(k_reortho_flag, 1, 32, 0, s, w1sq, h, nv, flag);
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -775,17 +794,17 @@ int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const do
     if (nv > MAXV) {   // long bases: plain updates, then the norm pass
         JF_RET(blas_mupdate(c, V, nv, ldv, h, w, n, sign, s, flag_in));
         const int nb = nblocks_red(c, n);
-        k_dot_partial<double><<<nb, RB, 0, s>>>(w, w, n, c->partial);
+        jf_launch(k_dot_partial<double>, nb, RB, 0, s, w, w, n, c->partial);
         jf_launched();
-        k_final_gs<<<1, RB, 0, s>>>(c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
+        jf_launch(k_final_gs, 1, RB, 0, s, c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
         jf_launched();
         JF_CK(cudaGetLastError());
         return JFNK_OK;
     }
     const int nb = nblocks_red(c, n);
-    k_mupdate_norm<MAXV><<<nb, RB, 0, s>>>(V, nv, ldv, h, w, n, sign, flag_in, c->partial);
+    jf_launch(k_mupdate_norm<MAXV>, nb, RB, 0, s, V, nv, ldv, h, w, n, sign, flag_in, c->partial);
     jf_launched();
-    k_final_gs<<<1, RB, 0, s>>>(c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
+    jf_launch(k_final_gs, 1, RB, 0, s, c->partial, nb, h, nv, flag_in, w1sq, nrm, flag_out);
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
@@ -794,20 +813,20 @@ int blas_mupdate_norm(jfnk_ctx *c, const double *V, int nv, size_t ldv, const do
 int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s) {
     if (((uintptr_t)x & 15) || ((uintptr_t)y & 15)) return JFNK_EINVAL;
     const int nb = nblocks_red(c, n);
-    k_f2d_eps<<<nb, RB, 0, s>>>(x, y, n, c->partial, c->ticket, eps_out);
+    jf_launch(k_f2d_eps, nb, RB, 0, s, x, y, n, c->partial, c->ticket, eps_out);
     jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int blas_copy_d2f(const double *x, float *y, size_t n, cudaStream_t s) {
-    k_d2f<<<grid_for(n), 256, 0, s>>>(x, y, n); jf_launched();
+    jf_launch(k_d2f, grid_for(n), 256, 0, s, x, y, n); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int blas_copy_f2d(const float *x, double *y, size_t n, cudaStream_t s) {
-    k_f2d<<<grid_for(n), 256, 0, s>>>(x, y, n); jf_launched();
+    jf_launch(k_f2d, grid_for(n), 256, 0, s, x, y, n); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }

@@ -77,6 +77,7 @@ template <class T, int IN, int NP1, bool VISC>
 __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
                                                typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
                                                typename OutT<T>::type *symz) {
+    jf_pdl_enter();
     typedef typename OutT<T>::type O;
     __shared__ PowTab spt;
     if (IN != 2) load_powtab(&spt, K.pt);   // the FP32 tangent power needs no table
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
                                                 const typename OutT<T>::type *symx,
                                                 const typename OutT<T>::type *phiz,
                                                 const typename OutT<T>::type *symz) {
+    jf_pdl_enter();
     typedef typename OutT<T>::type O;
     constexpr int NP = NP1 * NP1;
     constexpr int EPB = EPBOf<NP1, TV>::value;
@@ -426,6 +428,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
 // background fluxes at node rows and horizontal faces, with the residual's own
 // D64 functions so that U' = 0 cancels bit for bit
 __global__ void k_bg_dg(DGK K, double *fbx, double *fbz, double *hbx, double *hbxw, double *hbz) {
+    jf_pdl_enter();
     __shared__ PowTab spt;
     load_powtab(&spt, K.pt);
     __syncthreads();
@@ -524,16 +527,16 @@ int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, 
     const long long nf = (long long)K.nz * (K.nx + 1) * NP1 + (long long)(K.nz + 1) * K.nx * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
     const int tf = c->opts.tile_faces;
-    k_faces<T, IN, NP1, VISC><<<(unsigned)((nf + tf - 1) / tf), tf, 0, s>>>(K, ld, phix, symx, phiz, symz); jf_launched();
+    jf_launch(k_faces<T, IN, NP1, VISC>, (unsigned)((nf + tf - 1) / tf), tf, 0, s, K, ld, phix, symx, phiz, symz); jf_launched();
     if (c->timing) JF_CK(cudaEventRecord(c->tev[1], s));
     if (c->opts.tile_volume == 1) {
         constexpr int EPB = EPBOf<NP1, 1>::value;
         const int nb = (K.n_el + EPB - 1) / EPB;
-        k_volume<T, IN, MODE, NP1, VISC, 1><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz);
+        jf_launch(k_volume<T, IN, MODE, NP1, VISC, 1>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
     } else {
         constexpr int EPB = EPBOf<NP1, 2>::value;
         const int nb = (K.n_el + EPB - 1) / EPB;
-        k_volume<T, IN, MODE, NP1, VISC, 2><<<nb, EPB * NP1 * NP1, 0, s>>>(K, ld, a, phix, symx, phiz, symz);
+        jf_launch(k_volume<T, IN, MODE, NP1, VISC, 2>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
     }
     jf_launched();
     JF_CK(cudaGetLastError());

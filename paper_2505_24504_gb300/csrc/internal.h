@@ -4,13 +4,49 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <mutex>
+#include <utility>
 
 #include "../../include/jfnk.h"
 #include "physics.cuh"
 
 #define JF_MAXLEV 12
+
+// Programmatic dependent launch: the solver's kernels are launched with
+// programmatic stream serialisation and each first waits (griddepcontrol.wait)
+// for its predecessor grid to complete with its memory writes visible, so no
+// read or write moves ahead of that point.  The successor is released when the
+// predecessor completes (no early trigger: blocks that wait early would hold
+// SM resources the predecessor still needs); what is saved is part of the
+// launch latency between dependent kernels.  JFNK_PDL=0 in the environment
+// launches them with plain stream ordering.
+#ifdef __CUDACC__
+__device__ __forceinline__ void jf_pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t jf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    static const int pdl = [] {
+        const char *e = getenv("JFNK_PDL");
+        return e ? atoi(e) : 1;
+    }();
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Fixed 1D tables of the nodal Q_k space on Gauss-Legendre nodes (k <= 4).
 struct DGTab {

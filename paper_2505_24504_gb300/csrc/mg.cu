@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
                                             const double *fu, double adt, typename SOf<T>::type *out,
                                             int bf16 = 0) {
+    jf_pdl_enter();
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
     if (IN != 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
                                                             const double *fu, double adt, int fac,
                                                             typename SOf<T>::type *bc, typename SOf<T>::type *xc,
                                                             const typename SOf<T>::type *dtau_c, int bf16) {
+    jf_pdl_enter();
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
     if (IN != 2) load_pt(&spt, K.pt);
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
                                                       double adt, typename SOf<T>::type *out,
                                                       typename SOf<T>::type *xc,
                                                       const typename SOf<T>::type *dtau_c, int bf16) {
+    jf_pdl_enter();
     typedef typename SOf<T>::type S;
     constexpr int TX = FV_TX;
     __shared__ PowTab spt;
@@ -566,6 +569,7 @@ JF_D float wave_speed_r<float>(const float U[4], int D, const PhysC &P, const Po
 
 template <class S>
 __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) {
+    jf_pdl_enter();
     __shared__ PowTab spt;
     load_pt(&spt, K.pt);
     __syncthreads();
@@ -596,6 +600,7 @@ __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) 
 __global__ void k_dg_dtau(const double *U, const double *ubv, int nx, int nz, int np1, PhysC pc,
                           const PowTab *pt, double ihx, double ihz, double mu, double adt, double sigma,
                           double *dtau, float *dtauf) {
+    jf_pdl_enter();
     __shared__ PowTab spt;
     load_pt(&spt, pt);
     __syncthreads();
@@ -644,6 +649,7 @@ __device__ __forceinline__ void load_ttab(const TK &K, R sV[NP1][NP1], R sVi[NP1
 // elements x NP subcells.
 template <class Si, class So, int NP1>
 __global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix, So *x0, const So *dtau0) {
+    jf_pdl_enter();
     typedef typename RealOf<Si, So>::type R;
     constexpr int NP = NP1 * NP1;
     constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
@@ -708,6 +714,7 @@ __global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int mas
 // T^-1_mf: FV (Si) -> DG (So); acc 0: store, 1: add
 template <class Si, class So, int NP1>
 __global__ void __launch_bounds__(128) k_to_dg(TK K, const Si *v, So *u, int massfix, int acc_mode) {
+    jf_pdl_enter();
     typedef typename RealOf<Si, So>::type R;
     constexpr int NP = NP1 * NP1;
     constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
@@ -769,6 +776,7 @@ __global__ void __launch_bounds__(128) k_to_dg(TK K, const Si *v, So *u, int mas
 // R: coarse = mean of fac x fac children
 template <class S>
 __global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
+    jf_pdl_enter();
     const int NXc = NXf / fac, NZc = NZf / fac;
     const size_t nc = (size_t)NXc * NZc;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -787,6 +795,7 @@ __global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
 // when x_c is given, x_c = dtau_c b_c
 template <class S>
 __global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc, const S *dtau_c, int bf16 = 0) {
+    jf_pdl_enter();
     const int NXc = NXf / fac, NZc = NZf / fac;
     const size_t nc = (size_t)NXc * NZc;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -806,6 +815,7 @@ __global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc
 // x = (zero ? 0 : x) - P v
 template <class S>
 __global__ void k_prolong(S *x, const S *vc, int NXf, int NZf, int fac, int zero) {
+    jf_pdl_enter();
     const size_t nf = (size_t)NXf * NZf;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * nf) return;
@@ -820,6 +830,7 @@ __global__ void k_prolong(S *x, const S *vc, int NXf, int NZf, int fac, int zero
 // x = dtau b (first smoothing step from zero)
 template <class S>
 __global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1) {
+    jf_pdl_enter();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * n1) return;
     x[t] = dtau[t % n1] * b[t];
@@ -827,6 +838,7 @@ __global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1) {
 
 template <class S>
 __global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int NP) {
+    jf_pdl_enter();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * N1) return;
     z[t] = dtau[(t % N1) / NP] * r[t];
@@ -834,17 +846,20 @@ __global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int 
 
 template <class S>
 __global__ void k_neg(S *x, const S *b, size_t n) {
+    jf_pdl_enter();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) x[t] = -b[t];
 }
 
 template <class S>
-__global__ void k_sub(const S *r, const S *w, S *d, size_t n) {   // d = r - w
+__global__ void k_sub(const S *r, const S *w, S *d, size_t n) {
+    jf_pdl_enter();   // d = r - w
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) d[t] = r[t] - w[t];
 }
 
 __global__ void k_bg_fv(FVK K, double *hbx, double *hbxw, double *hbz) {
+    jf_pdl_enter();
     __shared__ PowTab spt;
     load_pt(&spt, K.pt);
     __syncthreads();
@@ -937,10 +952,10 @@ int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s, So *x0 = nullptr, con
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: k_to_fv<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 3: k_to_fv<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 4: k_to_fv<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 5: k_to_fv<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 2: jf_launch(k_to_fv<Si, So, 2>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 3: jf_launch(k_to_fv<Si, So, 3>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 4: jf_launch(k_to_fv<Si, So, 4>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 5: jf_launch(k_to_fv<Si, So, 5>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -954,10 +969,10 @@ int to_dg(jfnk_ctx *c, const Si *v, So *u, int acc, cudaStream_t s) {
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: k_to_dg<Si, So, 2><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 3: k_to_dg<Si, So, 3><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 4: k_to_dg<Si, So, 4><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 5: k_to_dg<Si, So, 5><<<g, EPB * NP, 0, s>>>(K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 2: jf_launch(k_to_dg<Si, So, 2>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 3: jf_launch(k_to_dg<Si, So, 3>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 4: jf_launch(k_to_dg<Si, So, 4>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 5: jf_launch(k_to_dg<Si, So, 5>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -976,10 +991,10 @@ void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const 
                const typename SOf<T>::type *x, const typename SOf<T>::type *b, const typename SOf<T>::type *dt,
                const double *fu, double adt, typename SOf<T>::type *out, int bf = 0) {
     if (l4) {
-        k_fv<T, IN, MODE, V, 4><<<g, tb, 0, s>>>(K, ld, x, b, dt, fu, adt, out, bf);
+        jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf);
     } else {
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 7) / 8));
-        k_fv_tile<T, IN, MODE, V, 8><<<gt, FV_TX * 8, 0, s>>>(K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
+        jf_launch(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
     }
     jf_launched();
 }
@@ -1058,7 +1073,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     const bool f2 = L.fac == 2;
     const unsigned g = nblk((l4 ? (f2 ? 16 : 4) : 1) * nc, tb);   // lanes per coarse cell
     c->fv_calls++;
-#define JF_DR(T, IN, V, LN, F2, ...) k_fv_defect_restrict<T, IN, V, LN, F2><<<g, tb, 0, s>>>(__VA_ARGS__)
+#define JF_DR(T, IN, V, LN, F2, ...) jf_launch(k_fv_defect_restrict<T, IN, V, LN, F2>, g, tb, 0, s, __VA_ARGS__)
 #define JF_DR2(T, IN, V, ...)                                \
     do {                                                     \
         if (!l4) JF_DR(T, IN, V, 1, false, __VA_ARGS__);     \
@@ -1068,7 +1083,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     // large levels with 2 x 2 agglomeration: the face-once tile kernel
     const unsigned gt = (unsigned)(((L.NX + FV_TX - 1) / FV_TX) * ((L.NZ + 7) / 8));
 #define JF_DRT(T, IN, V, ld, bb, fuu, outc, xcc, dtc_, bff)                                                 \
-    k_fv_tile<T, IN, FV_DEFRES, V, 8><<<gt, FV_TX * 8, 0, s>>>(K, ld, bb, nullptr, fuu, c->mg_adt, outc, xcc, \
+    jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, outc, xcc, \
                                                                  dtc_, bff)
     if (!l4 && f2) {
         if (c->prec == 64) {
@@ -1138,7 +1153,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     auto smooth = [&](int steps) -> int {
         for (int i = 0; i < steps; ++i) {
             if (zero) {
-                k_scale_dtau<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)L.b, (const S *)L.dtau, n1);
+                jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)L.b, (const S *)L.dtau, n1);
                 jf_launched();
                 zero = false;
             } else {
@@ -1159,12 +1174,12 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             // FP64: separate defect and restriction (one thread per fine cell keeps the
             // FP64-bound defect kernel occupied)
             if (zero) {
-                k_neg<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.r, (const S *)L.b, L.n);
+                jf_launch(k_neg<S>, nblk(L.n, 256), 256, 0, s, (S *)L.r, (const S *)L.b, L.n);
                 jf_launched();
             } else {
                 JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
             }
-            k_restrict_b<S><<<nblk(C.n, 256), 256, 0, s>>>((const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
+            jf_launch(k_restrict_b<S>, nblk(C.n, 256), 256, 0, s, (const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
                                                            fuse ? (S *)C.x : nullptr, (const S *)C.dtau,
                                                            (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0);
             jf_launched();
@@ -1178,7 +1193,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             vz = false;
             fd = false;
         }
-        k_prolong<S><<<nblk(L.n, 256), 256, 0, s>>>((S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
+        jf_launch(k_prolong<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
         jf_launched();
         zero = false;
     }
@@ -1195,7 +1210,7 @@ template <>
 int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        k_scale_dtau_dg<double><<<nblk(c->N, 256), 256, 0, s>>>(z, r, c->dtau_dg, c->npt, NP); jf_launched();
+        jf_launch(k_scale_dtau_dg<double>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dg, c->npt, NP); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1221,7 +1236,7 @@ template <>
 int dg_smooth_step<float>(jfnk_ctx *c, const float *r, float *&z, float *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        k_scale_dtau_dg<float><<<nblk(c->N, 256), 256, 0, s>>>(z, r, c->dtau_dgf, c->npt, NP); jf_launched();
+        jf_launch(k_scale_dtau_dg<float>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dgf, c->npt, NP); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1256,7 +1271,7 @@ int dg_defect<double>(jfnk_ctx *c, const double *r, const double *z, double *d, 
     a.adt = c->mg_adt;
     a.out0 = c->w2;
     JF_RET(dg_apply(c, DG_JV, a, s));
-    k_sub<double><<<nblk(c->N, 256), 256, 0, s>>>(r, c->w2, d, c->N); jf_launched();
+    jf_launch(k_sub<double>, nblk(c->N, 256), 256, 0, s, r, c->w2, d, c->N); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -1270,7 +1285,7 @@ int dg_defect<float>(jfnk_ctx *c, const float *r, const float *z, float *d, cuda
     a.adt = c->mg_adt;
     a.out0 = d;
     JF_RET(dg_apply(c, DG_TLJV, a, s));
-    k_sub<float><<<nblk(c->N, 256), 256, 0, s>>>(r, d, d, c->N); jf_launched();
+    jf_launch(k_sub<float>, nblk(c->N, 256), 256, 0, s, r, d, d, c->N); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -1326,7 +1341,7 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
     const double *U = c->Ulin;
     c->mg_adt = adt;
     c->mg_U = U;
-    k_dg_dtau<<<nblk(c->n_el), 128, 0, s>>>(U, c->ubv, c->grid.nx, c->grid.nz, c->np1, c->pc, c->powtab,
+    jf_launch(k_dg_dtau, nblk(c->n_el), 128, 0, s, U, c->ubv, c->grid.nx, c->grid.nz, c->np1, c->pc, c->powtab,
                                              1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt, c->opts.sigma_dg,
                                              c->dtau_dg, c->dtau_dgf); jf_launched();
     JF_CK(cudaGetLastError());
@@ -1343,18 +1358,18 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
         if (l > 0) {
             FVLev &F = c->lev[l - 1];
             if (c->prec == 64)
-                k_restrict<double><<<nblk(L.n, 256), 256, 0, s>>>((const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
+                jf_launch(k_restrict<double>, nblk(L.n, 256), 256, 0, s, (const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
             else
-                k_restrict_b<float><<<nblk(L.n, 256), 256, 0, s>>>((const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u,
+                jf_launch(k_restrict_b<float>, nblk(L.n, 256), 256, 0, s, (const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u,
                                                                    nullptr, nullptr,
                                                                    (c->prec == 16 && l == c->nlev - 1) ? 1 : 0);
             jf_launched();
         }
         if (c->prec == 64) {
             JF_RET(fv_op64(c, l, FV_RES, (const double *)L.u, nullptr, nullptr, (double *)L.fu, s));
-            k_fv_dtau<double><<<nblk(n1), 128, 0, s>>>(K, (const double *)L.u, adt, c->opts.sigma_fv, (double *)L.dtau); jf_launched();
+            jf_launch(k_fv_dtau<double>, nblk(n1), 128, 0, s, K, (const double *)L.u, adt, c->opts.sigma_fv, (double *)L.dtau); jf_launched();
         } else {
-            k_fv_dtau<float><<<nblk(n1), 128, 0, s>>>(K, (const float *)L.u, adt, c->opts.sigma_fv, (float *)L.dtau); jf_launched();
+            jf_launch(k_fv_dtau<float>, nblk(n1), 128, 0, s, K, (const float *)L.u, adt, c->opts.sigma_fv, (float *)L.dtau); jf_launched();
         }
         JF_CK(cudaGetLastError());
     }
