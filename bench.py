@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 512 << 20
 # instructions of their IEEE-correct sequences; x^gamma the table power's.
 FLOPS_FACE_POINT = 298.0   # k_faces, FD product (profiles/dg_fp64_fd_product_w2.md)
 FLOPS_NODE = 185.0         # k_volume, FD product
-TRAFFIC_FACE = 13_271_296  # dram read + write bytes of one k_faces FD launch (ncu, cold L2)
+TRAFFIC_FACE = 13_275_392  # dram read + write bytes of one k_faces FD launch (ncu, cold L2; writes stay in L2)
 
 
 def parse():

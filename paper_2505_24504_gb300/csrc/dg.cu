@@ -24,6 +24,10 @@ struct DGK {
     double two_hx, two_hz, g, mu, eta_x, eta_z;
     float two_hxf, two_hzf, gf, eta_xf, eta_zf;   // float copies for the FP32 tangent
     float tlp[5], tlm[5], tdlp[5], tdlm[5];       // trace tables l_a(+-1), l_a'(+-1) in float
+    // volume tables with the 2/h factors folded in, built on the host in both
+    // precisions: Dx = (2/hx) Dw, Dz = (2/hz) Dw, lift[0..3] x-lifts, lift[4..7] z-lifts
+    double Dx[5][5], Dz[5][5], lift[8][5];
+    float Dxf[5][5], Dzf[5][5], Dnf[5][5], liftf[8][5];
     PhysC pc;
     const PowTab *pt;
     const double *ubv, *dubv, *fbx, *fbz, *hbx, *hbxw, *ubh, *dubh, *hbz;
@@ -295,20 +299,14 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     ld.prepare();
     if (threadIdx.x < NP) {
         const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
-        sDx[r][q] = (O)(K.two_hx * K.tab.Dw[r][q]);
-        sDz[r][q] = (O)(K.two_hz * K.tab.Dw[r][q]);
-        sDn[r][q] = (O)K.tab.Dn[r][q];
+        sDx[r][q] = pick<O>(K.Dx[r][q], K.Dxf[r][q]);
+        sDz[r][q] = pick<O>(K.Dz[r][q], K.Dzf[r][q]);
+        sDn[r][q] = pick<O>(K.tab.Dn[r][q], K.Dnf[r][q]);
     }
     if (threadIdx.x < NP1) {
         const int q = threadIdx.x;
-        sl[0][q] = (O)(K.two_hx * K.tab.lmw[q]);
-        sl[1][q] = (O)(K.two_hx * K.tab.lpw[q]);
-        sl[2][q] = (O)(K.two_hx * K.two_hx * K.tab.dlmw[q]);
-        sl[3][q] = (O)(K.two_hx * K.two_hx * K.tab.dlpw[q]);
-        sl[4][q] = (O)(K.two_hz * K.tab.lmw[q]);
-        sl[5][q] = (O)(K.two_hz * K.tab.lpw[q]);
-        sl[6][q] = (O)(K.two_hz * K.two_hz * K.tab.dlmw[q]);
-        sl[7][q] = (O)(K.two_hz * K.two_hz * K.tab.dlpw[q]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sl[r][q] = pick<O>(K.lift[r][q], K.liftf[r][q]);
     }
     const int le = threadIdx.x / NP;
     const int node = threadIdx.x % NP;
@@ -500,6 +498,25 @@ DGK make_K(jfnk_ctx *c) {
     K.two_hzf = (float)K.two_hz;
     K.eta_xf = (float)K.eta_x;
     K.eta_zf = (float)K.eta_z;
+    for (int r = 0; r < 5; ++r)
+        for (int q = 0; q < 5; ++q) {
+            K.Dx[r][q] = K.two_hx * K.tab.Dw[r][q];
+            K.Dz[r][q] = K.two_hz * K.tab.Dw[r][q];
+            K.Dxf[r][q] = (float)K.Dx[r][q];
+            K.Dzf[r][q] = (float)K.Dz[r][q];
+            K.Dnf[r][q] = (float)K.tab.Dn[r][q];
+        }
+    for (int q = 0; q < 5; ++q) {
+        K.lift[0][q] = K.two_hx * K.tab.lmw[q];
+        K.lift[1][q] = K.two_hx * K.tab.lpw[q];
+        K.lift[2][q] = K.two_hx * K.two_hx * K.tab.dlmw[q];
+        K.lift[3][q] = K.two_hx * K.two_hx * K.tab.dlpw[q];
+        K.lift[4][q] = K.two_hz * K.tab.lmw[q];
+        K.lift[5][q] = K.two_hz * K.tab.lpw[q];
+        K.lift[6][q] = K.two_hz * K.two_hz * K.tab.dlmw[q];
+        K.lift[7][q] = K.two_hz * K.two_hz * K.tab.dlpw[q];
+        for (int r = 0; r < 8; ++r) K.liftf[r][q] = (float)K.lift[r][q];
+    }
     for (int a = 0; a < 5; ++a) {
         K.tlp[a] = (float)K.tab.lp[a];
         K.tlm[a] = (float)K.tab.lm[a];

@@ -442,6 +442,24 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     const size_t n1 = (size_t)NX * NZ;
     const int ntx = (NX + TX - 1) / TX;
     const int I0 = (int)(blockIdx.x % ntx) * TX, J0 = (int)(blockIdx.x / ntx) * TZ;
+    const int tx = threadIdx.x % TX, tz = threadIdx.x / TX;
+    const int I = I0 + tx, J = J0 + tz;
+    const bool live = I < NX && J < NZ;
+    const size_t c = live ? (size_t)J * NX + I : 0;
+    // the epilogue's operands, loaded before the face work so that their latency overlaps it
+    S xv[4], bv[4], up0 = 0, dtc = 0;
+    double fuv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (live) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const size_t gi = (size_t)v * n1 + c;
+            xv[v] = MODE == FV_RES ? (S)0 : (S)ld.dir(v, c, I, J);
+            bv[v] = MODE == FV_RES ? (S)0 : b[gi];
+            if (IN == 1) fuv[v] = fu[gi];
+        }
+        up0 = (S)oval(ld(0, c, I, J));
+        if (MODE == FV_SMOOTH) dtc = dtau[c];
+    }
     for (int idx = threadIdx.x; idx < (TZ + 2) * (TX + 2); idx += blockDim.x) {
         const int li = idx % (TX + 2), lj = idx / (TX + 2);
         int I = I0 + li - 1;
@@ -455,7 +473,6 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     }
     __syncthreads();
     const bool sub = (IN != 2);
-    const int tx = threadIdx.x % TX, tz = threadIdx.x / TX;
     const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
     // x face west of local cell (i, j): global face index I0 + i in [0, NX]
     auto xface = [&](int i, int j) {
@@ -508,9 +525,6 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     if (tz == 0) zface(tx, TZ);              // north edge of the tile
     else if (tz == 1 && tx < TZ) xface(TX, tx);   // east edge of the tile
     __syncthreads();
-    const int I = I0 + tx, J = J0 + tz;
-    const bool live = I < NX && J < NZ;
-    const size_t c = live ? (size_t)J * NX + I : 0;
     const S iHx = pick<S>(K.iHx, K.iHxf), iHz = pick<S>(K.iHz, K.iHzf);
     const float adtf = IN == 2 ? (float)adt : 0.0f;
     const double eps = ld.step();
@@ -518,19 +532,19 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             S f = (sGx[v][tz][tx] - sGx[v][tz][tx + 1]) * iHx + (sGz[v][tz][tx] - sGz[v][tz + 1][tx]) * iHz;
-            if (v == 2) f -= pick<S>(K.g, K.gf) * (S)oval(ld(0, c, I, J));   // -g rho' (tangent: -g x_rho)
+            if (v == 2) f -= pick<S>(K.g, K.gf) * up0;   // -g rho' (tangent: -g x_rho)
             const size_t gi = (size_t)v * n1 + c;
             if (MODE == FV_RES) {
                 out[gi] = f;
                 continue;
             }
-            const S x = (S)ld.dir(v, c, I, J);
+            const S x = xv[v];
             S gx;
-            if (IN == 1) gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)f - fu[gi]) / eps);
+            if (IN == 1) gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)f - fuv[v]) / eps);
             else gx = x - (S)adtf * f;
-            if (MODE == FV_SMOOTH) out[gi] = store_round<S>(x + dtau[c] * (b[gi] - gx), bf16);
-            else if (MODE == FV_DEFECT) out[gi] = gx - b[gi];
-            else sD[v][tz][tx] = gx - b[gi];
+            if (MODE == FV_SMOOTH) out[gi] = store_round<S>(x + dtc * (bv[v] - gx), bf16);
+            else if (MODE == FV_DEFECT) out[gi] = gx - bv[v];
+            else sD[v][tz][tx] = gx - bv[v];
         }
     }
     if (MODE != FV_DEFRES) return;
