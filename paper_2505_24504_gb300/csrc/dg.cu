@@ -318,6 +318,26 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     const size_t N1 = (size_t)K.n_el * NP;
     const size_t nrow = (size_t)nz * NP1;
     const int J = ez * NP1 + b;
+    // FP32 tangent modes: face terms and the epilogue's operands are loaded now so
+    // that their latency overlaps the flux work below (the FP64 modes are bound by
+    // FP64 arithmetic and keep their registers for it)
+    constexpr bool PF = (IN == 2);
+    const size_t fsx = (size_t)nz * (nx + 1) * NP1, fsz = (size_t)(nz + 1) * nx * NP1;
+    const size_t iL = ((size_t)ez * (nx + 1) + ex) * NP1 + b, iR = iL + NP1;
+    const size_t iB = ((size_t)ez * nx + ex) * NP1 + a, iT = iB + (size_t)nx * NP1;
+    O pxl[4], pxr[4], pzb[4], pzt[4];
+    float ef[4], edt = 0.0f;   // operands of the FP32 smoothing mode
+    if (PF && active) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            pxl[v] = phix[v * fsx + iL];
+            pxr[v] = phix[v * fsx + iR];
+            pzb[v] = phiz[v * fsz + iB];
+            pzt[v] = phiz[v * fsz + iT];
+            if (MODE == DG_TLSMOOTH) ef[v] = A.rf[(size_t)v * N1 + (size_t)e * NP + node];
+        }
+        if (MODE == DG_TLSMOOTH) edt = A.dtauf[e];
+    }
     __syncthreads();
     T Up[4], U[4];
     if (active) {
@@ -371,9 +391,6 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     }
     __syncthreads();
     if (!active) return;
-    const size_t fsx = (size_t)nz * (nx + 1) * NP1, fsz = (size_t)(nz + 1) * nx * NP1;
-    const size_t iL = ((size_t)ez * (nx + 1) + ex) * NP1 + b, iR = iL + NP1;
-    const size_t iB = ((size_t)ez * nx + ex) * NP1 + a, iT = iB + (size_t)nx * NP1;
     const O lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
     const O lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
     const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
@@ -388,10 +405,10 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
             f = fma(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
         }
         if (v == 2) f = fma(-pick<O>(K.g, K.gf), (O)outv(Up[0]), f);
-        f = fma(lmxa, phix[v * fsx + iL], f);
-        f = fma(-lpxa, phix[v * fsx + iR], f);
-        f = fma(lmzb, phiz[v * fsz + iB], f);
-        f = fma(-lpzb, phiz[v * fsz + iT], f);
+        f = fma(lmxa, PF ? pxl[v] : phix[v * fsx + iL], f);
+        f = fma(-lpxa, PF ? pxr[v] : phix[v * fsx + iR], f);
+        f = fma(lmzb, PF ? pzb[v] : phiz[v * fsz + iB], f);
+        f = fma(-lpzb, PF ? pzt[v] : phiz[v * fsz + iT], f);
         if (VISC && v > 0) {
             const int c = v - 1;
             f = fma(dlmxa, symx[(size_t)(3 + c) * fsx + iL], f);
@@ -413,12 +430,12 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
             const double Jz = (eps == 0.0) ? z : fma(-ceps, (double)f - A.fU[gi], z);
             ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
         } else if (MODE == DG_TLJV) {
-            const float z = A.yf[gi];
+            const float z = (float)outv(Up[v]);   // the loader's tangent input is y
             ((float *)A.out0)[gi] = z - adtf * (float)f;
         } else {  // DG_TLSMOOTH
-            const float z = A.yf[gi];
+            const float z = (float)outv(Up[v]);
             const float Jz = z - adtf * (float)f;
-            ((float *)A.out0)[gi] = z + A.dtauf[e] * (A.rf[gi] - Jz);
+            ((float *)A.out0)[gi] = z + edt * (ef[v] - Jz);
         }
     }
 }
