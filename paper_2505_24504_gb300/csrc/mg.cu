@@ -79,6 +79,21 @@ template <> struct FLoad<TL32, 2> {
         return TL32{u[i], x[i]};
     }
 };
+// IN 3: FP32 tangent at the coarse-corrected iterate x - P v_c (Sec. 3.4), formed
+// on the fly (x = 0 when `zero`), so the correction needs no launch of its own
+template <> struct FLoad<TL32, 3> {
+    const float *u, *x, *vc;
+    size_t n1;
+    int NXc, fac, zero;
+    size_t nc;
+    JF_D void prepare() {}
+    JF_D double step() const { return 0.0; }
+    JF_D float dir(int v, size_t c, int I, int J) const {
+        const float pv = vc[(size_t)v * nc + (size_t)(J / fac) * NXc + I / fac];
+        return zero ? -pv : x[v * n1 + c] - pv;
+    }
+    JF_D TL32 operator()(int v, size_t c, int I, int J) const { return TL32{u[v * n1 + c], dir(v, c, I, J)}; }
+};
 enum { FV_RES = 0, FV_SMOOTH = 1, FV_DEFECT = 2 };
 
 // BF16 storage numerics on the coarsest level (precond_prec = 16): values are
@@ -128,7 +143,7 @@ JF_D void visc2(const T UL[4], const T UR[4], T coef, T V[4]) {
 template <class T, int IN, bool VISC>
 JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size_t c, int I, int Jz, T f[4]) {
     const int NX = K.NX, NZ = K.NZ;
-    const bool sub = (IN != 2);
+    const bool sub = (IN < 2);
     T U[4], Un[4][4];   // own state and the W, E, S, N neighbours
     int nb[4] = {-1, -1, -1, -1};
     int nI[4] = {I - 1, I + 1, I, I}, nJ[4] = {Jz, Jz, Jz - 1, Jz + 1};
@@ -204,7 +219,7 @@ JF_D T reduce_scatter4(const T f[4], int q) {
 template <class T, int IN, bool VISC>
 JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size_t c, int I, int Jz, int q) {
     const int NX = K.NX, NZ = K.NZ;
-    const bool sub = (IN != 2);
+    const bool sub = (IN < 2);
     const bool zf = q >= 2, right = (q & 1) != 0;
     long nb = -1;
     int nI = I, nJ = Jz;
@@ -296,11 +311,11 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     jf_pdl_enter();
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
-    if (IN != 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
+    if (IN < 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
     FLoad<T, IN> ld = ld0;
     ld.prepare();
     __syncthreads();
-    const float adtf = IN == 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? (float)adt : 0.0f;
     const size_t n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = L == 4 ? (int)(t & 3) : 0;
@@ -344,7 +359,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     jf_pdl_enter();
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
-    if (IN != 2) load_pt(&spt, K.pt);
+    if (IN < 2) load_pt(&spt, K.pt);
     FLoad<T, IN> ld = ld0;
     ld.prepare();
     __syncthreads();
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double eps = ld.step();
-    const float adtf = IN == 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? (float)adt : 0.0f;
     if (L == 1) {
         if (t >= nc) return;
         const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
@@ -435,7 +450,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     __shared__ S sGx[4][TZ][TX + 1];   // net flux H - V through the west face of local cell (i, j)
     __shared__ S sGz[4][TZ + 1][TX];   // ... through the south face
     __shared__ S sD[MODE == FV_DEFRES ? 4 : 1][MODE == FV_DEFRES ? TZ : 1][MODE == FV_DEFRES ? TX : 1];
-    if (IN != 2) load_pt(&spt, K.pt);
+    if (IN < 2) load_pt(&spt, K.pt);
     FLoad<T, IN> ld = ld0;
     ld.prepare();
     const int NX = K.NX, NZ = K.NZ;
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         }
     }
     __syncthreads();
-    const bool sub = (IN != 2);
+    const bool sub = (IN < 2);
     const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
     // x face west of local cell (i, j): global face index I0 + i in [0, NX]
     auto xface = [&](int i, int j) {
@@ -526,7 +541,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     else if (tz == 1 && tx < TZ) xface(TX, tx);   // east edge of the tile
     __syncthreads();
     const S iHx = pick<S>(K.iHx, K.iHxf), iHz = pick<S>(K.iHz, K.iHzf);
-    const float adtf = IN == 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? (float)adt : 0.0f;
     const double eps = ld.step();
     if (live) {
 #pragma unroll
@@ -1072,6 +1087,31 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     return JFNK_OK;
 }
 
+// One FP32 smoothing step at the corrected iterate x - P v_c of level l (v_c = the
+// coarse level's iterate), written to out: the prolongation and the first
+// post-smoothing step in one launch.
+int fv_smooth32_corrected(jfnk_ctx *c, int l, const float *x, bool zero, const float *b, float *out,
+                          cudaStream_t s) {
+    FVLev &L = c->lev[l];
+    FVLev &C = c->lev[l + 1];
+    FVK K = make_fvk(c, l);
+    const size_t n1 = (size_t)L.NX * L.NZ;
+    const bool visc = c->phys.mu != 0.0;
+    c->fv_calls++;
+    const int tb = c->opts.tile_fv;
+    const bool l4 = fv_four_lanes(c, n1);
+    const unsigned g = nblk((l4 ? 4 : 1) * n1, tb);
+    FLoad<TL32, 3> ld{(const float *)L.u, x, (const float *)C.x, n1, C.NX, L.fac, zero ? 1 : 0,
+                      (size_t)C.NX * C.NZ};
+    const float *dt = (const float *)L.dtau;
+    const double adt = c->mg_adt;
+    const int bf = (c->prec == 16 && l == c->nlev - 1) ? 1 : 0;
+    if (visc) { JF_FV(TL32, 3, FV_SMOOTH, true, K, ld, x, b, dt, nullptr, adt, out, bf); }
+    else { JF_FV(TL32, 3, FV_SMOOTH, false, K, ld, x, b, dt, nullptr, adt, out, bf); }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
+}
+
 // defect g'x - b on level l restricted to level l+1 (b_{l+1}, and x_{l+1} = dtau b
 // when xc is given)
 int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *bc, void *xc, const void *dtc,
@@ -1207,8 +1247,18 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             vz = false;
             fd = false;
         }
-        jf_launch(k_prolong<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac, zero ? 1 : 0);
-        jf_launched();
+        if (sizeof(S) == 4 && post >= 1) {
+            // FP32: the correction x - P v_c is formed inside the first post-smoothing step
+            JF_RET(fv_smooth32_corrected(c, l, (const float *)L.x, zero, (const float *)L.b, (float *)L.x2, s));
+            void *t = L.x;
+            L.x = L.x2;
+            L.x2 = t;
+            post -= 1;
+        } else {
+            jf_launch(k_prolong<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac,
+                      zero ? 1 : 0);
+            jf_launched();
+        }
         zero = false;
     }
     JF_RET(smooth(post));
