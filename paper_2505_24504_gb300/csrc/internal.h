@@ -234,7 +234,9 @@ int blas_scale(double a, const double *x, double *y, size_t n, cudaStream_t s);
 
 // preconditioner (mg.cu)
 int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s);
-int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s);
+// r32 (optional): r already in FP32 (FP32 preconditioner, used when the kernels
+// are launched or captured directly)
+int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float *r32 = nullptr);
 int mg_graph_prepare(jfnk_ctx *c);
 void jf_invalidate_graphs(jfnk_ctx *c);
 int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s);

@@ -1376,8 +1376,11 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     JF_RET(mg_cycle_t<S>(c, 0, true, fuse0, s));
     JF_RET(to_dg<S, S>(c, (const S *)c->lev[0].x, z, zero ? 0 : 1, s));
     zero = false;
-    for (int i = 0; i < c->dg_post; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
-    JF_CK(cudaMemcpyAsync(zout, z, c->N * sizeof(S), cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < c->dg_post; ++i) {
+        if (i == c->dg_post - 1) z2 = zout;   // the last step writes the output itself
+        JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+    }
+    if (c->dg_post == 0) JF_CK(cudaMemcpyAsync(zout, z, c->N * sizeof(S), cudaMemcpyDeviceToDevice, s));
     for (int l = 0; l < c->nlev; ++l) {
         c->lev[l].x = sx[l];
         c->lev[l].x2 = sx2[l];
@@ -1500,8 +1503,13 @@ void jf_invalidate_graphs(jfnk_ctx *c) {
         }
 }
 
-int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s) {
+int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float *r32) {
     const size_t sS = c->prec == 64 ? 8 : 4;
+    if (c->prec != 64 && r32 && (c->capturing || !c->opts.use_graphs)) {
+        // inside an Arnoldi step: the FP32 copy of r exists already, and the
+        // launches go straight into the caller's stream (or capture)
+        return apply_t<float>(c, r32, (float *)z, s);
+    }
     if (c->prec == 64) JF_CK(cudaMemcpyAsync(c->pin, r, 8 * c->N, cudaMemcpyDeviceToDevice, s));
     else JF_RET(blas_copy_d2f(r, (float *)c->pin, c->N, s));   // FP32 preconditioner: r enters in FP32
     if (c->opts.use_graphs && !c->capturing) {

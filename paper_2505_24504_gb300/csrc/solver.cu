@@ -89,7 +89,8 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
     int rc;
     if (ph) ph->mark(0, s);
     if (c->mg_on) {
-        JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s));
+        JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s,
+                        c->prec == 64 ? nullptr : c->V32 + (size_t)j * N));
     } else {
         JF_CK(cudaMemcpyAsync((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
     }
@@ -116,6 +117,7 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
     JF_RET(blas_mupdate_norm(c, V, j + 1, N, c->scal + S_H2, w, N, -1.0, c->scal + S_FLAG, nullptr,
                              c->scal + S_NORM, nullptr, s));
     JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
+    JF_RET(blas_copy_d2f(w, c->V32 + (size_t)(j + 1) * N, N, s));   // float copy of the basis
     if (ph) ph->mark(3, s);
     JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
     return JFNK_OK;
