@@ -626,34 +626,49 @@ __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) 
 
 // DG pseudo-time step per element: lambda_E = (k+1)^2 max_nodes(|v| + c)(1/hx + 1/hz)
 // + 2 mu (k+1)^4 (1/hx^2 + 1/hz^2).
-__global__ void k_dg_dtau(const double *U, const double *ubv, int nx, int nz, int np1, PhysC pc,
-                          const PowTab *pt, double ihx, double ihz, double mu, double adt, double sigma,
-                          double *dtau, float *dtauf) {
+template <class R>
+__global__ void k_dg_dtau(const R *U, const R *ubv, int nx, int nz, int np1, PhysC pc, const PowTab *pt,
+                          double ihx, double ihz, double mu, double adt, double sigma, double *dtau,
+                          float *dtauf) {
     jf_pdl_enter();
     __shared__ PowTab spt;
-    load_pt(&spt, pt);
+    if (sizeof(R) == 8) load_pt(&spt, pt);
     __syncthreads();
+    // one warp per element, one lane per node, max over the lanes
     const int n_el = nx * nz;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
+    const int lane = threadIdx.x & 31;
+    const int e = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (e >= n_el) return;   // uniform over the warp
     const int NP = np1 * np1;
     const size_t N1 = (size_t)n_el * NP;
     const int ez = e / nx;
     const size_t nrow = (size_t)nz * np1;
-    double vmax = 0.0;
-    for (int node = 0; node < NP; ++node) {
-        const int J = ez * np1 + node / np1;
-        double W[4];
-        for (int v = 0; v < 4; ++v) W[v] = U[v * N1 + (size_t)e * NP + node] + ubv[v * nrow + J];
-        const double ir = 1.0 / W[0];
-        const double p = pc.p0 * pow_gamma_tab(pc.R_over_p0 * W[3], &spt);
-        const double s = sqrt((W[1] * ir) * (W[1] * ir) + (W[2] * ir) * (W[2] * ir)) + sqrt(pc.gamma * p * ir);
-        vmax = fmax(vmax, s);
+    R sp = 0;
+    if (lane < NP) {
+        const int J = ez * np1 + lane / np1;
+        R W[4];
+        for (int v = 0; v < 4; ++v) W[v] = U[v * N1 + (size_t)e * NP + lane] + ubv[v * nrow + J];
+        if (sizeof(R) == 8) {
+            const double ir = 1.0 / (double)W[0];
+            const double p = pc.p0 * pow_gamma_tab(pc.R_over_p0 * (double)W[3], &spt);
+            sp = (R)(sqrt(((double)W[1] * ir) * ((double)W[1] * ir) + ((double)W[2] * ir) * ((double)W[2] * ir)) +
+                     sqrt(pc.gamma * p * ir));
+        } else {
+            const float ir = 1.0f / (float)W[0];
+            const float p = pc.p0f * __powf(pc.R_over_p0f * (float)W[3], pc.gammaf);
+            sp = (R)(sqrtf(((float)W[1] * ir) * ((float)W[1] * ir) + ((float)W[2] * ir) * ((float)W[2] * ir)) +
+                     sqrtf(pc.gammaf * p * ir));
+        }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+    if (lane != 0) return;
+    const double vmax = (double)sp;
     const double n2 = (double)np1 * np1;
     const double lam = n2 * vmax * (ihx + ihz) + 2.0 * mu * n2 * n2 * (ihx * ihx + ihz * ihz);
-    dtau[e] = sigma / (1.0 + adt * lam);
-    if (dtauf) dtauf[e] = (float)dtau[e];
+    const double d = sigma / (1.0 + adt * lam);
+    if (dtau) dtau[e] = d;
+    if (dtauf) dtauf[e] = (float)d;
 }
 
 // ---- transfer -------------------------------------------------------------
@@ -1408,15 +1423,24 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
     const double *U = c->Ulin;
     c->mg_adt = adt;
     c->mg_U = U;
-    jf_launch(k_dg_dtau, nblk(c->n_el), 128, 0, s, U, c->ubv, c->grid.nx, c->grid.nz, c->np1, c->pc, c->powtab,
-                                             1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt, c->opts.sigma_dg,
-                                             c->dtau_dg, c->dtau_dgf); jf_launched();
-    JF_CK(cudaGetLastError());
+    // DG pseudo-time steps: FP64 for the FP64 preconditioner, FP32 from the FP32
+    // copy of the state otherwise (a step-size heuristic; one warp per element)
+    const unsigned gd = (unsigned)(((size_t)c->n_el * 32 + 127) / 128);
     if (c->prec == 64) {
+        jf_launch(k_dg_dtau<double>, gd, 128, 0, s, U, (const double *)c->ubv, c->grid.nx, c->grid.nz, c->np1,
+                  c->pc, c->powtab, 1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt, c->opts.sigma_dg, c->dtau_dg,
+                  c->dtau_dgf);
+        jf_launched();
+        JF_CK(cudaGetLastError());
         JF_RET(to_fv<double, double>(c, U, (double *)c->lev[0].u, s));
     } else {
-        JF_RET(to_fv<double, float>(c, U, (float *)c->lev[0].u, s));
         JF_RET(blas_copy_d2f(U, c->Usf, c->N, s));
+        jf_launch(k_dg_dtau<float>, gd, 128, 0, s, (const float *)c->Usf, (const float *)c->ubvf, c->grid.nx,
+                  c->grid.nz, c->np1, c->pc, c->powtab, 1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt,
+                  c->opts.sigma_dg, c->dtau_dg, c->dtau_dgf);
+        jf_launched();
+        JF_CK(cudaGetLastError());
+        JF_RET(to_fv<double, float>(c, U, (float *)c->lev[0].u, s));
     }
     for (int l = 0; l < c->nlev; ++l) {
         FVLev &L = c->lev[l];
