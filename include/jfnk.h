@@ -111,9 +111,10 @@ typedef struct {
     int use_graphs;
     int tile_faces;      /* threads per block of the DG face kernel: 64, 128, 256 (0: 128) */
     int tile_volume;     /* elements per DG volume block: 1 = ~64 threads, 2 = ~128 (0: 2) */
-    int tile_fv;         /* threads per block of the FV cell kernels: 64, 128, 256 (0: 128) */
+    int tile_fv;         /* threads per block of the FV cell kernels: 64, 128, 256 (0: 128); the
+                            face-once kernel of large levels takes 32 x 8 cells at 256, 32 x 4 else */
     int fv_split_cells;  /* FV levels with fewer cells than this run four lanes per cell (one
-                            per face), larger levels one thread per cell (0: 65536) */
+                            per face), larger levels the face-once tile kernel (0: 65536) */
     int profile;         /* 1: time the phases of implicit_step with CUDA events (jfnk_stats) */
 } jfnk_opts;
 

@@ -1036,9 +1036,12 @@ void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const 
                const double *fu, double adt, typename SOf<T>::type *out, int bf = 0) {
     if (l4) {
         jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf);
-    } else {
+    } else if (tb >= 256) {   // tile rows follow the block size: 32 x 8 or 32 x 4 cells
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 7) / 8));
         jf_launch(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
+    } else {
+        const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 3) / 4));
+        jf_launch(k_fv_tile<T, IN, MODE, V, 4>, gt, FV_TX * 4, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
     }
     jf_launched();
 }
@@ -1150,10 +1153,17 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
         else JF_DR(T, IN, V, 4, false, __VA_ARGS__);         \
     } while (0)
     // large levels with 2 x 2 agglomeration: the face-once tile kernel
-    const unsigned gt = (unsigned)(((L.NX + FV_TX - 1) / FV_TX) * ((L.NZ + 7) / 8));
-#define JF_DRT(T, IN, V, ld, bb, fuu, outc, xcc, dtc_, bff)                                                 \
-    jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, outc, xcc, \
-                                                                 dtc_, bff)
+    const int tz = tb >= 256 ? 8 : 4;   // tile rows follow the block size
+    const unsigned gt = (unsigned)(((L.NX + FV_TX - 1) / FV_TX) * ((L.NZ + tz - 1) / tz));
+#define JF_DRT(T, IN, V, ld, bb, fuu, outc, xcc, dtc_, bff)                                                     \
+    do {                                                                                                        \
+        if (tz == 8)                                                                                            \
+            jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
+                      outc, xcc, dtc_, bff);                                                                    \
+        else                                                                                                    \
+            jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 4>, gt, FV_TX * 4, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
+                      outc, xcc, dtc_, bff);                                                                    \
+    } while (0)
     if (!l4 && f2) {
         if (c->prec == 64) {
             double *epsp = c->scal + S_EPSFV + l;
