@@ -59,6 +59,7 @@ def parse():
                    help="fp32: time only the FP32-preconditioner steps (for profiler runs)")
     p.add_argument("--ensemble", type=int, default=64, help="members of the batched ensemble (0: skip)")
     p.add_argument("--ensemble-steps", type=int, default=2)
+    p.add_argument("--ensemble-threads", type=int, default=16, help="host threads / streams of the batched ensemble")
     p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
     p.add_argument("--viscous-steps", type=int, default=3, help="timed steps of the viscous workload (0: skip)")
     p.add_argument("--igw-steps", type=int, default=5, help="timed steps of the inertia gravity workload (0: skip)")
@@ -180,7 +181,7 @@ def make_context_for(w, prec):
     return make_context(w, prec)
 
 
-def run_ensemble(n, steps, warmup):
+def run_ensemble(n, steps, warmup, threads=16):
     """64-member uneven ensemble (Q1..Q4, 40x20 .. 320x160), one batched SDIRK2 step
     per timed iteration, FP32 preconditioner; returns a dict for the JSON line."""
     import torch
@@ -196,7 +197,7 @@ def run_ensemble(n, steps, warmup):
         c0.close()
         ctxs.append(c)
         Us.append(U)
-    batch = P.Batch(ctxs, max_threads=16)
+    batch = P.Batch(ctxs, max_threads=threads)
     dts = [m.dt for m in members]
     sch = [m.scheme for m in members]
     for _ in range(warmup):
@@ -220,7 +221,7 @@ def run_ensemble(n, steps, warmup):
             "member_steps_per_s": n * steps / t, "dof_per_s": dof * steps / t,
             "ms_per_ensemble_step": 1e3 * t / steps, "failed_members": sum(1 for x in status if x != 0),
             "gmres_its_per_ensemble_step": sum(its) / len(its), "precond": "fp32",
-            "timing": "wall clock of jfnk_batch_step (host-driven members on 16 threads / streams)"}
+            "timing": f"wall clock of jfnk_batch_step (host-driven members on {threads} threads / streams)"}
 
 
 def run_serving(seconds, rate=200.0):
@@ -566,7 +567,7 @@ def main():
     if args.mg_sweep:
         line["mg_sweep"] = run_mg_sweep()
     if args.ensemble > 0:
-        line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1)
+        line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1, args.ensemble_threads)
     if args.serve_seconds > 0:
         line["serving"] = run_serving(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
