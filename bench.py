@@ -212,16 +212,50 @@ def run_ensemble(n, steps, warmup, threads=16):
         t += time.perf_counter() - t0
         its.append(sum(s.gmres_its for s in stats))
     dof = sum(m.n_unknowns for m in members)
+    grouped = time_grouped_residual(batch, ctxs, Us, dof)
     batch.close()
     for c in ctxs:
         c.close()
     del Us
     torch.cuda.empty_cache()
-    return {"members": n, "unknowns_total": dof, "ensemble_steps_per_s": steps / t,
+    return {"members": n, "unknowns_total": dof, "grouped_residual": grouped,
+            "ensemble_steps_per_s": steps / t,
             "member_steps_per_s": n * steps / t, "dof_per_s": dof * steps / t,
             "ms_per_ensemble_step": 1e3 * t / steps, "failed_members": sum(1 for x in status if x != 0),
             "gmres_its_per_ensemble_step": sum(its) / len(its), "precond": "fp32",
             "timing": f"wall clock of jfnk_batch_step (host-driven members on {threads} threads / streams)"}
+
+
+def time_grouped_residual(batch, ctxs, Us, dof, reps=10):
+    """FP64 residual of every member: one face + one volume launch per (order,
+    viscous) group (jfnk_batch_dg_residual) against one launch pair per member,
+    both on one stream, CUDA events."""
+    import torch
+    outs = [torch.empty(c.N, dtype=torch.float64, device="cuda") for c in ctxs]
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def per_member():
+        for c, u, f in zip(ctxs, Us, outs):
+            c.dg_residual(u, f)
+
+    g = timed(lambda: batch.jfnk_batch_dg_residual(Us, outs))
+    m = timed(per_member)
+    del outs
+    return {"ms_grouped": g, "ms_per_member_launches": m, "dof_per_s_grouped": dof / (g / 1e3),
+            "dof_per_s_per_member": dof / (m / 1e3), "launches_grouped": 2 * len({(c.k, c.phys.mu != 0.0) for c in ctxs}),
+            "launches_per_member": 2 * len(ctxs)}
 
 
 def run_serving(seconds, rate=200.0):

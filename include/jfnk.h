@@ -243,6 +243,17 @@ void jfnk_batch_destroy(jfnk_batch *batch);
 int jfnk_batch_step(jfnk_batch *batch, double *const *U_dev, const double *dt, const int *scheme,
                     int *status, jfnk_stats *stats);
 
+/* f_m = M^-1 L_h(U'_m) (the residual of dg_residual, Sec. 2.1 and Sec. 4) for every
+ * member m at once, on `stream`: members are grouped by (order k, viscous or
+ * not), and each group takes ONE face launch and ONE volume launch whose blocks
+ * are dealt out to the members in turn (a member's blocks see that member's
+ * grid, order, physics and buffers).  U_dev[m], f_dev[m]: device arrays of
+ * member m's jfnk_num_unknowns doubles in its layout, U_dev[m] != f_dev[m]
+ * (host arrays of n device pointers).  Results are bit-identical to
+ * dg_residual on each member.  Uses the members' face scratch, so no member may
+ * run other work concurrently.  JFNK_EINVAL for null or aliased arguments. */
+int jfnk_batch_dg_residual(jfnk_batch *batch, const double *const *U_dev, double *const *f_dev, void *stream);
+
 /* ---- diagnostics (pieces of mg_precondition, for parity tests) -------- */
 
 /* Number of FV levels and the size of level l (0 = finest subgrid). */

@@ -22,6 +22,7 @@ struct jfnk_batch {
     std::vector<cudaStream_t> streams;
     std::vector<int> order;      // members, largest first
     int threads;
+    void *desc;                  // device room for the grouped-operator descriptors
 };
 
 extern "C" {
@@ -49,6 +50,16 @@ int jfnk_batch_create(jfnk_ctx *const *ctxs, int n, int max_threads, jfnk_batch 
     std::stable_sort(b->order.begin(), b->order.end(),
                      [&](int x, int y) { return b->ctx[x]->N > b->ctx[y]->N; });
     b->threads = max_threads > 0 ? std::min(max_threads, n) : std::min(n, 16);
+    b->desc = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_jf_device_mu);   // no allocation during another thread's capture
+        if (cudaMalloc(&b->desc, dg_member_bytes() * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+            delete b;
+            return JFNK_ENOMEM;
+        }
+    }
     *out = b;
     return JFNK_OK;
 }
@@ -57,6 +68,10 @@ void jfnk_batch_destroy(jfnk_batch *b) {
     if (!b) return;
     for (cudaStream_t s : b->streams)
         if (s) cudaStreamDestroy(s);
+    if (b->desc) {
+        std::lock_guard<std::mutex> lock(g_jf_device_mu);
+        cudaFree(b->desc);
+    }
     delete b;
 }
 
@@ -87,6 +102,11 @@ int jfnk_batch_step(jfnk_batch *b, double *const *U, const double *dt, const int
         if (rc[i] != JFNK_OK && first == JFNK_OK) first = rc[i];
     }
     return first;
+}
+
+int jfnk_batch_dg_residual(jfnk_batch *b, const double *const *U, double *const *f, void *stream) {
+    if (!b) return JFNK_EINVAL;
+    return dg_residual_grouped(b->ctx.data(), b->n, U, f, b->desc, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -15,6 +15,8 @@
 //            pseudo-time smoothing step).
 // The same kernels run on D64 (FP64 residual and finite-difference products)
 // and on TL32 (FP32 tangent-linear products for the FP32 preconditioner).
+#include <vector>
+
 #include "internal.h"
 
 namespace {
@@ -77,11 +79,13 @@ template <class T>
 JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
 
 // ---------------------------------------------------------------------------
+// Body of the face kernel for block `blk` of one operator evaluation; K is the
+// launch parameter (single operator) or a member's descriptor in global memory
+// (grouped launch over ensemble members).
 template <class T, int IN, int NP1, bool VISC>
-__global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
-                                               typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
-                                               typename OutT<T>::type *symz) {
-    jf_pdl_enter();
+__device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld0, typename OutT<T>::type *phix,
+                                           typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
+                                           typename OutT<T>::type *symz, unsigned blk) {
     typedef typename OutT<T>::type O;
     __shared__ PowTab spt;
     if (IN != 2) load_powtab(&spt, K.pt);   // the FP32 tangent power needs no table
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
     const size_t N1 = (size_t)K.n_el * NP;
     const long long nvert = (long long)nz * (nx + 1) * NP1;
     const long long nhorz = (long long)(nz + 1) * nx * NP1;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blk * blockDim.x + threadIdx.x;
     if (t >= nvert + nhorz) return;
     const T zero = mk(0.0, T{});
     const T half = mk(0.5, T{});
@@ -268,6 +272,14 @@ __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, type
     }
 }
 
+template <class T, int IN, int NP1, bool VISC>
+__global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
+                                               typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
+                                               typename OutT<T>::type *symz) {
+    jf_pdl_enter();
+    faces_body<T, IN, NP1, VISC>(K, ld0, phix, symx, phiz, symz, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // elements per volume block: TV = 2 -> ~128 threads, TV = 1 -> ~64 threads
 template <int NP1, int TV> struct EPBOf {
@@ -277,12 +289,11 @@ template <int NP1, int TV> struct EPBOf {
 };
 
 template <class T, int IN, int MODE, int NP1, bool VISC, int TV>
-__global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
-                                                const typename OutT<T>::type *phix,
-                                                const typename OutT<T>::type *symx,
-                                                const typename OutT<T>::type *phiz,
-                                                const typename OutT<T>::type *symz) {
-    jf_pdl_enter();
+__device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &ld0, const DGArgs &A,
+                                            const typename OutT<T>::type *phix,
+                                            const typename OutT<T>::type *symx,
+                                            const typename OutT<T>::type *phiz,
+                                            const typename OutT<T>::type *symz, unsigned blk) {
     typedef typename OutT<T>::type O;
     constexpr int NP = NP1 * NP1;
     constexpr int EPB = EPBOf<NP1, TV>::value;
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     const int le = threadIdx.x / NP;
     const int node = threadIdx.x % NP;
     const int a = node % NP1, b = node / NP1;
-    const int e = blockIdx.x * EPB + le;
+    const int e = (int)blk * EPB + le;
     const bool active = (le < EPB) && (e < K.n_el);
     const int nx = K.nx, nz = K.nz;
     const int ez = active ? e / nx : 0, ex = active ? e % nx : 0;
@@ -438,6 +449,16 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
             ((float *)A.out0)[gi] = z + edt * (ef[v] - Jz);
         }
     }
+}
+
+template <class T, int IN, int MODE, int NP1, bool VISC, int TV>
+__global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
+                                                   const typename OutT<T>::type *phix,
+                                                   const typename OutT<T>::type *symx,
+                                                   const typename OutT<T>::type *phiz,
+                                                   const typename OutT<T>::type *symz) {
+    jf_pdl_enter();
+    volume_body<T, IN, MODE, NP1, VISC, TV>(K, ld0, A, phix, symx, phiz, symz, blockIdx.x);
 }
 
 // background fluxes at node rows and horizontal faces, with the residual's own
@@ -601,6 +622,49 @@ int dispatch_mode(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
     return JFNK_EINVAL;
 }
 
+// ---- one launch per operator across ensemble members ---------------------
+// A member's share of a grouped residual launch: its operator constants, state,
+// output and face buffers, and the first face / volume block of the launch that
+// belongs to it.
+struct DGMember {
+    DGK K;
+    Loader<D64, 0> ld;
+    DGArgs A;
+    double *phix, *symx, *phiz, *symz;
+    unsigned fb0, vb0;
+};
+constexpr int GRP_FACE_THREADS = 128;
+
+template <int NP1, bool VISC>
+__global__ void __launch_bounds__(256, 4) k_faces_grp(const DGMember *mem, int nm) {
+    jf_pdl_enter();
+    int m = 0;
+    while (m + 1 < nm && blockIdx.x >= mem[m + 1].fb0) ++m;   // members in block order
+    const DGMember &M = mem[m];
+    faces_body<D64, 0, NP1, VISC>(M.K, M.ld, M.phix, M.symx, M.phiz, M.symz, blockIdx.x - M.fb0);
+}
+
+template <int NP1, bool VISC>
+__global__ void __launch_bounds__(128, 8) k_volume_grp(const DGMember *mem, int nm) {
+    jf_pdl_enter();
+    int m = 0;
+    while (m + 1 < nm && blockIdx.x >= mem[m + 1].vb0) ++m;
+    const DGMember &M = mem[m];
+    volume_body<D64, 0, DG_RES, NP1, VISC, 2>(M.K, M.ld, M.A, M.phix, M.symx, M.phiz, M.symz, blockIdx.x - M.vb0);
+}
+
+template <int NP1, bool VISC>
+void launch_grp(const DGMember *dmem, const std::vector<DGMember> &h, int first, int cnt, cudaStream_t s) {
+    const DGMember &last = h[first + cnt - 1];
+    const long long nfl = (long long)last.K.nz * (last.K.nx + 1) * NP1 + (long long)(last.K.nz + 1) * last.K.nx * NP1;
+    const unsigned fb = last.fb0 + (unsigned)((nfl + GRP_FACE_THREADS - 1) / GRP_FACE_THREADS);
+    constexpr int EPB = EPBOf<NP1, 2>::value;
+    const unsigned vb = last.vb0 + (unsigned)((last.K.n_el + EPB - 1) / EPB);
+    jf_launch(k_faces_grp<NP1, VISC>, fb, GRP_FACE_THREADS, 0, s, dmem + first, cnt);
+    jf_launch(k_volume_grp<NP1, VISC>, vb, EPB * NP1 * NP1, 0, s, dmem + first, cnt);
+    jf_launched(2);
+}
+
 }  // namespace
 
 int dg_setup_background(jfnk_ctx *c) {
@@ -622,4 +686,66 @@ int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
         case 5: return visc ? dispatch_mode<5, true>(c, mode, a, s) : dispatch_mode<5, false>(c, mode, a, s);
     }
     return JFNK_EINVAL;
+}
+
+size_t dg_member_bytes() { return sizeof(DGMember); }
+
+// f_m = M^-1 L_h(U_m) for every member, grouped by (order, viscous): one face
+// and one volume launch per group.  dmem: device room for n descriptors.
+int dg_residual_grouped(jfnk_ctx *const *ctx, int n, const double *const *U, double *const *f, void *dmem,
+                        cudaStream_t s) {
+    if (!ctx || !U || !f || !dmem || n < 1) return JFNK_EINVAL;
+    std::vector<int> order;
+    for (int np1 = 2; np1 <= 5; ++np1)
+        for (int visc = 0; visc < 2; ++visc)
+            for (int i = 0; i < n; ++i) {
+                if (!ctx[i] || !U[i] || !f[i] || U[i] == f[i]) return JFNK_EINVAL;
+                if (ctx[i]->np1 == np1 && (ctx[i]->phys.mu != 0.0) == (visc != 0)) order.push_back(i);
+            }
+    if ((int)order.size() != n) return JFNK_EINVAL;
+    std::vector<DGMember> h(n);
+    std::vector<int> gstart;
+    unsigned fb = 0, vb = 0;
+    for (int q = 0; q < n; ++q) {
+        jfnk_ctx *c = ctx[order[q]];
+        if (q == 0 || c->np1 != ctx[order[q - 1]]->np1 ||
+            (c->phys.mu != 0.0) != (ctx[order[q - 1]]->phys.mu != 0.0)) {
+            gstart.push_back(q);
+            fb = vb = 0;
+        }
+        DGMember &M = h[q];
+        M.K = make_K(c);
+        M.ld = Loader<D64, 0>{U[order[q]]};
+        M.A = DGArgs{};
+        M.A.U = U[order[q]];
+        M.A.out0 = f[order[q]];
+        M.phix = (double *)c->phix;
+        M.symx = (double *)c->symx;
+        M.phiz = (double *)c->phiz;
+        M.symz = (double *)c->symz;
+        M.fb0 = fb;
+        M.vb0 = vb;
+        const int n1 = c->np1;
+        const long long nf = (long long)c->grid.nz * (c->grid.nx + 1) * n1 + (long long)(c->grid.nz + 1) * c->grid.nx * n1;
+        fb += (unsigned)((nf + GRP_FACE_THREADS - 1) / GRP_FACE_THREADS);
+        const int epb = (128 / (n1 * n1)) > 0 ? 128 / (n1 * n1) : 1;
+        vb += (unsigned)((c->n_el + epb - 1) / epb);
+        c->dg_calls++;
+    }
+    JF_CK(cudaMemcpyAsync(dmem, h.data(), sizeof(DGMember) * (size_t)n, cudaMemcpyHostToDevice, s));
+    const DGMember *dm = (const DGMember *)dmem;
+    gstart.push_back(n);
+    for (size_t gi = 0; gi + 1 < gstart.size(); ++gi) {
+        const int a = gstart[gi], cnt = gstart[gi + 1] - a;
+        const bool visc = h[a].K.mu != 0.0;
+        switch (h[a].K.tab.np1) {
+            case 2: visc ? launch_grp<2, true>(dm, h, a, cnt, s) : launch_grp<2, false>(dm, h, a, cnt, s); break;
+            case 3: visc ? launch_grp<3, true>(dm, h, a, cnt, s) : launch_grp<3, false>(dm, h, a, cnt, s); break;
+            case 4: visc ? launch_grp<4, true>(dm, h, a, cnt, s) : launch_grp<4, false>(dm, h, a, cnt, s); break;
+            case 5: visc ? launch_grp<5, true>(dm, h, a, cnt, s) : launch_grp<5, false>(dm, h, a, cnt, s); break;
+            default: return JFNK_EINVAL;
+        }
+    }
+    JF_CK(cudaGetLastError());
+    return JFNK_OK;
 }

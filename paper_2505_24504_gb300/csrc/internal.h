@@ -206,6 +206,9 @@ struct DGArgs {
 };
 
 int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+size_t dg_member_bytes();
+int dg_residual_grouped(jfnk_ctx *const *ctx, int n, const double *const *U, double *const *f, void *dmem,
+                        cudaStream_t s);
 
 // reductions / BLAS-1 (blas.cu)
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out_dev, int op, cudaStream_t s);

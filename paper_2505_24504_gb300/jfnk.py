@@ -92,6 +92,7 @@ def _lib():
             "jfnk_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
             "jfnk_batch_destroy": (None, [P]),
             "jfnk_batch_step": (I, [P, P, P, P, P, P]),
+            "jfnk_batch_dg_residual": (I, [P, P, P, P]),
             "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
@@ -142,6 +143,14 @@ class Batch:
         if raise_on_error:
             _check(rc, "jfnk_batch_step")
         return list(status), list(stats)
+
+    def jfnk_batch_dg_residual(self, states, outs, stream=None):
+        """f_m = M^-1 L_h(U_m) for all members: one face and one volume launch per
+        (order, viscous) group of members."""
+        n = len(self.contexts)
+        U = (C.c_void_p * n)(*[_ptr(s).value for s in states])
+        f = (C.c_void_p * n)(*[_ptr(o).value for o in outs])
+        _check(_lib().jfnk_batch_dg_residual(self.h, U, f, _stream(stream)), "jfnk_batch_dg_residual")
 
 
 def norm2_noalloc(x, out, n=None, stream=None):

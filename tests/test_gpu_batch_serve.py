@@ -81,3 +81,31 @@ def test_serving_mix_equals_alone_under_eviction():
         torch.cuda.synchronize()
         assert np.array_equal(to_cpu(U), to_cpu(specs[sid].U)), sid
         ctx.close()
+
+
+@pytest.mark.timeout(300)
+def test_grouped_residual_bitwise_equals_per_member():
+    # one face + one volume launch per (order, viscous) group must give each
+    # member exactly its own dg_residual; two members share order k = 2 so a
+    # group holds more than one member
+    import paper_2505_24504_gb300 as P
+    ms, _ = _members()
+    w = synth.BUBBLE_Q2_20x10
+    ms = ms + [synth.scaled(w, 10, 6, k=2, scheme=1), synth.scaled(w, 6, 3, k=1, scheme=1)]
+    ctxs = [gpu_context(m) for m in ms]
+    states, alone = [], []
+    for i, (m, c) in enumerate(zip(ms, ctxs)):
+        dg = oracle_dg(m)
+        u = to_gpu(synth.random_perturbation(dg.shape[1:], 40 + i))
+        f = torch.empty(c.N, dtype=torch.float64, device="cuda")
+        c.dg_residual(u, f)
+        states.append(u)
+        alone.append(to_cpu(f))
+    batch = P.Batch(ctxs)
+    outs = [torch.full((c.N,), float("nan"), dtype=torch.float64, device="cuda") for c in ctxs]
+    for _ in range(2):   # twice: the descriptors are rewritten in place
+        batch.jfnk_batch_dg_residual(states, outs)
+        torch.cuda.synchronize()
+        for a, o in zip(alone, outs):
+            assert np.array_equal(a, to_cpu(o))
+    batch.close()
