@@ -13,8 +13,9 @@
 // block order (so the bits do not depend on which block that is), writes the
 // result and resets the counter.  Nothing waits on another block.
 // Gram-Schmidt twice (CGS2) in three passes over the basis: h1 = V^T w; then
-// w1 = w - V h1 fused with h2 = V^T w1 and |w1|^2; then, when the device-side
-// test asks for it, w2 = w1 - V h2 with |w2|^2.
+// w1 = w - V h1 fused with h2 = V^T w1 and |w1|^2 (so |w2|^2 = |w1|^2 - |h2|^2);
+// then, when the device-side test asks for it, w2 = w1 - V h2, fused with the
+// normalisation.
 #include "internal.h"
 
 namespace {
@@ -244,62 +245,28 @@ __global__ void __launch_bounds__(RB) k_gs_update_dot(const double *V, size_t ld
     finish_multi<NV>(part, gridDim.x, h2);
     const double tot = sum_partials(part + (size_t)NV * gridDim.x, gridDim.x);
     if (threadIdx.x == 0) {
-        double hh = 0.0;
-        for (int j = 0; j < NV; ++j) hh += h1[j] * h1[j];
-        *w1sq = tot;
-        const double nr = sqrt(tot);
-        nrm[0] = nr;
-        nrm[S_INV - S_NORM] = nr != 0.0 ? 1.0 / nr : 0.0;
-        *flag = (tot < 0.5 * (tot + hh)) ? 1.0 : 0.0;
-        *ticket = 0u;
-    }
-}
-
-// pass 3 (only when flag != 0): w <- w - V h2, nrm = |w|
-template <int NV>
-__global__ void __launch_bounds__(RB) k_gs_update_norm(const double *V, size_t ldv, double *w, size_t n2,
-                                                       const double *h2, const double *flag, double *part,
-                                                       unsigned *ticket, double *nrm) {
-    jf_pdl_enter();
-    if (*flag == 0.0) return;
-    double2 *wv = reinterpret_cast<double2 *>(w);
-    const double2 *Vp[NV];
-    double c[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        Vp[j] = reinterpret_cast<const double2 *>(V + (size_t)j * ldv);
-        c[j] = -h2[j];
-    }
-    double sq = 0.0;
-    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
-        double2 a = wv[i];
-        double2 v[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
-#pragma unroll
+        double hh = 0.0, hh2 = 0.0;
         for (int j = 0; j < NV; ++j) {
-            a.x = fma(c[j], v[j].x, a.x);
-            a.y = fma(c[j], v[j].y, a.y);
+            hh += h1[j] * h1[j];
+            hh2 += h2[j] * h2[j];
         }
-        wv[i] = a;
-        sq = fma(a.y, a.y, fma(a.x, a.x, sq));
-    }
-    const double bs = block_sum(sq);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    if (!last_block(ticket)) return;
-    const double tot = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-        const double nr = sqrt(tot);
+        *w1sq = tot;
+        const bool second = tot < 0.5 * (tot + hh);
+        // |w2|^2 = |w1|^2 - |h2|^2 for w2 = w1 - V h2 with V orthonormal and h2 = V^T w1;
+        // after the first pass h2 is tiny against |w1|, so the difference does not cancel
+        const double nr = sqrt(second ? fmax(tot - hh2, 0.0) : tot);
         nrm[0] = nr;
         nrm[S_INV - S_NORM] = nr != 0.0 ? 1.0 / nr : 0.0;
+        *flag = second ? 1.0 : 0.0;
         *ticket = 0u;
     }
 }
 
 // double -> float by truncation of the fraction on the integer pipe (error below
-// one float ulp; enough for the first Gram-Schmidt pass): binary32 exponent =
-// binary64 exponent - 896, fraction = the top 23 of the 52 bits (IEEE 754
-// formats).  Values outside the normal float range use the conversion instruction.
+// one float ulp; enough for the first Gram-Schmidt pass and the preconditioner's
+// input): binary32 exponent = binary64 exponent - 896, fraction = the top 23 of
+// the 52 bits (IEEE 754 formats).  Values outside the normal float range use the
+// conversion instruction.
 __device__ __forceinline__ float d2f_trunc(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const int e = (int)((b >> 52) & 0x7ff) - 1023;
@@ -309,20 +276,41 @@ __device__ __forceinline__ float d2f_trunc(double d) {
     return __uint_as_float(r);
 }
 
-// v = w * inv (inv = 1/|w| from the Gram-Schmidt kernels), two elements per
-// thread; also the float copy of v used by the next first passes (v32 may be null)
-__global__ void k_scale_inv(const double *w, const double *inv, double *v, float *v32, size_t n2) {
+// pass 3 and the normalisation in one sweep, without a reduction (|w2| comes from
+// pass 2): v = (w - V h2) / |w2| when the second pass is needed, v = w / |w| else;
+// also the float copy of v for later first passes (w32 may be null)
+template <int NV>
+__global__ void __launch_bounds__(RB) k_gs_update_scale(const double *V, size_t ldv, double *w, float *w32,
+                                                        size_t n2, const double *h2, const double *flag,
+                                                        const double *inv) {
     jf_pdl_enter();
-    const double s = *inv;
-    const double2 *w2 = reinterpret_cast<const double2 *>(w);
-    double2 *v2 = reinterpret_cast<double2 *>(v);
-    float2 *f2 = reinterpret_cast<float2 *>(v32);
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        const double2 a = w2[i];
-        const double2 o = make_double2(a.x * s, a.y * s);
-        v2[i] = o;
-        if (v32) f2[i] = make_float2(d2f_trunc(o.x), d2f_trunc(o.y));
+    const bool second = *flag != 0.0;
+    const double sc = *inv;
+    double2 *wv = reinterpret_cast<double2 *>(w);
+    float2 *f2 = reinterpret_cast<float2 *>(w32);
+    const double2 *Vp[NV];
+    double c[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        Vp[j] = reinterpret_cast<const double2 *>(V + (size_t)j * ldv);
+        c[j] = -h2[j];
+    }
+    for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n2; i += (size_t)gridDim.x * RB) {
+        double2 a = wv[i];
+        if (second) {
+            double2 v[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) v[j] = Vp[j][i];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                a.x = fma(c[j], v[j].x, a.x);
+                a.y = fma(c[j], v[j].y, a.y);
+            }
+        }
+        a.x *= sc;
+        a.y *= sc;
+        wv[i] = a;
+        if (w32) f2[i] = make_float2(d2f_trunc(a.x), d2f_trunc(a.y));
     }
 }
 
@@ -640,7 +628,7 @@ int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out,
 
 // CGS2 of w against V_0..V_{nv-1} (nv <= GS_FUSED_MAX; n even, V, w 16-byte
 // aligned), then w <- w / |w|: h1, h2, |w1|^2, the second-pass flag, |w| and
-// 1/|w| (nrm[S_INV - S_NORM]) land in device memory.
+// 1/|w| (nrm[S_INV - S_NORM]) land in device memory.  Three launches.
 // One wave: the SM count times the blocks of this kernel an SM holds, at most
 // three (FP64-bound kernels lose a partial second wave otherwise), fewer for
 // short vectors.
@@ -663,7 +651,7 @@ template <int NV>
 static void cgs2_t(jfnk_ctx *c, const double *V, const float *V32, size_t ldv, double *w, float *w32, size_t n,
                    double *h1, double *h2, double *w1sq, double *nrm, double *flag, cudaStream_t s) {
     const size_t n2 = n / 2;
-    const int g2 = one_wave(c, k_gs_update_dot<NV>, n2), g3 = one_wave(c, k_gs_update_norm<NV>, n2);
+    const int g2 = one_wave(c, k_gs_update_dot<NV>, n2), g3 = one_wave(c, k_gs_update_scale<NV>, n2);
     if (V32) {
         const int g1 = one_wave(c, k_gs_dot32<NV>, n2);
         jf_launch(k_gs_dot32<NV>, g1, RB, 0, s, V32, ldv, w, n2, c->partial, c->ticket, h1);
@@ -672,9 +660,8 @@ static void cgs2_t(jfnk_ctx *c, const double *V, const float *V32, size_t ldv, d
         jf_launch(k_gs_dot<NV>, g1, RB, 0, s, V, ldv, w, n2, c->partial, c->ticket, h1);
     }
     jf_launch(k_gs_update_dot<NV>, g2, RB, 0, s, V, ldv, w, n2, h1, c->partial, c->ticket, h2, w1sq, nrm, flag);
-    jf_launch(k_gs_update_norm<NV>, g3, RB, 0, s, V, ldv, w, n2, h2, flag, c->partial, c->ticket, nrm);
-    jf_launch(k_scale_inv, grid_for(n2), 256, 0, s, w, nrm + (S_INV - S_NORM), w, w32, n2);
-    jf_launched(4);
+    jf_launch(k_gs_update_scale<NV>, g3, RB, 0, s, V, ldv, w, w32, n2, h2, flag, nrm + (S_INV - S_NORM));
+    jf_launched(3);
 }
 
 int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv, double *w, float *w32, size_t n,
