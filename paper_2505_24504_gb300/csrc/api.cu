@@ -164,6 +164,7 @@ size_t workspace(const jfnk_grid *g, int k, const jfnk_opts *o, const jfnk_physi
         b += sS * n * 6 + sS * n / 4;
     }
     b += 8 * 4096 * 32 + 8 * 256;
+    b += 8 * (fx + fz) * (visc ? 16 : 8);   // face traces of the Newton iterate
     if (nlev_out) *nlev_out = nl;
     return b;
 }
@@ -489,6 +490,11 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
         c->n_sm = nsm;
     }
     A_(c->partial, 8 * (size_t)c->nb_red * 32);
+    {
+        const size_t nfp = (size_t)g->nz * (g->nx + 1) * c->np1 + (size_t)(g->nz + 1) * g->nx * c->np1;
+        A_(c->trU, 8 * nfp * (ph->mu != 0.0 ? 16 : 8));
+        c->tr_valid = 0;
+    }
     A_(c->scal, 8 * (size_t)S_COUNT);
     A_(c->ticket, 256);
     {

@@ -79,13 +79,45 @@ template <class T>
 JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
 
 // ---------------------------------------------------------------------------
+// Value and (viscous) derivative traces along a line of NP1 nodes i0 + q st with
+// the end-point tables (pa: l_q(+-1), pd: l_q'(+-1)).
+template <class T, int IN, int NP1, bool VISC>
+JF_D void line_trace(const Loader<T, IN> &ld, size_t i0, size_t st, const double *pa, const float *paf,
+                     const double *pd, const float *pdf, T &a, T &d) {
+    a = mk(0.0, T{});
+    d = mk(0.0, T{});
+#pragma unroll
+    for (int q = 0; q < NP1; ++q) {
+        const T u = ld(i0 + q * st);
+        a = jfma(mkc(pa[q], paf[q], T{}), u, a);
+        if (VISC) d = jfma(mkc(pd[q], pdf[q], T{}), u, d);
+    }
+}
+// The same traces of the FD state U + eps y from the stored traces of U (Newton
+// iterate, written by the residual) and the traces of y: tr(U + eps y) =
+// tr(U) + eps tr(y) -- the U part is then the same bits as in f(U).
+template <int NP1, bool VISC>
+JF_D void line_trace_fd(const Loader<D64, 1> &ld, size_t i0, size_t st, const double *pa, const double *pd,
+                        double trU, double dU, D64 &a, D64 &d) {
+    double ay = 0.0, dy = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP1; ++q) {
+        const double y = ld.y[i0 + q * st];
+        ay = __fma_rn(pa[q], y, ay);
+        if (VISC) dy = __fma_rn(pd[q], y, dy);
+    }
+    a = D64{__fma_rn(ld.eps, ay, trU)};
+    d = D64{VISC ? __fma_rn(ld.eps, dy, dU) : 0.0};
+}
+
 // Body of the face kernel for block `blk` of one operator evaluation; K is the
 // launch parameter (single operator) or a member's descriptor in global memory
 // (grouped launch over ensemble members).
 template <class T, int IN, int NP1, bool VISC>
 __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld0, typename OutT<T>::type *phix,
                                            typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
-                                           typename OutT<T>::type *symz, unsigned blk) {
+                                           typename OutT<T>::type *symz, unsigned blk, double *tr_out,
+                                           const double *tr_in) {
     typedef typename OutT<T>::type O;
     __shared__ PowTab spt;
     if (IN != 2) load_powtab(&spt, K.pt);   // the FP32 tangent power needs no table
@@ -121,18 +153,34 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
         }
         // traces: L at xi = +1 (row s), R at xi = -1
         T trL[4], trR[4], gL[4], gR[4];
+        const size_t nfp = (size_t)(nvert + nhorz);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            T aL = zero, aR = zero, dL = zero, dR = zero;
-#pragma unroll
-            for (int a = 0; a < NP1; ++a) {
-                const T uL = ld((size_t)v * N1 + (size_t)eL * NP + s * NP1 + a);
-                const T uR = ld((size_t)v * N1 + (size_t)eR * NP + s * NP1 + a);
-                aL = jfma(mkc(K.tab.lp[a], K.tlp[a], T{}), uL, aL);
-                aR = jfma(mkc(K.tab.lm[a], K.tlm[a], T{}), uR, aR);
-                if (VISC) {
-                    dL = jfma(mkc(K.tab.dlp[a], K.tdlp[a], T{}), uL, dL);
-                    dR = jfma(mkc(K.tab.dlm[a], K.tdlm[a], T{}), uR, dR);
+            T aL, aR, dL, dR;
+            const size_t iL0 = (size_t)v * N1 + (size_t)eL * NP + s * NP1;
+            const size_t iR0 = (size_t)v * N1 + (size_t)eR * NP + s * NP1;
+            bool done = false;
+            if constexpr (IN == 1) {
+                if (tr_in) {
+                    line_trace_fd<NP1, VISC>(ld, iL0, 1, K.tab.lp, K.tab.dlp, tr_in[(2 * v) * nfp + t],
+                                             VISC ? tr_in[(8 + 2 * v) * nfp + t] : 0.0, aL, dL);
+                    line_trace_fd<NP1, VISC>(ld, iR0, 1, K.tab.lm, K.tab.dlm, tr_in[(2 * v + 1) * nfp + t],
+                                             VISC ? tr_in[(9 + 2 * v) * nfp + t] : 0.0, aR, dR);
+                    done = true;
+                }
+            }
+            if (!done) {
+                line_trace<T, IN, NP1, VISC>(ld, iL0, 1, K.tab.lp, K.tlp, K.tab.dlp, K.tdlp, aL, dL);
+                line_trace<T, IN, NP1, VISC>(ld, iR0, 1, K.tab.lm, K.tlm, K.tab.dlm, K.tdlm, aR, dR);
+            }
+            if constexpr (IN == 0) {
+                if (tr_out) {
+                    tr_out[(2 * v) * nfp + t] = outv(aL);
+                    tr_out[(2 * v + 1) * nfp + t] = outv(aR);
+                    if (VISC) {
+                        tr_out[(8 + 2 * v) * nfp + t] = outv(dL);
+                        tr_out[(9 + 2 * v) * nfp + t] = outv(dR);
+                    }
                 }
             }
             trL[v] = aL;
@@ -200,18 +248,34 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
         const int eB = (wallB ? 0 : fz - 1) * nx + ex;
         const int eT = (wallT ? nz - 1 : fz) * nx + ex;
         T trB[4], trT[4], gB[4], gT[4];
+        const size_t nfp = (size_t)(nvert + nhorz);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            T aB = zero, aT = zero, dB = zero, dT = zero;
-#pragma unroll
-            for (int b = 0; b < NP1; ++b) {
-                const T uB = ld((size_t)v * N1 + (size_t)eB * NP + b * NP1 + s);
-                const T uT = ld((size_t)v * N1 + (size_t)eT * NP + b * NP1 + s);
-                aB = jfma(mkc(K.tab.lp[b], K.tlp[b], T{}), uB, aB);
-                aT = jfma(mkc(K.tab.lm[b], K.tlm[b], T{}), uT, aT);
-                if (VISC) {
-                    dB = jfma(mkc(K.tab.dlp[b], K.tdlp[b], T{}), uB, dB);
-                    dT = jfma(mkc(K.tab.dlm[b], K.tdlm[b], T{}), uT, dT);
+            T aB, aT, dB, dT;
+            const size_t iB0 = (size_t)v * N1 + (size_t)eB * NP + s;
+            const size_t iT0 = (size_t)v * N1 + (size_t)eT * NP + s;
+            bool done = false;
+            if constexpr (IN == 1) {
+                if (tr_in) {
+                    line_trace_fd<NP1, VISC>(ld, iB0, NP1, K.tab.lp, K.tab.dlp, tr_in[(2 * v) * nfp + t],
+                                             VISC ? tr_in[(8 + 2 * v) * nfp + t] : 0.0, aB, dB);
+                    line_trace_fd<NP1, VISC>(ld, iT0, NP1, K.tab.lm, K.tab.dlm, tr_in[(2 * v + 1) * nfp + t],
+                                             VISC ? tr_in[(9 + 2 * v) * nfp + t] : 0.0, aT, dT);
+                    done = true;
+                }
+            }
+            if (!done) {
+                line_trace<T, IN, NP1, VISC>(ld, iB0, NP1, K.tab.lp, K.tlp, K.tab.dlp, K.tdlp, aB, dB);
+                line_trace<T, IN, NP1, VISC>(ld, iT0, NP1, K.tab.lm, K.tlm, K.tab.dlm, K.tdlm, aT, dT);
+            }
+            if constexpr (IN == 0) {
+                if (tr_out) {
+                    tr_out[(2 * v) * nfp + t] = outv(aB);
+                    tr_out[(2 * v + 1) * nfp + t] = outv(aT);
+                    if (VISC) {
+                        tr_out[(8 + 2 * v) * nfp + t] = outv(dB);
+                        tr_out[(9 + 2 * v) * nfp + t] = outv(dT);
+                    }
                 }
             }
             trB[v] = aB;
@@ -275,9 +339,9 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
 template <class T, int IN, int NP1, bool VISC>
 __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
                                                typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
-                                               typename OutT<T>::type *symz) {
+                                               typename OutT<T>::type *symz, double *tr_out, const double *tr_in) {
     jf_pdl_enter();
-    faces_body<T, IN, NP1, VISC>(K, ld0, phix, symx, phiz, symz, blockIdx.x);
+    faces_body<T, IN, NP1, VISC>(K, ld0, phix, symx, phiz, symz, blockIdx.x, tr_out, tr_in);
 }
 
 // ---------------------------------------------------------------------------
@@ -582,7 +646,8 @@ int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, 
     const long long nf = (long long)K.nz * (K.nx + 1) * NP1 + (long long)(K.nz + 1) * K.nx * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
     const int tf = c->opts.tile_faces;
-    jf_launch(k_faces<T, IN, NP1, VISC>, (unsigned)((nf + tf - 1) / tf), tf, 0, s, K, ld, phix, symx, phiz, symz); jf_launched();
+    jf_launch(k_faces<T, IN, NP1, VISC>, (unsigned)((nf + tf - 1) / tf), tf, 0, s, K, ld, phix, symx, phiz, symz,
+              a.tr_out, a.tr_in); jf_launched();
     if (c->timing) JF_CK(cudaEventRecord(c->tev[1], s));
     if (c->opts.tile_volume == 1) {
         constexpr int EPB = EPBOf<NP1, 1>::value;
@@ -641,7 +706,7 @@ __global__ void __launch_bounds__(256, 4) k_faces_grp(const DGMember *mem, int n
     int m = 0;
     while (m + 1 < nm && blockIdx.x >= mem[m + 1].fb0) ++m;   // members in block order
     const DGMember &M = mem[m];
-    faces_body<D64, 0, NP1, VISC>(M.K, M.ld, M.phix, M.symx, M.phiz, M.symz, blockIdx.x - M.fb0);
+    faces_body<D64, 0, NP1, VISC>(M.K, M.ld, M.phix, M.symx, M.phiz, M.symz, blockIdx.x - M.fb0, nullptr, nullptr);
 }
 
 template <int NP1, bool VISC>
@@ -678,6 +743,8 @@ int dg_setup_background(jfnk_ctx *c) {
 
 int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
     c->dg_calls++;
+    // the stored traces belong to the cached f(U): any other writer of the cache drops them
+    if (a.out0 == c->fU || a.out1 == c->fU) c->tr_valid = a.tr_out == c->trU ? 1 : 0;
     const bool visc = c->phys.mu != 0.0;
     switch (c->np1) {
         case 2: return visc ? dispatch_mode<2, true>(c, mode, a, s) : dispatch_mode<2, false>(c, mode, a, s);

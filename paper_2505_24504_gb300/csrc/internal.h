@@ -119,6 +119,8 @@ struct jfnk_ctx {
     FVLev lev[JF_MAXLEV];
     // reductions
     double *partial;     // scratch partial sums
+    double *trU;         // face traces of the Newton iterate (values, and derivatives when viscous)
+    int tr_valid;        // trU and fU come from the same residual evaluation
     unsigned *ticket;    // arrival counter of the single-launch reductions (0 between launches)
     int nb_red;          // partial-sum blocks
     int n_sm;            // streaming multiprocessors of the context's device
@@ -203,6 +205,8 @@ struct DGArgs {
     double adt;
     void *out0;
     double *out1;
+    double *tr_out;        // FP64 residual / G: store the face traces of U here (may be null)
+    const double *tr_in;   // FP64 FD product: face traces of U from the residual at U (may be null)
 };
 
 int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);

@@ -67,6 +67,7 @@ int apply_jv(jfnk_ctx *c, const double *U, double adt, const double *y, double *
     a.eps = c->scal + S_EPS;
     a.adt = adt;
     a.out0 = w;
+    a.tr_in = c->tr_valid ? c->trU : nullptr;   // U is the iterate of the last residual
     return dg_apply(c, DG_JV, a, s);
 }
 
@@ -264,6 +265,7 @@ int eval_G(jfnk_ctx *c, const double *U, double adt, double *nrm, cudaStream_t s
     a.adt = adt;
     a.out0 = c->G;
     a.out1 = c->fU;
+    a.tr_out = c->trU;   // the FD products of this Newton iterate reuse its face traces
     JF_RET(dg_apply(c, DG_G, a, s));
     return read_norm(c, c->G, nrm, s);
 }
