@@ -42,9 +42,9 @@ L2_FLUSH_BYTES = 512 << 20
 # volume kernel (per node) for Euler, k = 3; see DESIGN.md "roofline".  An FMA
 # counts 2 flops, add / mul 1; division and square root count the FP64
 # instructions of their IEEE-correct sequences; x^gamma the table power's.
-FLOPS_FACE_POINT = 298.0   # k_faces, FD product (profiles/dg_fp64_fd_product_w2.md)
-FLOPS_NODE = 185.0         # k_volume, FD product
-TRAFFIC_FACE = 13_275_392  # dram read + write bytes of one k_faces FD launch (ncu, cold L2; writes stay in L2)
+FLOPS_FACE_POINT = 250.0   # k_faces, FD product from stored traces of U (profiles/dg_fp64_fd_product_w2.md)
+FLOPS_NODE = 184.0         # k_volume, FD product
+TRAFFIC_FACE = 13_339_904  # dram read + write bytes of one k_faces FD launch (ncu, cold L2; writes stay in L2)
 
 
 def parse():

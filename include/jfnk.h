@@ -277,8 +277,10 @@ int jfnk_eos_pressure(jfnk_ctx *ctx, const double *E_dev, size_t n, double *p_de
 
 /* Times the two kernels of one DG operator evaluation with CUDA events
  * recorded on `stream` around each launch: which 0 = FP64 residual,
- * 1 = FP64 finite-difference product with direction y, 2 = FP32 tangent
- * product (contexts with precond_prec < 64).  Runs `reps` evaluations;
+ * 1 = FP64 finite-difference product with direction y (in the form the
+ * solver's Arnoldi steps use: face traces of U stored by the residual at U,
+ * plus eps times the traces of y), 2 = FP32 tangent product (contexts with
+ * precond_prec < 64).  Runs `reps` evaluations;
  * ms[0], ms[1] receive the mean duration of the face and the volume kernel. */
 int jfnk_time_operator(jfnk_ctx *ctx, int which, const double *U_dev, const double *y_dev, int reps,
                        double *ms_host, void *stream);

@@ -633,13 +633,17 @@ int jfnk_time_operator(jfnk_ctx *c, int which, const double *U, const double *y,
     a.U = U;
     a.adt = 1.0;
     if (which == 1) {
-        // f(U) and eps once, outside the timed launches
+        // f(U), its face traces and eps once, outside the timed launches; the timed
+        // products take the form the solver's Arnoldi steps use (stored traces of U)
         a.out0 = c->fU;
+        a.tr_out = c->trU;
         rc = dg_apply(c, DG_RES, a, s);
+        a.tr_out = nullptr;
         if (!rc) rc = red_dot(c, y, y, c->N, c->scal + S_EPS, RED_EPS, s);
         a.y = y;
         a.fU = c->fU;
         a.eps = c->scal + S_EPS;
+        a.tr_in = c->trU;
     }
     if (which == 2) {
         rc = blas_copy_d2f(y, (float *)c->pz, c->N, s);
