@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 # FP64 pipe operations per unit of the two DG kernels in the FD-product mode,
 # counted from the D64 source of the face kernel (per face point) and of the
-# volume kernel (per node) for Euler, k = 3; see DESIGN.md "roofline".  An FMA
+# volume kernel (per node) for Euler, k = 3 (profiles/dg_fp64_fd_product_w2.md).  An FMA
 # counts 2 flops, add / mul 1; division and square root count the FP64
 # instructions of their IEEE-correct sequences; x^gamma the table power's.
 FLOPS_FACE_POINT = 250.0   # k_faces, FD product from stored traces of U (profiles/dg_fp64_fd_product_w2.md)
@@ -615,7 +615,7 @@ def main():
         dist.destroy_process_group()
 
 
-FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (a DFMA-chain probe measured 1.19)
 
 if __name__ == "__main__":
     main()
