@@ -2,7 +2,8 @@
 
 `jfnk_autotune` (C ABI) times the tile choices of one context on the device:
 threads per block of the DG face kernel, elements per DG volume block, threads
-per block of the FV cell kernels.  This module keys the winners by GPU name,
+per block of the FV cell kernels and the level size below which FV levels run
+four lanes per cell.  This module keys the winners by GPU name,
 order, grid, viscosity, preconditioner precision and mg key, stores them in a
 JSON file (default: _tune_cache.json next to this module, not versioned) and
 applies them to the options of new contexts of the same shape.
