@@ -265,14 +265,20 @@ __global__ void __launch_bounds__(RB) k_gs_update_dot(const double *V, size_t ld
 // double -> float by truncation of the fraction on the integer pipe (error below
 // one float ulp; enough for the first Gram-Schmidt pass and the preconditioner's
 // input): binary32 exponent = binary64 exponent - 896, fraction = the top 23 of
-// the 52 bits (IEEE 754 formats).  Values outside the normal float range use the
-// conversion instruction.
+// the 52 bits (IEEE 754 formats).  Magnitudes below the normal float range give
+// a signed zero, larger ones (and NaN) use the conversion instruction.
+// Rare inputs take an out-of-line conversion: inline, the compiler would turn the
+// branch into a select and run the FP64-pipe conversion for every element.
+__device__ __noinline__ float d2f_slow(double d) { return (float)d; }
+__device__ __noinline__ double f2d_slow(float f) { return (double)f; }
+
 __device__ __forceinline__ float d2f_trunc(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126 || e > 127) return (float)d;
-    const unsigned r = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e + 127) << 23) |
-                       (unsigned)((b >> 29) & 0x7fffffu);
+    const unsigned sign = (unsigned)((b >> 32) & 0x80000000u);
+    if (e > 127) return d2f_slow(d);   // overflow, infinity, NaN
+    // below the normal float range (zero included): signed zero
+    const unsigned r = e < -126 ? sign : sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
     return __uint_as_float(r);
 }
 
@@ -520,15 +526,17 @@ __global__ void __launch_bounds__(RB) k_final_gs(const double *part, int nb, con
 
 // float -> double widening on the integer pipe, exact: binary64 re-biases the
 // binary32 exponent by 1023 - 127 = 896 and takes the 23 fraction bits as the
-// top of its 52 (IEEE 754 formats).  Zero, subnormal, infinite and NaN inputs
-// use the conversion instruction (an FP64-pipe operation, like the DFMA).
+// top of its 52 (IEEE 754 formats); zero keeps its sign.  Subnormal, infinite
+// and NaN inputs use the conversion instruction (an FP64-pipe operation, like
+// the DFMA), out of line.
 __device__ __forceinline__ double f2d_bits(float f) {
     const unsigned b = __float_as_uint(f);
     const unsigned e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + 896u) << 52) |
-                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if ((b & 0x7fffffffu) != 0u && (e == 0u || e == 0xffu)) return f2d_slow(f);   // subnormal, inf, NaN
+    const unsigned long long r = (b & 0x7fffffffu) == 0u ? sign
+                                                          : sign | ((unsigned long long)(e + 896u) << 52) |
+                                                                ((unsigned long long)(b & 0x7fffffu) << 29);
     return __longlong_as_double((long long)r);
 }
 
