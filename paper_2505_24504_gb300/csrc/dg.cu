@@ -409,7 +409,7 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
             pxr[v] = phix[v * fsx + iR];
             pzb[v] = phiz[v * fsz + iB];
             pzt[v] = phiz[v * fsz + iT];
-            if (MODE == DG_TLSMOOTH) ef[v] = A.rf[(size_t)v * N1 + (size_t)e * NP + node];
+            if (MODE == DG_TLSMOOTH || (MODE == DG_TLJV && A.rf)) ef[v] = A.rf[(size_t)v * N1 + (size_t)e * NP + node];
         }
         if (MODE == DG_TLSMOOTH) edt = A.dtauf[e];
     }
@@ -506,7 +506,8 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
             ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
         } else if (MODE == DG_TLJV) {
             const float z = (float)outv(Up[v]);   // the loader's tangent input is y
-            ((float *)A.out0)[gi] = z - adtf * (float)f;
+            const float jz = z - adtf * (float)f;
+            ((float *)A.out0)[gi] = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
         } else {  // DG_TLSMOOTH
             const float z = (float)outv(Up[v]);
             const float Jz = z - adtf * (float)f;

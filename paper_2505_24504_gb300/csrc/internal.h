@@ -186,7 +186,7 @@ enum DGMode {
     DG_JV = 1,       // out0 = y - adt (f(U' + eps y) - fU) / eps       (eps: device scalar)
     DG_G = 2,        // out0 = U' - adt f - Ubar_s ; out1 = f
     DG_SMOOTH64 = 3, // out0 = z + dtau (r - [z - adt (f(U'+eps z) - fU)/eps])
-    DG_TLJV = 4,     // out0 = z - adt J z                             (FP32 tangent)
+    DG_TLJV = 4,     // out0 = z - adt J z, or r - (z - adt J z) when rf is given  (FP32 tangent)
     DG_TLSMOOTH = 5  // out0 = z + dtau (r - (z - adt J z))            (FP32 tangent)
 };
 

@@ -1371,12 +1371,10 @@ int dg_defect<float>(jfnk_ctx *c, const float *r, const float *z, float *d, cuda
     a.U = c->mg_U;
     a.Uf = c->Usf;
     a.yf = z;
+    a.rf = r;   // the tangent product's epilogue forms d = r - G'z
     a.adt = c->mg_adt;
     a.out0 = d;
-    JF_RET(dg_apply(c, DG_TLJV, a, s));
-    jf_launch(k_sub<float>, nblk(c->N, 256), 256, 0, s, r, d, d, c->N); jf_launched();
-    JF_CK(cudaGetLastError());
-    return JFNK_OK;
+    return dg_apply(c, DG_TLJV, a, s);
 }
 
 template <class S>
