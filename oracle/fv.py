@@ -18,7 +18,9 @@
 * Smoother: explicit Euler in pseudo time for dw/dtau = -(g'(u) w - b) with the
   local step dtau = sigma / (1 + alpha dt lambda_c) (Sec. 3.5).
 * g'(u) x by the finite difference of Sec. 3.1 applied to g(u) = u - alpha dt
-  f_low(u) - ubar_s, with eps = sqrt(eps_mach)/|x| over the level's vector.
+  f_low(u) - ubar_s, with eps = sqrt(eps_mach)/|x| over the level's vector
+  (`fd_eps` replaces the numerator sqrt(eps_mach) for the preconditioner's FD
+  products, FV and DG smoothing alike; the paper's value is the default).
 """
 from __future__ import annotations
 
@@ -210,7 +212,7 @@ class Multigrid:
     """Q^-1 = T^-1 q^-1 T with DG pre/post smoothing (Sec. 3.2-3.5)."""
 
     def __init__(self, dg: DG, levels: int, mg_key="mg111111V", sigma_fv=1.0, sigma_dg=1.0,
-                 massfix=True, l2=False):
+                 massfix=True, l2=False, fd_eps=None):
         self.dg = dg
         self.key = parse_mg_key(mg_key)
         sizes, facs = hierarchy(dg.nx, dg.nz, dg.k, levels)
@@ -220,7 +222,9 @@ class Multigrid:
         self.T = Transfer(dg, l2=l2)
         self.sigma_fv, self.sigma_dg = sigma_fv, sigma_dg
         self.massfix = massfix
-        self.stats = dict(dg_calls=0, fv_calls=[0] * len(sizes))
+        # numerator of eps = c / |x| in the preconditioner's FD products (Sec. 3.1: c = sqrt(eps_mach))
+        self.fd_c = np.sqrt(EPS_MACH) if fd_eps is None else float(fd_eps)
+        self.stats = dict(dg_calls=0, fv_calls=[0] * len(sizes), visits=[0] * len(sizes))
 
     # -- linearisation at the Newton iterate U^k ----------------------------
     def linearize(self, Up, alpha_dt, fU=None):
@@ -243,7 +247,7 @@ class Multigrid:
         nx_ = np.sqrt(np.sum(x * x))
         if nx_ == 0.0:
             return np.zeros_like(x)
-        eps = np.sqrt(EPS_MACH) / nx_
+        eps = self.fd_c / nx_
         self.stats['fv_calls'][l] += 1
         return x - self.alpha_dt * (self.levels[l].rhs(self.u[l] + eps * x) - self.fu[l]) / eps
 
@@ -260,6 +264,7 @@ class Multigrid:
     def mg(self, l, x, b, zero):
         """MG_l(x, b; u_l), level index l counted from the finest (0)."""
         nl = len(self.levels)
+        self.stats['visits'][l] += 1
         if l == 0:
             pre, post = self.key['fine_pre'], self.key['fine_post']
         else:
@@ -283,7 +288,10 @@ class Multigrid:
     # -- DG level --------------------------------------------------------------
     def dg_gprime(self, z):
         self.stats['dg_calls'] += 1
-        return self.dg.jv(self.Up, self.fU, z, self.alpha_dt)
+        nz_ = np.sqrt(np.sum(z * z))
+        if nz_ == 0.0:
+            return np.zeros_like(z)
+        return self.dg.jv(self.Up, self.fU, z, self.alpha_dt, eps=self.fd_c / nz_)
 
     def apply(self, r):
         """z = Q^-1 r: DG pre-smoothing, transfer of the DG residual, FV multigrid

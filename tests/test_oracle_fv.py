@@ -188,3 +188,108 @@ def test_l2_transfer_gives_cell_averages_and_conserves_mass(k):
         m_dg = np.sum(dg.mass_weights() * ur[var])
         assert abs(cell * vr[var].sum() - m_dg) <= 1e-13 * np.sum(np.abs(dg.mass_weights() * ur[var]))
     np.testing.assert_allclose(T.to_dg(vr), ur, atol=1e-11 * np.abs(ur).max())
+
+
+# ---- pins of the two-point viscous flux of f_low (reading of Sec. 3.2 / 4.3) ----
+
+def _visc_level(NX, NZ, periodic):
+    ph = Physics(cp=1004.0, cv=717.0, g=0.0, p0=1e5, theta0=300.0, mu=75.0, background=UNIFORM)
+    return FVLevel(NX, NZ, 0.0, 16000.0, 0.0, 6000.0, ph, periodic_x=periodic), ph
+
+
+def test_fv_viscous_flux_is_the_periodic_five_point_laplacian_in_x():
+    # rho constant, no motion, theta = theta0 + a cos(2 pi m x / L) at the cell
+    # centres, periodic in x: mu {rho} (theta_R - theta_L)/H summed over the two x
+    # faces is mu rho times the periodic 3-point second difference, whose
+    # eigenvalue on this mode is -(4/H^2) sin^2(pi m H / L) (closed form).  A
+    # flipped sign, a wrong 1/2 in the face average or a wrong spacing fails.
+    lev, ph = _visc_level(16, 3, True)
+    rho0, a, m = 1.17, 0.8, 3
+    xc = (np.arange(lev.NX) + 0.5) * lev.Hx
+    th = 300.0 + a * np.cos(2 * np.pi * m * xc / 16000.0)
+    U = np.zeros(lev.shape)
+    U[0] = rho0
+    U[3] = rho0 * th[None, :]
+    V = lev._viscous(U)
+    lam = -(4.0 / lev.Hx ** 2) * np.sin(np.pi * m * lev.Hx / 16000.0) ** 2
+    ref = ph.mu * rho0 * lam * a * np.cos(2 * np.pi * m * xc / 16000.0)
+    np.testing.assert_allclose(V[3], np.broadcast_to(ref, V[3].shape), rtol=1e-12, atol=1e-15)
+    assert np.all(V[0] == 0.0) and np.abs(V[1:3]).max() < 1e-18
+
+
+def test_fv_viscous_flux_has_no_wall_flux_in_z():
+    # u = a cos(pi m (z - z0)/Lz) at the centres with slip walls at z0 and z1:
+    # zero viscous flux through the walls makes this the cell-centred Neumann
+    # second difference, eigenvalue -(4/H^2) sin^2(pi m H / (2 Lz)) on every row,
+    # boundary rows included (a wall flux would change exactly those rows).
+    lev, ph = _visc_level(4, 12, False)
+    rho0, a, m = 0.93, 2.5, 2
+    zc = (np.arange(lev.NZ) + 0.5) * lev.Hz
+    u = a * np.cos(np.pi * m * zc / 6000.0)
+    U = np.zeros(lev.shape)
+    U[0] = rho0
+    U[1] = rho0 * u[:, None]
+    U[3] = rho0 * 300.0
+    V = lev._viscous(U)
+    lam = -(4.0 / lev.Hz ** 2) * np.sin(np.pi * m * lev.Hz / (2 * 6000.0)) ** 2
+    ref = ph.mu * rho0 * lam * u
+    np.testing.assert_allclose(V[1], np.broadcast_to(ref[:, None], V[1].shape), rtol=1e-12, atol=1e-15)
+    assert np.abs(V[2]).max() < 1e-18 and np.abs(V[3]).max() < 1e-12
+
+
+def test_fv_viscous_flux_of_a_linear_shear_with_variable_density():
+    # u = s z with rho varying by row: the two-point flux mu {rho} (u_R - u_L)/H is
+    # exact for a linear u, mu s (rho_j + rho_{j+1})/2 through face j+1/2, so the
+    # interior divergence is mu s (rho_{j+1} - rho_{j-1}) / (2 H).  Differencing
+    # the momentum instead of the velocity, or dropping the density average, fails.
+    lev, ph = _visc_level(5, 9, True)
+    s = 3.0e-3
+    rho = 1.0 + 0.2 * np.random.default_rng(3).random(lev.NZ)
+    zc = (np.arange(lev.NZ) + 0.5) * lev.Hz
+    U = np.zeros(lev.shape)
+    U[0] = rho[:, None]
+    U[1] = (rho * s * zc)[:, None]
+    U[3] = rho[:, None] * 300.0
+    V = lev._viscous(U)
+    ref = ph.mu * s * (rho[2:] - rho[:-2]) / (2 * lev.Hz)
+    np.testing.assert_allclose(V[1, 1:-1], np.broadcast_to(ref[:, None], V[1, 1:-1].shape), rtol=1e-10)
+    assert np.abs(V[2]).max() < 1e-15 and np.abs(V[3]).max() < 1e-10
+
+
+# ---- pins of the W cycle (Sec. 3.4: the coarse correction applied twice) ----
+
+def test_w_cycle_visits_level_l_two_to_the_l_times():
+    # MG_l calls MG_{l+1} `cycles` times: one cycle from the finest level visits
+    # level l once (V) or 2^l times (W)
+    w, dg, Up = _mg_case()
+    w4 = synth.scaled(w, 16, 8, k=1, fv_levels=4)
+    dg4 = DG(w4.nx, w4.nz, w4.x0, w4.x1, w4.z0, w4.z1, w4.k, ROBERT)
+    U4 = dg4.init_state(w4.theta_pert(dg4.X, dg4.Z))
+    for key, expect in (("mg001111V", [1, 1, 1, 1]), ("mg001111W", [1, 2, 4, 8])):
+        mg = Multigrid(dg4, 4, key)
+        assert len(mg.levels) == 4
+        mg.linearize(U4, 0.1 * w4.dt)
+        b = np.random.default_rng(1).standard_normal(mg.levels[0].shape)
+        mg.mg(0, np.zeros_like(b), b, True)
+        assert mg.stats['visits'] == expect
+
+
+def test_w_cycle_converges_at_least_as_fast_as_v_per_cycle():
+    # the W cycle solves the coarse-grid problems more accurately, so as a stand-
+    # alone solver on the moderate pseudo-CFL problem it contracts monotonically
+    # and per cycle at least as fast as the V cycle
+    w, dg, Up = _mg_case()
+    b = np.random.default_rng(0).standard_normal((4, 30, 60))
+    hist = {}
+    for key in ("mg001111V", "mg001111W"):
+        mg = Multigrid(dg, w.fv_levels, key)
+        mg.linearize(Up, 0.1 * w.dt)
+        x = np.zeros_like(b)
+        res = [norm(b)]
+        for _ in range(5):
+            x = x + mg.mg(0, np.zeros_like(b), b - mg.gprime(0, x), True)
+            res.append(norm(b - mg.gprime(0, x)))
+        hist[key] = res
+    rv, rw = hist["mg001111V"], hist["mg001111W"]
+    assert all(r1 < r0 for r0, r1 in zip(rw, rw[1:]))
+    assert rw[-1] <= rv[-1] * 1.000001
