@@ -5,10 +5,11 @@ multigrid preconditioner on one GB300, as one JSON line.
 Workload: warm bubble on DG Q3, 160 x 80 quads over [0,20 km] x [0,10 km]
 (819,200 unknowns), isentropic atmosphere theta0 = 300 K, +2 K cosine bubble
 plus seeded +-0.1 K white noise in theta, SDIRK2 at dt = 20x the acoustic CFL
-step, Newton TOL 1e-8, mg111111V with 5 FV levels.  A step is one SDIRK2 step
-(two Newton solves, every kernel of the path).  `value` is the FP32-
-preconditioner form (the preconditioner in FP32, residual / FD products /
-Arnoldi in FP64); the plain FP64 form is timed beside it.
+step, Newton TOL 1e-8, 5 FV levels, the recorded schedule and launch shapes of
+presets.WARM_BUBBLE_Q3_160x80.  A step is one SDIRK2 step (two Newton solves,
+every kernel of the path).  `value` is the FP32-preconditioner form (the
+preconditioner in FP32, residual / FD products / Arnoldi in FP64); the plain
+FP64 form is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -19,32 +20,41 @@ times the FP64 CPU oracle on the host cores (rank 0 only).
 """
 from __future__ import annotations
 
-import argparse
-import json
 import os
-import statistics
-import subprocess
 import sys
-import tempfile
-import time
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    # the CPU reference is single-threaded numpy: keep any math library on one thread
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+from paper_2505_24504_gb300 import presets  # noqa: E402
 
 WORKLOAD = synth.BUBBLE_Q3_160x80
+PRESET = presets.WARM_BUBBLE_Q3_160x80
 METRIC = "implicit steps/s & DOF/s at 1e-8 Newton tol (batched mixed vs plain FP64); p50/p99"
 L2_FLUSH_BYTES = 512 << 20
-
-# FP64 pipe operations per unit of the two DG kernels in the FD-product mode,
-# counted from the D64 source of the face kernel (per face point) and of the
-# volume kernel (per node) for Euler, k = 3 (profiles/dg_fp64_fd_product_w2.md).  An FMA
-# counts 2 flops, add / mul 1; division and square root count the FP64
-# instructions of their IEEE-correct sequences; x^gamma the table power's.
-FLOPS_FACE_POINT = 250.0   # k_faces, FD product from stored traces of U (profiles/dg_fp64_fd_product_w2.md)
-FLOPS_NODE = 184.0         # k_volume, FD product
-TRAFFIC_FACE = 13_339_904  # dram read + write bytes of one k_faces FD launch (ncu, cold L2; writes stay in L2)
+COUNTS_FILE = os.path.join(ROOT, "tests", "golden", "oracle_step_counts.json")
+COUNTS_KEY = "warm_bubble_q3_160x80"
+# nvidia-smi-free fallback of the roofline denominators (MEASURED_PEAKS.json absent)
+FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic per SM and clock: the nominal 1.25 TFLOP/s of a 152-SM GB300 at
+# 2.07 GHz is 2 DFMA (4 flops) per SM and clock
+FP64_FLOP_PER_SM_CLK = 4.0
+# DRAM bytes (read + write) of one FP64 FD-product face launch on this workload,
+# ncu, cold L2 (writes stay in L2)
+TRAFFIC_FACE = 13_339_904
 
 
 def parse():
@@ -57,16 +67,18 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=None)
     p.add_argument("--form", default="both", choices=["both", "fp32"],
                    help="fp32: time only the FP32-preconditioner steps (for profiler runs)")
+    p.add_argument("--tune", action="store_true",
+                   help="run the autotuner (schedule and launch shapes) instead of the recorded preset")
     p.add_argument("--ensemble", type=int, default=64, help="members of the batched ensemble (0: skip)")
     p.add_argument("--ensemble-steps", type=int, default=2)
     p.add_argument("--ensemble-threads", type=int, default=16, help="host threads / streams of the batched ensemble")
-    p.add_argument("--serve-seconds", type=float, default=1.0, help="Poisson arrival horizon (0: skip)")
-    p.add_argument("--viscous-steps", type=int, default=3, help="timed steps of the viscous workload (0: skip)")
-    p.add_argument("--igw-steps", type=int, default=5, help="timed steps of the inertia gravity workload (0: skip)")
-    p.add_argument("--schedule", default=None, metavar="KEY",
-                   help="use this mg key instead of searching the schedule (profiler runs)")
-    p.add_argument("--mg-sweep", action="store_true",
-                   help="also sweep the preconditioner key (none, mg001111V, mg111111V, mg111111W)")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="Poisson horizon below capacity (0: skip)")
+    p.add_argument("--serve-rate", type=float, default=40.0, help="arrival rate of the below-capacity run (1/s)")
+    p.add_argument("--overload-seconds", type=float, default=2.0, help="horizon of the 200/s overload run")
+    p.add_argument("--secondary-steps", type=int, default=3,
+                   help="timed steps of the viscous, inertia-gravity and rising-bubble workloads (0: skip)")
+    p.add_argument("--no-sweep", action="store_true", help="skip the mg-key sweep and the dt trends")
+    p.add_argument("--schedule", default=None, metavar="KEY", help="override the preset's mg key")
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
                    help="only run REPS FP64 FD products (face + volume kernels) of the workload "
                         "and print their CUDA-event times (small profiler captures)")
@@ -122,6 +134,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def config_of(w, world: int, preset=PRESET) -> dict:
+    """The `config` object of both arms (the same workload, schedule and tolerance)."""
+    return {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
+            "newton_tol": w.newton_tol, "fv_levels": w.fv_levels, "mg_key": preset["mg_key"],
+            "sigma_fv": preset["sigma_fv"], "sigma_dg": preset["sigma_dg"],
+            "l2": "GPU arm: flushed between timed steps (512 MiB write); CPU arm: host caches",
+            "parallelism": f"replicas x{world}"}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 # ---------------------------------------------------------------------------
 def make_args(w, prec, **kw):
     import paper_2505_24504_gb300 as P
@@ -159,6 +188,8 @@ def time_steps(ctx, U, w, steps, warmup, dist, flush):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    from paper_2505_24504_gb300 import jfnk
+    n0 = jfnk.launch_count()
     for _ in range(steps):
         flush.add_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -172,16 +203,99 @@ def time_steps(ctx, U, w, steps, warmup, dist, flush):
         ms += e0.elapsed_time(e1)
         stats.append(st.as_dict())
     torch.cuda.synchronize()
+    time_steps.launches = jfnk.launch_count() - n0   # this library's kernels in the timed steps
     if dist:
         dist.barrier()
     return ms, stats
 
 
-def make_context_for(w, prec):
-    return make_context(w, prec)
+def timed_once(ctx, U, w, **kw):
+    """(ms, stats) of one implicit step after one untimed step."""
+    import torch
+    ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    st = ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1), st
 
 
-def run_ensemble(n, steps, warmup, threads=16):
+# ---------------------------------------------------------------------------
+# Algorithmic FP64 flops of the FD product, from the formulas (a divide, square
+# root or x^gamma counts one flop, an FMA two, compares and selects none):
+#  face point, stored traces of U plus eps times the traces of y:
+#    traces of y: 2 sides x 4 variables x (k+1) FMA; tr(U) + eps tr(y): 8 FMA;
+#    + background: 8; HLLC: 1/rho 2, velocities 2, pressures 2 x 3, sound speeds
+#    2 x 3, wave-speed bounds 4, S - u 2, contact speed numerator 7, denominator
+#    3, quotient 1, star factor 4, star state 5, side flux 4, F + S (U* - U) 12
+#    (58); minus the background flux: 4
+#  node, volume term: U + eps y 4 FMA; + background 4; 1/rho 1; pressure 3;
+#    velocities 2; two convective fluxes 8; minus the background fluxes 8;
+#    sum factorisation 4 variables x 2 directions x (k+1) FMA; gravity 2; lift of
+#    the four face terms 4 x 4 FMA; FD quotient and update 3 per variable
+HLLC_FLOPS = 58
+
+
+def alg_flops_face_point(k):
+    return 2 * (2 * 4 * (k + 1)) + 2 * 8 + 8 + HLLC_FLOPS + 4
+
+
+def alg_flops_node(k):
+    return 2 * 4 + 4 + 1 + 3 + 2 + 8 + 8 + 2 * (4 * 2 * (k + 1)) + 2 + 2 * 16 + 3 * 4
+
+
+def fp64_peak_tflops(sm_mhz):
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return nsm * FP64_FLOP_PER_SM_CLK * sm_mhz * 1e6 / 1e12, nsm
+
+
+def kernel_bandwidths(w, preset, hbm_peak, peak_note, flush, U0):
+    """Live CUDA-event times of the FP32 preconditioner kernels and the CGS2
+    passes on this workload (L2 flushed before every timed launch) with their
+    algorithmic bytes per launch and the fraction of the HBM peak."""
+    import torch
+    n1 = w.k + 1
+    cells = w.n_el * n1 * n1            # finest FV level: one cell per DG node
+    nodes = cells
+    ctx = make_context(w, 32, **preset)
+    y = torch.randn(ctx.N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+
+    def avg(which, reps=6):
+        a, b = [], []
+        ctx.time_operator(which, U0, y, 1)   # warm
+        for _ in range(reps):
+            flush.add_(1.0)
+            torch.cuda.synchronize()
+            m0, m1 = ctx.time_operator(which, U0, y, 1)
+            a.append(m0)
+            b.append(m1)
+        return statistics.median(a), statistics.median(b)
+
+    def entry(ms, nbytes, what):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": ms, "bytes": nbytes, "gbs": gbs, "frac": gbs / hbm_peak, "algorithmic_bytes": what}
+
+    fv_s, fv_d = avg(3)
+    dg_f, dg_v = avg(2)
+    gs1, gs23 = avg(4)
+    out = {
+        "peak_gbs": hbm_peak, "peak": peak_note,
+        "fv_smooth_fp32_finest": entry(fv_s, 68 * cells, "read u, x, b (16 B each) and dtau (4 B), write x (16 B) per cell"),
+        "fv_defect_restrict_fp32_finest": entry(fv_d, 56 * cells, "read u, x, b per cell, write b_c and x_c (4 B per fine cell)"),
+        "dg_tangent_fp32": entry(dg_f + dg_v, 64 * nodes, "read U, z, r (16 B each), write the defect (16 B) per node"),
+        "cgs2_nv8": entry(gs1 + gs23, (20 * 8 + 44) * ctx.N, "(20 NV + 44) B per element: V32 and w, then V, w in and out twice"),
+        "cgs2_pass1_fp32": entry(gs1, (4 * 8 + 8) * ctx.N, "V32 (4 NV B) and w (8 B) per element"),
+    }
+    ctx.close()
+    return out
+
+
+def run_ensemble(n, steps, warmup, threads, hbm_peak):
     """64-member uneven ensemble (Q1..Q4, 40x20 .. 320x160), one batched SDIRK2 step
     per timed iteration, FP32 preconditioner; returns a dict for the JSON line."""
     import torch
@@ -205,14 +319,17 @@ def run_ensemble(n, steps, warmup, threads=16):
     torch.cuda.synchronize()
     t = 0.0
     its = []
+    status = []
+    n0 = P.jfnk.launch_count()
     for _ in range(steps):
         t0 = time.perf_counter()
         status, stats = batch.jfnk_batch_step(Us, dts, sch, raise_on_error=False)
         torch.cuda.synchronize()
         t += time.perf_counter() - t0
         its.append(sum(s.gmres_its for s in stats))
+    launches = (P.jfnk.launch_count() - n0) / steps
     dof = sum(m.n_unknowns for m in members)
-    grouped = time_grouped_residual(batch, ctxs, Us, dof)
+    grouped = time_grouped_residual(batch, ctxs, Us, dof, hbm_peak)
     batch.close()
     for c in ctxs:
         c.close()
@@ -222,14 +339,17 @@ def run_ensemble(n, steps, warmup, threads=16):
             "ensemble_steps_per_s": steps / t,
             "member_steps_per_s": n * steps / t, "dof_per_s": dof * steps / t,
             "ms_per_ensemble_step": 1e3 * t / steps, "failed_members": sum(1 for x in status if x != 0),
-            "gmres_its_per_ensemble_step": sum(its) / len(its), "precond": "fp32",
+            "gmres_its_per_ensemble_step": sum(its) / len(its), "launches_per_ensemble_step": launches,
+            "precond": "fp32", "dt": "10x acoustic CFL per member",
             "timing": f"wall clock of jfnk_batch_step (host-driven members on {threads} threads / streams)"}
 
 
-def time_grouped_residual(batch, ctxs, Us, dof, reps=10):
+def time_grouped_residual(batch, ctxs, Us, dof, hbm_peak, reps=10):
     """FP64 residual of every member: one face + one volume launch per (order,
     viscous) group (jfnk_batch_dg_residual) against one launch pair per member,
-    both on one stream, CUDA events."""
+    both on one stream, CUDA events.  The 64 members' states (470 MB) exceed
+    the L2, so the residual's algorithmic 16 B per unknown (read U', write f) is
+    also quoted as a fraction of the HBM peak."""
     import torch
     outs = [torch.empty(c.N, dtype=torch.float64, device="cuda") for c in ctxs]
     s = torch.cuda.current_stream()
@@ -253,69 +373,100 @@ def time_grouped_residual(batch, ctxs, Us, dof, reps=10):
     g = timed(lambda: batch.jfnk_batch_dg_residual(Us, outs))
     m = timed(per_member)
     del outs
+    gbs = 16.0 * dof / (g * 1e-3) / 1e9
     return {"ms_grouped": g, "ms_per_member_launches": m, "dof_per_s_grouped": dof / (g / 1e3),
             "dof_per_s_per_member": dof / (m / 1e3), "launches_grouped": 2 * len({(c.k, c.phys.mu != 0.0) for c in ctxs}),
-            "launches_per_member": 2 * len(ctxs)}
+            "launches_per_member": 2 * len(ctxs), "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+            "note": "16 B per unknown algorithmic; FP64-ALU bound, so far below the HBM roof"}
 
 
-def run_serving(seconds, rate=200.0):
+def run_serving(seconds, rate, overload_seconds):
     """Poisson arrivals of implicit-step requests on resident states: 16 ensemble
-    members (80 %) and 4 viscous density-current states (20 %), HBM budget of half
-    the total solver footprint (admission waits and evictions happen)."""
+    members (80 %) and 4 viscous density-current states (20 %).  The HBM budget
+    is what the device has free, so every state keeps its context (Krylov basis,
+    FV levels, graphs) resident across requests.  One run below capacity over the
+    full horizon, one short overload run at 200/s, and the same request list
+    stepped serially with plain FP64 contexts for comparison."""
     import numpy as np
     import torch
 
-    import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300 import jfnk
     from paper_2505_24504_gb300.serve import Server, StateSpec
     ens = synth.ensemble(16)
     visc = [synth.DENSITY_CURRENT_Q2_256x32] * 4
-    specs = {}
-    for sid, m in enumerate(ens + visc):
-        c = make_context(m, 32)
-        specs[sid] = StateSpec(grid=c.grid, k=c.k, phys=c.phys, opts=c.opts, dt=m.dt, scheme=m.scheme,
-                               U=initial_state(c, m))
+    work = ens + visc
+
+    def specs_for(prec):
+        specs = {}
+        for sid, m in enumerate(work):
+            c = make_context(m, prec)
+            specs[sid] = StateSpec(grid=c.grid, k=c.k, phys=c.phys, opts=c.opts, dt=m.dt, scheme=m.scheme,
+                                   U=initial_state(c, m))
+            c.close()
+        return specs
+
+    def requests(r, horizon, seed):
+        arr = synth.poisson_arrivals(r, horizon, seed=seed)
+        rng = np.random.Generator(np.random.Philox(seed + 4))
+        return [(float(t), int(rng.integers(0, 16)) if rng.random() < 0.8 else 16 + int(rng.integers(0, 4)))
+                for t in arr]
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    out = {"states": len(work), "hbm_budget_bytes": budget}
+    for name, r, horizon in (("below_capacity", rate, seconds), ("overload", 200.0, overload_seconds)):
+        if horizon <= 0:
+            continue
+        specs = specs_for(32)
+        reqs = requests(r, horizon, 7)
+        srv = Server(specs, hbm_budget=budget, workers=16)
+        rep = srv.run(reqs, timeout_s=max(600.0, 20 * horizon))
+        srv.close()
+        s = rep.summary()
+        s.update({"arrival_rate_per_s": r, "horizon_s": horizon,
+                  "basis_rebuilds": rep.contexts_created - len({q[1] for q in reqs}),
+                  "footprint_total_bytes": sum(sp.footprint for sp in specs.values())})
+        out[name] = s
+        del specs
+        torch.cuda.empty_cache()
+    # the same request list (first 200 requests of the below-capacity run) stepped
+    # one at a time with plain FP64 contexts, one context per state
+    reqs = requests(rate, seconds if seconds > 0 else 5.0, 7)[:200]
+    specs = specs_for(64)
+    ctxs = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, sid in reqs:
+        sp = specs[sid]
+        if sid not in ctxs:
+            ctxs[sid] = jfnk.Context(sp.grid, sp.k, sp.phys, sp.opts)
+        ctxs[sid].implicit_step(sp.U, sp.dt, scheme=sp.scheme)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    for c in ctxs.values():
         c.close()
-    total = sum(sp.footprint for sp in specs.values())
-    budget = max(total // 2, max(sp.footprint for sp in specs.values()))
-    arr = synth.poisson_arrivals(rate, seconds, seed=7)
-    rng = np.random.Generator(np.random.Philox(11))
-    reqs = []
-    for t in arr:
-        sid = int(rng.integers(0, 16)) if rng.random() < 0.8 else 16 + int(rng.integers(0, 4))
-        reqs.append((float(t), sid))
-    srv = Server(specs, hbm_budget=budget, workers=16)
-    rep = srv.run(reqs)
-    srv.close()
-    out = rep.summary()
-    out.update({"arrival_rate_per_s": rate, "horizon_s": seconds, "hbm_budget_bytes": budget,
-                "footprint_total_bytes": total, "states": len(specs)})
     del specs
     torch.cuda.empty_cache()
+    out["plain_fp64_serial"] = {"requests": len(reqs), "steps_per_s": len(reqs) / t, "wall_s": t,
+                                "note": "same requests, one at a time, FP64 preconditioner, contexts kept"}
+    if "below_capacity" in out:
+        out["served_vs_plain_fp64_serial"] = out["below_capacity"]["steps_per_s"] / out["plain_fp64_serial"]["steps_per_s"]
     return out
 
 
-def run_viscous(steps):
-    """Viscous density current (mu = 75 m^2/s, Q2 256x32, SDIRK2, dt = 1 s), FP32 preconditioner."""
-    return run_case(synth.DENSITY_CURRENT_Q2_256x32, steps)
-
-
-def run_inertia_gravity(steps):
-    """Inertia gravity wave (constant N, mean flow, periodic x; Q3 80x3, SDIRK2, dt = 25 s),
-    FP32 preconditioner, with the interpolation transfer and with the L2 projection."""
-    w = synth.INERTIA_GRAVITY_Q3_80x3
-    out = run_case(w, steps)
-    out["transfer_l2"] = {k: v for k, v in run_case(w, steps, transfer_l2=1).items() if k != "workload"}
-    return out
-
-
-def run_case(w, steps, **opt):
-    """Timed SDIRK2 steps of a secondary workload with tuned launch tiles."""
+def run_case(w, steps, preset=None, **opt):
+    """Timed SDIRK2 steps of a secondary workload (FP32 preconditioner)."""
     import torch
     from paper_2505_24504_gb300 import autotune
-    c0 = make_context(w, 32, **opt)
+    o = dict(preset or {})
+    o.update(opt)
+    c0 = make_context(w, 32, **o)
     U = initial_state(c0, w)
-    ctx, _ = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U)
-    c0.close()
+    if preset is None:
+        ctx, _ = autotune.tuned_context(c0.grid, c0.k, c0.phys, c0.opts, U)
+        c0.close()
+    else:
+        ctx = c0
     ctx.implicit_step(U, w.dt, scheme=w.scheme)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
@@ -331,30 +482,56 @@ def run_case(w, steps, **opt):
         its.append((st.newton_its, st.gmres_its))
     ctx.close()
     return {"workload": w.name, "steps_per_s": steps / (ms / 1e3), "dof_per_s": w.n_unknowns * steps / (ms / 1e3),
-            "ms_per_step": ms / steps, "newton_gmres_per_step": its[-1], "precond": "fp32"}
+            "ms_per_step": ms / steps, "newton_gmres_per_step": its[-1], "precond": "fp32",
+            "mg_key": o.get("mg_key", w.mg_key)}
 
 
 def run_mg_sweep():
-    """Iterations, operator calls and time per SDIRK2 step for the paper's key variants."""
-    import torch
+    """GMRES iterations, operator calls and time of one SDIRK2 (or BE) step for the
+    paper's schedule variants (Sec. 4.2): none, mg001111V, mg111111V, mg111111W and
+    the tuned key, on the three measured workloads (FP32 preconditioner)."""
     out = {}
-    for w in (synth.BUBBLE_Q3_160x80,):
+    cases = ((synth.BUBBLE_Q2_20x10, {}), (WORKLOAD, PRESET), (synth.DENSITY_CURRENT_Q2_256x32, {}))
+    for w, pre in cases:
         rows = {}
-        for key in ("", "mg001111V", "mg111111V", "mg111111W", "mg112211V"):
-            ctx = make_context(w, 32, mg_key=key, gmres_max=3000)
+        keys = ["", "mg001111V", "mg111111V", "mg111111W"]
+        if pre and pre["mg_key"] not in keys:
+            keys.append(pre["mg_key"])
+        for key in keys:
+            o = dict(pre)
+            o.update(mg_key=key, gmres_max=3000)
+            ctx = make_context(w, 32, **o)
             U = initial_state(ctx, w)
-            ctx.implicit_step(U, w.dt, scheme=w.scheme)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            s = torch.cuda.current_stream()
-            e0.record(s)
-            st = ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
-            e1.record(s)
-            e1.synchronize()
-            rows[key or "none"] = {"ms": e0.elapsed_time(e1), "status": st.status, "newton": st.newton_its,
-                                   "gmres": st.gmres_its, "dg_calls": st.dg_calls, "fv_calls": st.fv_calls}
+            ms, st = timed_once(ctx, U, w)
+            rows[key or "none"] = {"ms": ms, "status": st.status, "newton": st.newton_its, "gmres": st.gmres_its,
+                                   "dg_calls": st.dg_calls, "fv_calls": st.fv_calls}
             ctx.close()
+        out[w.name] = rows
+    return out
+
+
+def run_dt_trends():
+    """Newton / GMRES iterations per step against the time step, with the
+    preconditioner (mg111111V) and without, on the paper's three test cases at
+    reduced grids (Sec. 4.1-4.3: the preconditioner's iteration counts grow
+    slowly with dt, the unpreconditioned ones fast)."""
+    cases = (synth.scaled(synth.INERTIA_GRAVITY_Q3_80x3, 40, 3),
+             synth.scaled(synth.RISING_BUBBLE_Q3_40x80, 10, 20, fv_levels=4),
+             synth.scaled(synth.DENSITY_CURRENT_Q2_256x32, 64, 32, x1=12800.0, fv_levels=4))
+    out = {}
+    for w in cases:
+        rows = []
+        for f in (0.25, 0.5, 1.0, 2.0):
+            wd = synth.replace(w, dt_fixed=f * w.dt)
+            row = {"dt": wd.dt}
+            for key in ("mg111111V", ""):
+                ctx = make_context(wd, 32, mg_key=key, gmres_max=3000)
+                U = initial_state(ctx, wd)
+                st = ctx.implicit_step(U, wd.dt, scheme=1, raise_on_error=False)
+                row["precond" if key else "none"] = {"status": st.status, "newton": st.newton_its,
+                                                     "gmres": st.gmres_its}
+                ctx.close()
+            rows.append(row)
         out[w.name] = rows
     return out
 
@@ -375,64 +552,146 @@ def whole_job_rate(units_per_rank, ms_max, world):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(w, newton_per_step, gmres_per_step, budget_its=None, mg_key=None):
-    """The FP64 oracle as it stands on the host cores: one Newton iteration of
-    the first SDIRK2 stage (residual, linearisation, GMRES iterations equal to
-    the workload's mean per Newton iteration).  Returns (seconds per step
-    extrapolated by the step's Newton / GMRES counts, sample description)."""
-    import numpy as np
+# The FP64 oracle as it stands, timed on the host cores.
+def oracle_counts():
+    """The oracle's own iteration counts of one step of the workload (written by
+    tests/golden/make_oracle_step_counts.py, which runs the oracle's step)."""
+    with open(COUNTS_FILE) as fh:
+        rec = json.load(fh)[COUNTS_KEY]
+    want = presets.schedule(PRESET)
+    if rec["schedule"] != want:
+        raise RuntimeError(f"{COUNTS_FILE} was made with {rec['schedule']}, the preset runs {want}")
+    return rec
 
+
+class OracleSampler:
+    """Bounded samples of the oracle's implicit step on the workload: the Newton
+    residual G(U), the preconditioner's linearisation, and preconditioned FGMRES
+    iterations (each = Q^-1 v, the FD product, modified Gram-Schmidt), timed at
+    the step's first Newton iterate with the workload's schedule."""
+
+    def __init__(self, w, preset):
+        from oracle.dg import DG
+        from oracle.fv import Multigrid
+        from oracle.physics import Physics
+        from oracle.solver import SDIRK2_ALPHA
+        ph = Physics(cp=w.cp, cv=w.cv, g=w.g, p0=w.p0, theta0=w.theta0, mu=w.mu)
+        self.dg = DG(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, w.k, ph)
+        self.U = self.dg.init_state(w.theta_pert(self.dg.X, self.dg.Z))
+        self.adt = SDIRK2_ALPHA * w.dt
+        self.mg = Multigrid(self.dg, w.fv_levels, **presets.schedule(preset))
+        self.t_res, self.t_lin, self.t_it = [], [], []
+
+    def sample(self, gmres_its=2):
+        """One sample: residual, linearisation and `gmres_its` FGMRES iterations."""
+        from oracle.solver import fgmres
+        t0 = time.perf_counter()
+        G, fU = self.dg.G(self.U, self.adt, self.U)
+        t1 = time.perf_counter()
+        self.mg.linearize(self.U, self.adt, fU)
+        t2 = time.perf_counter()
+        A = lambda y: self.dg.jv(self.U, fU, y, self.adt)
+        _, done, _ = fgmres(A, -G, self.mg.apply, tol_abs=0.0, m=30, maxit=gmres_its)
+        t3 = time.perf_counter()
+        self.t_res.append(t1 - t0)
+        self.t_lin.append(t2 - t1)
+        self.t_it.append((t3 - t2) / max(done, 1))
+        return t3 - t0
+
+    def seconds_per_step(self, rec):
+        """Whole-step time from the sampled unit times and the oracle's counts:
+        per stage one initial residual, per Newton iteration one linearisation,
+        its GMRES iterations and one residual."""
+        r, l, it = (statistics.mean(x) for x in (self.t_res, self.t_lin, self.t_it))
+        return rec["stages"] * r + rec["newton_its"] * (l + r) + rec["gmres_its"] * it
+
+
+def _oracle_whole_step_seconds(w):
+    """One whole oracle step of a small workload, timed (runs in a child process
+    for the all-core figure)."""
     from oracle.dg import DG
     from oracle.fv import Multigrid
     from oracle.physics import Physics
-    from oracle.solver import fgmres, SDIRK2_ALPHA
+    from oracle.solver import implicit_step
     ph = Physics(cp=w.cp, cv=w.cv, g=w.g, p0=w.p0, theta0=w.theta0, mu=w.mu)
     dg = DG(w.nx, w.nz, w.x0, w.x1, w.z0, w.z1, w.k, ph)
-    U = dg.init_state(w.theta_pert(dg.X, dg.Z))
-    adt = SDIRK2_ALPHA * w.dt
-    its = budget_its or max(1, int(round(gmres_per_step / max(newton_per_step, 1))))
+    U0 = dg.init_state(w.theta_pert(dg.X, dg.Z))
     t0 = time.perf_counter()
-    G, fU = dg.G(U, adt, U)
-    mg = Multigrid(dg, w.fv_levels, mg_key or w.mg_key)
-    mg.linearize(U, adt, fU)
+    implicit_step(dg, U0, w.dt, scheme=w.scheme, tol=w.newton_tol, precond=Multigrid(dg, w.fv_levels, w.mg_key))
+    return time.perf_counter() - t0
+
+
+def _child_whole_step(_):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    return _oracle_whole_step_seconds(synth.BUBBLE_Q2_20x10)
+
+
+def cpu_baseline(w):
+    """The oracle on the host: a bounded sample of this workload's step on one
+    core scaled to steps/s by the oracle's own counts, plus one whole step of the
+    small warm-bubble workload on one core and on every core at once (independent
+    steps in `nproc` processes)."""
+    import multiprocessing as mp
+    rec = oracle_counts()
+    smp = OracleSampler(w, PRESET)
+    t0 = time.perf_counter()
+    smp.sample(gmres_its=2)
+    smp.sample(gmres_its=2)
+    sampled = time.perf_counter() - t0
+    sec = smp.seconds_per_step(rec)
+    one = _oracle_whole_step_seconds(synth.BUBBLE_Q2_20x10)
+    ncores = min(len(os.sched_getaffinity(0)), 64)
     t1 = time.perf_counter()
-    A = lambda y: dg.jv(U, fU, y, adt)
-    _, done, _ = fgmres(A, -G, mg.apply, tol_abs=0.0, m=30, maxit=its)
-    t2 = time.perf_counter()
-    t_newton = t1 - t0
-    t_it = (t2 - t1) / max(done, 1)
-    per_step = newton_per_step * t_newton + gmres_per_step * t_it
-    desc = (f"oracle (numpy FP64, 1 thread, {mg_key or w.mg_key}): 1 residual + linearisation + {done} "
-            f"preconditioned FGMRES iterations of workload 2's first Newton step, scaled to "
-            f"{newton_per_step} Newton / {gmres_per_step} GMRES iterations per SDIRK2 step")
-    return per_step, desc, t2 - t0
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        pool.map(_child_whole_step, range(ncores))
+    wall = time.perf_counter() - t1
+    return {"value": 1.0 / sec, "unit": "implicit steps/s", "cores": 1, "kind": "oracle",
+            "dof_per_s": w.n_unknowns / sec, "seconds_sampled": sampled,
+            "sample": (f"oracle (numpy FP64, 1 thread, {PRESET['mg_key']}): 2 samples of residual + "
+                       f"linearisation + 2 preconditioned FGMRES iterations at the first Newton iterate of "
+                       f"this workload, scaled to a whole SDIRK2 step by the oracle's own counts "
+                       f"({rec['newton_its']} Newton, {rec['gmres_its']} GMRES; tests/golden/oracle_step_counts.json)"),
+            "small_workload_whole_step": {"workload": synth.BUBBLE_Q2_20x10.name, "seconds_1_core": one,
+                                          "steps_per_s_1_core": 1.0 / one, "cores_all": ncores,
+                                          "steps_per_s_all_cores": ncores / wall,
+                                          "note": "independent steps, one process per core"}}
 
 
 def run_reference(args):
+    """The reference leg: the FP64 oracle on the host, each timed step one bounded
+    sample (residual, linearisation, 2 preconditioned FGMRES iterations) of this
+    workload's SDIRK2 step; `value` scales the sampled unit times to whole steps
+    with the oracle's own iteration counts."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     w = WORKLOAD
-    newton_per_step, gmres_per_step = 8, 96   # the workload's counts (GPU run, same algorithm)
-    per = []
+    rec = oracle_counts()
+    smp = OracleSampler(w, PRESET)
     for _ in range(args.warmup):
-        oracle_sample(w, newton_per_step, gmres_per_step, budget_its=1)
-    desc = ""
+        smp.sample()
+    smp.t_res, smp.t_lin, smp.t_it = [], [], []
+    per = []
     for _ in range(args.steps):
-        sec, desc, _ = oracle_sample(w, newton_per_step, gmres_per_step, budget_its=3)
-        per.append(sec)
-    ms_per_step = 1e3 * statistics.mean(per)
-    value = 1e3 / ms_per_step
+        per.append(smp.sample())
+    sec = smp.seconds_per_step(rec)
+    value = 1.0 / sec
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    desc = (f"oracle (numpy FP64, 1 thread, {PRESET['mg_key']}): each timed step = residual + linearisation + "
+            f"2 preconditioned FGMRES iterations at the first Newton iterate; value = whole SDIRK2 steps/s from "
+            f"the mean unit times and the oracle's own counts ({rec['newton_its']} Newton, {rec['gmres_its']} "
+            f"GMRES per step, tests/golden/oracle_step_counts.json)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "implicit steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(per), "ms_per_implicit_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "dof_per_s": value * w.n_unknowns,
-        "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "mg_key": w.mg_key},
-        "cpu_baseline": {"value": value, "unit": "implicit steps/s", "cores": 1, "kind": "oracle",
-                         "sample": desc.replace("3 preconditioned", "3 preconditioned")},
+        "config": config_of(w, world),
+        "cpu_baseline": {"value": value, "unit": "implicit steps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "implicit steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "unit_seconds": {"residual": statistics.mean(smp.t_res), "linearise": statistics.mean(smp.t_lin),
+                         "fgmres_iteration": statistics.mean(smp.t_it)},
     }
     print(json.dumps(line))
 
@@ -459,30 +718,35 @@ def main():
     torch.cuda.set_device(local)
     w = WORKLOAD
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    preset = dict(PRESET)
+    if args.schedule:
+        preset["mg_key"] = args.schedule
     if args.profile_dg:
-        c64 = make_context(w, 64)
+        c64 = make_context(w, 64, **preset)
         U0 = initial_state(c64, w)
         y = torch.randn(c64.N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
         fm, vm = c64.time_operator(1, U0, y, args.profile_dg)
         print(json.dumps({"profile": "FP64 FD product", "face_ms": fm, "volume_ms": vm, "reps": args.profile_dg}))
         return
 
-    # ---- the product form: FP32 preconditioner, launch shapes from the autotuner --
-    from paper_2505_24504_gb300 import autotune
-    c0 = make_context(w, 32)
+    # ---- the product form: FP32 preconditioner ---------------------------------
+    c0 = make_context(w, 32, **preset)
     U = initial_state(c0, w)
     U0 = U.clone()
-    c0.close()
-    # preconditioner schedule (smoothing counts / cycle) and launch shapes from the autotuner
-    if args.schedule:
-        ctx, tiles = autotune.tuned_context(*make_args(w, 32, mg_key=args.schedule), U0)
-        tiles = dict(tiles, mg_key=args.schedule, sigma_fv=1.0, sigma_dg=1.0, schedule_trials_ms={})
-    else:
+    tuning = {"source": "presets.WARM_BUBBLE_Q3_160x80 (recorded autotuner choice)"}
+    if args.tune:
+        from paper_2505_24504_gb300 import autotune
+        c0.close()
         ctx, tiles = autotune.tuned_schedule_context(*make_args(w, 32), U0, w.dt, w.scheme)
-    n0 = P.jfnk.launch_count()
+        preset = {k: tiles[k] for k in ("mg_key", "sigma_fv", "sigma_dg", "tile_faces", "tile_volume", "tile_fv",
+                                        "fv_split_cells")}
+        tuning = {"source": "autotuner run in this process", "chosen": preset,
+                  "schedule_trials_ms": tiles.get("schedule_trials_ms")}
+    else:
+        ctx = c0
     with Clocks(local) as clk:
         ms, stats = time_steps(ctx, U, w, args.steps, args.warmup, dist, flush)
-    launches = P.jfnk.launch_count() - n0
+    launches = time_steps.launches
     clocks = clk.summary()
     ms = max_over_ranks(ms, dist)
     value = whole_job_rate(args.steps, ms, world)
@@ -521,25 +785,33 @@ def main():
     e2e = world * ne2e / (e2e_ms / 1e3)
 
     # ---- roofline of the dominant kernel (FP64 FD product, face kernel) --------
-    y = torch.randn(ctx.N, dtype=torch.float64, device="cuda")
-    ctx64 = make_context(w, 64)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+    hbm_note = "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "of fallback"
+    sm_mhz = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak64, nsm = fp64_peak_tflops(sm_mhz)
+    y = torch.randn(ctx.N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    ctx64 = make_context(w, 64, **preset)
     fm, vm = ctx64.time_operator(1, U0, y, 20)
     n1 = w.k + 1
     face_pts = (w.nz * (w.nx + 1) + (w.nz + 1) * w.nx) * n1
     nodes = w.n_el * n1 * n1
-    ach = FLOPS_FACE_POINT * face_pts / (fm * 1e-3) / 1e12
-    ach_v = FLOPS_NODE * nodes / (vm * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
+    fl_face, fl_node = alg_flops_face_point(w.k), alg_flops_node(w.k)
+    ach = fl_face * face_pts / (fm * 1e-3) / 1e12
+    ach_v = fl_node * nodes / (vm * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "k_faces<D64> FP64 FD product (face points)", "achieved": ach,
-            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC_FACE,
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "launch_ms": fm, "flop_per_launch": FLOPS_FACE_POINT * face_pts,
-            "volume_kernel": {"achieved": ach_v, "frac": ach_v / peak, "launch_ms": vm,
-                              "flop_per_launch": FLOPS_NODE * nodes}}
+            "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64, "traffic": TRAFFIC_FACE,
+            "peak_source": (f"derived, not measured: {nsm} SMs (device properties) x {FP64_FLOP_PER_SM_CLK:g} FP64 "
+                            f"flop/SM/clock x {sm_mhz:g} MHz"),
+            "launch_ms": fm, "flop_per_unit": fl_face, "units_per_launch": face_pts,
+            "flop_counting": "algorithmic, from the formulas (bench.py alg_flops_face_point); ncu counts 250 "
+                             "executed FP64-pipe flops per face point (IEEE divide/sqrt sequences, table power)",
+            "volume_kernel": {"achieved": ach_v, "frac": ach_v / peak64, "launch_ms": vm,
+                              "flop_per_unit": fl_node, "units_per_launch": nodes},
+            "hbm": kernel_bandwidths(w, preset, hbm_peak, hbm_note, flush, U0)}
 
     # ---- phase breakdown of one more step (events at the solver's own syncs) ----
-    ctx_p, _ = autotune.tuned_context(*make_args(w, 32, profile=1, mg_key=tiles["mg_key"],
-                                                 sigma_fv=tiles["sigma_fv"], sigma_dg=tiles["sigma_dg"]), U0)
+    ctx_p = make_context(w, 32, profile=1, **preset)
     Up = U0.clone()
     ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
     stp = ctx_p.implicit_step(Up, w.dt, scheme=w.scheme)
@@ -549,8 +821,7 @@ def main():
     ctx_p.close()
 
     # ---- BF16 numerics on the coarsest FV level (precond_prec = 16), same schedule ----
-    c16, _ = autotune.tuned_context(*make_args(w, 16, mg_key=tiles["mg_key"], sigma_fv=tiles["sigma_fv"],
-                                               sigma_dg=tiles["sigma_dg"]), U0)
+    c16 = make_context(w, 16, **preset)
     U16 = U0.clone()
     U32 = U0.clone()
     ms16, st16 = time_steps(c16, U16, w, 2, 1, None, flush)
@@ -573,18 +844,17 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "dof_per_s": value * w.n_unknowns,
+        "precision": "FP64 residual, FD products and Arnoldi; FP32 preconditioner",
         "plain_fp64": {"value": plain, "unit": "implicit steps/s", "dof_per_s": plain * w.n_unknowns,
-                       "ms_per_step": ms64 / kp},
+                       "ms_per_step": ms64 / kp,
+                       "iterations_per_step": {"newton": sum(x["newton_its"] for x in st64) / kp,
+                                               "gmres": sum(x["gmres_its"] for x in st64) / kp}},
         "iterations_per_step": {"newton": newton, "gmres": gmres},
         "phases_per_step": phases,
         "bf16_coarsest": bf16,
-        "config": {"workload": w.name, "unknowns": w.n_unknowns, "scheme": "SDIRK2", "dt": w.dt,
-                   "newton_tol": w.newton_tol, "mg_key": tiles["mg_key"], "fv_levels": w.fv_levels,
-                   "precond": "fp32", "l2": "flushed between timed steps (512 MiB write)",
-                   "tiles": {k: tiles.get(k) for k in ("tile_faces", "tile_volume", "tile_fv", "fv_split_cells")},
-                   "mg_key_tuned": tiles["mg_key"], "sigma_fv": tiles["sigma_fv"], "sigma_dg": tiles["sigma_dg"],
-                   "schedule_trials_ms": tiles["schedule_trials_ms"],
-                   "parallelism": f"replicas x{world}"},
+        "config": config_of(w, world, preset),
+        "tuning": dict(tuning, tiles={k: preset.get(k) for k in ("tile_faces", "tile_volume", "tile_fv",
+                                                                 "fv_split_cells")}),
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e, "unit": "implicit steps/s", "h2d_bytes_per_step": 8 * ctx.N,
@@ -594,28 +864,27 @@ def main():
     }
     ctx.close()
     ctx64.close()
-    if args.viscous_steps > 0:
-        line["viscous"] = run_viscous(args.viscous_steps)
-    if args.igw_steps > 0:
-        line["inertia_gravity"] = run_inertia_gravity(args.igw_steps)
-    if args.mg_sweep:
+    if args.secondary_steps > 0:
+        line["viscous"] = run_case(synth.DENSITY_CURRENT_Q2_256x32, args.secondary_steps)
+        igw = synth.INERTIA_GRAVITY_Q3_80x3
+        line["inertia_gravity"] = run_case(igw, args.secondary_steps)
+        line["inertia_gravity"]["transfer_l2"] = {k: v for k, v in run_case(igw, args.secondary_steps,
+                                                                            transfer_l2=1).items() if k != "workload"}
+        line["rising_bubble"] = run_case(synth.RISING_BUBBLE_Q3_40x80, args.secondary_steps)
+    if not args.no_sweep:
         line["mg_sweep"] = run_mg_sweep()
+        line["dt_trends"] = run_dt_trends()
     if args.ensemble > 0:
-        line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1, args.ensemble_threads)
-    if args.serve_seconds > 0:
-        line["serving"] = run_serving(args.serve_seconds)
+        line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1, args.ensemble_threads, hbm_peak)
+    if args.serve_seconds > 0 or args.overload_seconds > 0:
+        line["serving"] = run_serving(args.serve_seconds, args.serve_rate, args.overload_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        per_step, desc, _ = oracle_sample(w, int(round(newton)), int(round(gmres)), mg_key=tiles["mg_key"])
-        line["cpu_baseline"] = {"value": 1.0 / per_step, "unit": "implicit steps/s", "cores": 1,
-                                "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
-
-FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (a DFMA-chain probe measured 1.19)
 
 if __name__ == "__main__":
     main()

@@ -40,7 +40,7 @@ extern "C" {
 #define JFNK_ENOMEM (-2)    /* device allocation failed (nothing leaked) */
 #define JFNK_ECUDA (-3)     /* a CUDA call failed */
 #define JFNK_ENOTCONV (-4)  /* Newton or GMRES hit its iteration cap; state restored */
-#define JFNK_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define JFNK_ETIMEOUT (-5)  /* the step's time budget (opts.time_budget_ms) ran out; state restored */
 #define JFNK_ENAN (-6)      /* a norm became non-finite; state restored */
 
 typedef struct jfnk_ctx jfnk_ctx;
@@ -96,7 +96,17 @@ typedef struct {
  *               it; 0: launch the kernels one by one.  Same results either way.
  *  tile_*, fv_split_cells  launch shapes (results do not depend on them, except
  *               fv_split_cells, which changes the summation order of the FV
- *               operator at rounding level); jfnk_autotune picks them by timing. */
+ *               operator at rounding level); jfnk_autotune picks them by timing.
+ *  precond_fd_eps  numerator c of the step eps = c / |x| of the finite-difference
+ *               products inside the FP64 preconditioner (FV levels and DG
+ *               smoothing); 0 (default): c = sqrt(eps_mach) as in Sec. 3.1.  A
+ *               larger c keeps eps x_i many ulps above the state's rounding, so
+ *               that two implementations of Q^-1 can be compared tightly.  The
+ *               outer Jacobian-free product of GMRES always uses Sec. 3.1's eps.
+ *  time_budget_ms  wall-clock budget of one implicit_step in milliseconds, checked
+ *               on the host after every Arnoldi step and Newton iteration; when it
+ *               runs out the step returns JFNK_ETIMEOUT with U restored to U^n.
+ *               0 (default): no budget. */
 typedef struct {
     double newton_tol;
     int newton_max;
@@ -116,6 +126,8 @@ typedef struct {
     int fv_split_cells;  /* FV levels with fewer cells than this run four lanes per cell (one
                             per face), larger levels the face-once tile kernel (0: 65536) */
     int profile;         /* 1: time the phases of implicit_step with CUDA events (jfnk_stats) */
+    double precond_fd_eps;
+    double time_budget_ms;
 } jfnk_opts;
 
 /* Counters of one implicit_step (Sec. 4.2 counts linear iterations and
@@ -194,8 +206,8 @@ int mg_precondition(jfnk_ctx *ctx, const double *U_dev, double alpha_dt, const d
  * scheme 0 backward Euler, 1 SDIRK2 of Ellsiepen (Sec. 2.2, alpha = 1 -
  * sqrt(2)/2).  Each stage solves eq. (newton) by inexact Newton from
  * U_s^0 = Ubar_s with right-preconditioned flexible GMRES and Eisenstat-
- * Walker tolerances (Sec. 3.1).  On JFNK_ENOTCONV or JFNK_ENAN the state is
- * restored to U^n.  stats may be NULL.  Synchronises the stream. */
+ * Walker tolerances (Sec. 3.1).  On JFNK_ENOTCONV, JFNK_ENAN or JFNK_ETIMEOUT
+ * the state is restored to U^n.  stats may be NULL.  Synchronises the stream. */
 int implicit_step(jfnk_ctx *ctx, double *U_dev, double dt, int scheme, jfnk_stats *stats,
                   void *stream);
 
@@ -217,7 +229,9 @@ int jfnk_norm2(jfnk_ctx *ctx, const double *x_dev, size_t n, double *out_dev, vo
  * JFNK_EINVAL before anything is launched.
  * The first call on a device looks up that device's address of the array
  * (cudaGetSymbolAddress, with the device current): make that first call before
- * capturing a stream.  Every call uses the same array, so calls that overlap on
+ * capturing a stream.  The address stays cached for the life of the process,
+ * so a device that is reset (cudaDeviceReset) afterwards must not be given to
+ * this call again in that process.  Every call uses the same array, so calls that overlap on
  * the GPU (on different streams, or from several host threads) race; order
  * them on one stream.  Each call overwrites every partial it later reads, so
  * nothing needs clearing between calls. */
@@ -281,7 +295,13 @@ int jfnk_eos_pressure(jfnk_ctx *ctx, const double *E_dev, size_t n, double *p_de
  * solver's Arnoldi steps use: face traces of U stored by the residual at U,
  * plus eps times the traces of y), 2 = FP32 tangent product (contexts with
  * precond_prec < 64).  Runs `reps` evaluations;
- * ms[0], ms[1] receive the mean duration of the face and the volume kernel. */
+ * ms[0], ms[1] receive the mean duration of the face and the volume kernel.
+ * which 3 (FP32 contexts with a preconditioner): the finest FV level's two
+ * FP32 kernels linearised at U with alpha dt = 1 and x = b = y, ms[0] one
+ * pseudo-time smoothing step, ms[1] the defect fused with the restriction;
+ * which 4: the three Gram-Schmidt launches against 8 basis vectors (y unused),
+ * ms[0] the FP32 first pass, ms[1] the second and third passes.  Modes 3 and 4
+ * overwrite the context's preconditioner and Krylov workspace. */
 int jfnk_time_operator(jfnk_ctx *ctx, int which, const double *U_dev, const double *y_dev, int reps,
                        double *ms_host, void *stream);
 

@@ -83,6 +83,7 @@ class NewtonStats:
     def __init__(self):
         self.newton_its = 0
         self.gmres_its = 0
+        self.gmres_per_newton = []   # GMRES iterations of each Newton iteration, in order
         self.res_history = []
         self.converged = True
 
@@ -126,6 +127,7 @@ def newton(dg, Ubar_s, alpha_dt, tol, precond=None, ew_gamma=0.1, ew_alpha=1.0,
         A = lambda y, U=U, fU=fU: dg.jv(U, fU, y, alpha_dt)
         dU, its, _ = fgmres(A, -G, M, tol_abs=eta * nk, m=gmres_m, maxit=gmres_max)
         st.gmres_its += its
+        st.gmres_per_newton.append(its)
         st.newton_its += 1
         U = U + dU
         G, fU = dg.G(U, alpha_dt, Ubar_s)

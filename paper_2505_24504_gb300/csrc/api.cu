@@ -205,7 +205,7 @@ const char *jfnk_strerror(int code) {
         case JFNK_ENOMEM: return "device allocation failed";
         case JFNK_ECUDA: return "CUDA error";
         case JFNK_ENOTCONV: return "Newton or GMRES did not converge within the iteration caps";
-        case JFNK_ETIMEOUT: return "bounded device wait ran out";
+        case JFNK_ETIMEOUT: return "the implicit step's time budget ran out";
         case JFNK_ENAN: return "non-finite norm";
     }
     return "unknown error";
@@ -258,6 +258,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     else jfnk_default_opts(&o);
     if (o.gmres_restart < 1 || o.gmres_restart > 64 || o.gmres_max < 1 || o.newton_max < 1) return JFNK_EINVAL;
     if (o.precond_prec != 64 && o.precond_prec != 32 && o.precond_prec != 16) return JFNK_EINVAL;
+    if (!(o.precond_fd_eps >= 0.0) || !(o.time_budget_ms >= 0.0)) return JFNK_EINVAL;
     if (o.fv_levels < 1) o.fv_levels = 1;
     if (o.tile_faces == 0) o.tile_faces = 128;
     if (o.tile_volume == 0) o.tile_volume = 2;
@@ -308,6 +309,23 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     c->pc.R_over_p0f = (float)c->pc.R_over_p0;
     c->pc.muf = (float)c->pc.mu;
     jf_build_tables(k, &c->tab);
+    // Set-up copies and kernels run on a private stream that only this call
+    // waits for: creating a context never drains other threads' streams.
+    struct SetupStream {
+        cudaStream_t s = nullptr;
+        ~SetupStream() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } setup;
+    if (cudaStreamCreateWithFlags(&setup.s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_unlocked(c);
+        return JFNK_ECUDA;
+    }
+    const cudaStream_t ss = setup.s;
+    auto h2d = [ss](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ss) == cudaSuccess;
+    };
 
 #define A_(p, bytes)                         \
     do {                                     \
@@ -333,10 +351,13 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     A_(c->hbz, 8 * 4 * nf);
     A_(c->prow, 8 * nrow);
     A_(c->theta_row, 8 * nrow);
+    // host copies of the background (node rows and horizontal faces), kept for
+    // the FP32 copies below
+    std::vector<double> ub(4 * nrow), dub(4 * nrow), uh(4 * nf), duh(4 * nf);
+    PowTab pt;
     {
-        PowTab pt;
         jf_build_powtab(c->pc.gamma, &pt);
-        std::vector<double> ub(4 * nrow), dub(4 * nrow), uh(4 * nf), duh(4 * nf), pr(nrow), tr(nrow);
+        std::vector<double> pr(nrow), tr(nrow);
         for (int ez = 0; ez < g->nz; ++ez)
             for (int b = 0; b < n1; ++b) {
                 const int J = ez * n1 + b;
@@ -358,13 +379,12 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
                 duh[v * nf + j] = dU[v];
             }
         }
-        if (cudaMemcpy(c->powtab, &pt, sizeof(pt), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->ubv, ub.data(), 8 * ub.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->dubv, dub.data(), 8 * dub.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->ubh, uh.data(), 8 * uh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->dubh, duh.data(), 8 * duh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->prow, pr.data(), 8 * pr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->theta_row, tr.data(), 8 * tr.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        // pageable sources: each copy has read its source when it returns
+        if (!h2d(c->powtab, &pt, sizeof(pt)) || !h2d(c->ubv, ub.data(), 8 * ub.size()) ||
+            !h2d(c->dubv, dub.data(), 8 * dub.size()) || !h2d(c->ubh, uh.data(), 8 * uh.size()) ||
+            !h2d(c->dubh, duh.data(), 8 * duh.size()) || !h2d(c->prow, pr.data(), 8 * pr.size()) ||
+            !h2d(c->theta_row, tr.data(), 8 * tr.size())) {
+            cudaGetLastError();
             destroy_unlocked(c);
             return JFNK_ECUDA;
         }
@@ -417,27 +437,11 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
         A_(c->dubvf, 4 * 4 * nrow);
         A_(c->ubhf, 4 * 4 * nf);
         A_(c->dubhf, 4 * 4 * nf);
-        std::vector<float> a1(4 * nrow), a2(4 * nrow), a3(4 * nf), a4(4 * nf);
-        std::vector<double> b1(4 * nrow), b2(4 * nrow), b3(4 * nf), b4(4 * nf);
-        if (cudaMemcpy(b1.data(), c->ubv, 8 * b1.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(b2.data(), c->dubv, 8 * b2.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(b3.data(), c->ubh, 8 * b3.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(b4.data(), c->dubh, 8 * b4.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            destroy_unlocked(c);
-            return JFNK_ECUDA;
-        }
-        for (size_t i = 0; i < b1.size(); ++i) {
-            a1[i] = (float)b1[i];
-            a2[i] = (float)b2[i];
-        }
-        for (size_t i = 0; i < b3.size(); ++i) {
-            a3[i] = (float)b3[i];
-            a4[i] = (float)b4[i];
-        }
-        if (cudaMemcpy(c->ubvf, a1.data(), 4 * a1.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->dubvf, a2.data(), 4 * a2.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->ubhf, a3.data(), 4 * a3.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->dubhf, a4.data(), 4 * a4.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        std::vector<float> a1(ub.begin(), ub.end()), a2(dub.begin(), dub.end());
+        std::vector<float> a3(uh.begin(), uh.end()), a4(duh.begin(), duh.end());
+        if (!h2d(c->ubvf, a1.data(), 4 * a1.size()) || !h2d(c->dubvf, a2.data(), 4 * a2.size()) ||
+            !h2d(c->ubhf, a3.data(), 4 * a3.size()) || !h2d(c->dubhf, a4.data(), 4 * a4.size())) {
+            cudaGetLastError();
             destroy_unlocked(c);
             return JFNK_ECUDA;
         }
@@ -472,8 +476,8 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
             for (int v = 0; v < 4; ++v) ub[v * NZ[l] + J] = U[v];
         }
         std::vector<float> ubf(ub.begin(), ub.end());
-        if (cudaMemcpy(L.ub, ub.data(), 8 * ub.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(L.ubf, ubf.data(), 4 * ubf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (!h2d(L.ub, ub.data(), 8 * ub.size()) || !h2d(L.ubf, ubf.data(), 4 * ubf.size())) {
+            cudaGetLastError();
             destroy_unlocked(c);
             return JFNK_ECUDA;
         }
@@ -508,12 +512,18 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
         c->h_pinned = (double *)h;
     }
 #undef A_
-    if (cudaMemset(c->scal, 0, 8 * (size_t)S_COUNT) != cudaSuccess || cudaMemset(c->ticket, 0, 256) != cudaSuccess) {
+    if (cudaMemsetAsync(c->scal, 0, 8 * (size_t)S_COUNT, ss) != cudaSuccess ||
+        cudaMemsetAsync(c->ticket, 0, 256, ss) != cudaSuccess) {
+        cudaGetLastError();
         destroy_unlocked(c);
         return JFNK_ECUDA;
     }
-    rc = dg_setup_background(c);
-    if (!rc) rc = fv_setup_background(c);
+    rc = dg_setup_background(c, ss);
+    if (!rc) rc = fv_setup_background(c, ss);
+    if (!rc && cudaStreamSynchronize(ss) != cudaSuccess) {
+        cudaGetLastError();
+        rc = JFNK_ECUDA;
+    }
     if (rc) {
         destroy_unlocked(c);
         return rc;
@@ -624,9 +634,11 @@ int jfnk_fv_levels(const jfnk_ctx *c) { return c ? c->nlev : 0; }
 
 int jfnk_time_operator(jfnk_ctx *c, int which, const double *U, const double *y, int reps, double *ms,
                        void *stream) {
-    if (!c || !U || !ms || reps < 1 || which < 0 || which > 2 || (which > 0 && !y)) return JFNK_EINVAL;
-    if (which == 2 && c->prec == 64) return JFNK_EINVAL;
+    if (!c || !U || !ms || reps < 1 || which < 0 || which > 4 || (which > 0 && which != 4 && !y)) return JFNK_EINVAL;
+    if ((which == 2 || which == 3) && c->prec == 64) return JFNK_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (which == 3) return mg_time_fv_level0(c, U, y, reps, ms, s);
+    if (which == 4) return blas_time_cgs2(c, reps, ms, s);
     for (int i = 0; i < 3; ++i) JF_CK(cudaEventCreate(&c->tev[i]));
     int rc = JFNK_OK;
     DGArgs a = {};

@@ -64,17 +64,18 @@ __device__ __forceinline__ double sum_partials(const double *part, int nb) {
     return block_sum(acc);
 }
 
-__device__ __forceinline__ double finish_op(double acc, int op) {
+// cnum: numerator of the eps ops (sqrt(2^-52) for RED_EPS, sqrt(2^-23) for
+// RED_EPS32, the preconditioner's choice for RED_EPSP)
+__device__ __forceinline__ double finish_op(double acc, int op, double cnum = 1.4901161193847656e-08) {
     if (op == RED_SQRT) return sqrt(acc);
-    if (op == RED_EPS) return acc > 0.0 ? 1.4901161193847656e-08 / sqrt(acc) : 0.0;
-    if (op == RED_EPS32) return acc > 0.0 ? 3.4526698300124393e-04 / sqrt(acc) : 0.0;
+    if (op == RED_EPS || op == RED_EPS32 || op == RED_EPSP) return acc > 0.0 ? cnum / sqrt(acc) : 0.0;
     return acc;
 }
 
 // x . y (op applied) in one launch
 template <class S>
 __global__ void __launch_bounds__(RB) k_dot1(const S *x, const S *y, size_t n, double *part, unsigned *ticket,
-                                             double *out, int op) {
+                                             double *out, int op, double cnum) {
     jf_pdl_enter();
     double acc = 0.0, acc2 = 0.0;
     const size_t stride = (size_t)gridDim.x * RB;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(RB) k_dot1(const S *x, const S *y, size_t n, d
     if (!last_block(ticket)) return;
     const double t = sum_partials(part, gridDim.x);
     if (threadIdx.x == 0) {
-        *out = finish_op(t, op);
+        *out = finish_op(t, op, cnum);
         *ticket = 0u;
     }
 }
@@ -620,16 +621,24 @@ inline int nblocks_red(jfnk_ctx *c, size_t n) {
 
 }  // namespace
 
+static double eps_numerator(const jfnk_ctx *c, int op) {
+    if (op == RED_EPS32) return 3.4526698300124393e-04;   // sqrt(2^-23)
+    if (op == RED_EPSP && c->opts.precond_fd_eps > 0.0) return c->opts.precond_fd_eps;
+    return 1.4901161193847656e-08;                         // sqrt(2^-52)
+}
+
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    jf_launch(k_dot1<double>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op); jf_launched();
+    jf_launch(k_dot1<double>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op, eps_numerator(c, op));
+    jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
 
 int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out, int op, cudaStream_t s) {
     const int nb = nblocks_red(c, n);
-    jf_launch(k_dot1<float>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op); jf_launched();
+    jf_launch(k_dot1<float>, nb, RB, 0, s, x, y, n, c->partial, c->ticket, out, op, eps_numerator(c, op));
+    jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -683,6 +692,49 @@ int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv
     }
     JF_CK(cudaGetLastError());
     return JFNK_OK;
+}
+
+// Diagnostic timing of the three CGS2 launches with 8 basis vectors on the
+// context's basis buffers (filled with a fixed byte pattern, so the second pass
+// is always taken, as on the solver's problems).  ms[0]: pass 1 (FP32 multi-dot),
+// ms[1]: passes 2 and 3 (update + dot, update + normalisation); means over reps.
+int blas_time_cgs2(jfnk_ctx *c, int reps, double *ms, cudaStream_t s) {
+    constexpr int NV = 8;
+    const size_t N = c->N;
+    if (c->opts.gmres_restart < NV || (N & 1)) return JFNK_EINVAL;
+    JF_CK(cudaMemsetAsync(c->V, 0x3f, 8 * N * (NV + 1), s));
+    JF_CK(cudaMemsetAsync(c->V32, 0x3f, 4 * N * (NV + 1), s));
+    double *w = c->V + (size_t)NV * N;
+    cudaEvent_t e[3];
+    for (auto &x : e) JF_CK(cudaEventCreate(&x));
+    const size_t n2 = N / 2;
+    const int g1 = one_wave(c, k_gs_dot32<NV>, n2), g2 = one_wave(c, k_gs_update_dot<NV>, n2),
+              g3 = one_wave(c, k_gs_update_scale<NV>, n2);
+    double t0 = 0.0, t1 = 0.0;
+    int rc = JFNK_OK;
+    for (int r = 0; r < reps && rc == JFNK_OK; ++r) {
+        JF_CK(cudaMemsetAsync(w, 0x3f, 8 * N, s));
+        cudaEventRecord(e[0], s);
+        jf_launch(k_gs_dot32<NV>, g1, RB, 0, s, (const float *)c->V32, N, (const double *)w, n2, c->partial,
+                  c->ticket, c->scal + S_H);
+        cudaEventRecord(e[1], s);
+        jf_launch(k_gs_update_dot<NV>, g2, RB, 0, s, (const double *)c->V, N, w, n2, (const double *)(c->scal + S_H),
+                  c->partial, c->ticket, c->scal + S_H2, c->scal + S_W1, c->scal + S_NORM, c->scal + S_FLAG);
+        jf_launch(k_gs_update_scale<NV>, g3, RB, 0, s, (const double *)c->V, N, w, c->V32 + (size_t)NV * N, n2,
+                  (const double *)(c->scal + S_H2), (const double *)(c->scal + S_FLAG), c->scal + S_INV);
+        jf_launched(3);
+        cudaEventRecord(e[2], s);
+        if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = JFNK_ECUDA;
+        float m0 = 0.f, m1 = 0.f;
+        cudaEventElapsedTime(&m0, e[0], e[1]);
+        cudaEventElapsedTime(&m1, e[1], e[2]);
+        t0 += m0;
+        t1 += m1;
+    }
+    for (auto &x : e) cudaEventDestroy(x);
+    ms[0] = t0 / reps;
+    ms[1] = t1 / reps;
+    return rc;
 }
 
 template <int NV>

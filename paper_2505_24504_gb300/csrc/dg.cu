@@ -733,12 +733,11 @@ void launch_grp(const DGMember *dmem, const std::vector<DGMember> &h, int first,
 
 }  // namespace
 
-int dg_setup_background(jfnk_ctx *c) {
+int dg_setup_background(jfnk_ctx *c, cudaStream_t s) {
     DGK K = make_K(c);
     const int n = c->grid.nz * c->np1 + c->grid.nz + 1;
-    k_bg_dg<<<(n + 127) / 128, 128>>>(K, c->fbx, c->fbz, c->hbx, c->hbxw, c->hbz); jf_launched();
+    k_bg_dg<<<(n + 127) / 128, 128, 0, s>>>(K, c->fbx, c->fbz, c->hbx, c->hbxw, c->hbz); jf_launched();
     JF_CK(cudaGetLastError());
-    JF_CK(cudaDeviceSynchronize());
     return JFNK_OK;
 }
 

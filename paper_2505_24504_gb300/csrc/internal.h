@@ -132,6 +132,7 @@ struct jfnk_ctx {
     double *Ulin;
     // counters of the current call
     long long dg_calls, fv_calls;
+    double deadline;     // steady-clock seconds at which the current implicit step times out (0: none)
     // graph of one preconditioner application (captured on cap_stream, replayed
     // on the caller's stream); valid for one linearisation adt
     cudaGraphExec_t mg_graph;
@@ -177,8 +178,10 @@ inline void jf_launched(unsigned n = 1) {
 extern std::mutex g_jf_device_mu;
 
 // ---- kernels / launchers (implemented in the .cu files) ----
-int dg_setup_background(jfnk_ctx *c);
-int fv_setup_background(jfnk_ctx *c);
+// background fluxes of the DG operator and of every FV level, launched on s
+// (context creation runs them on a private stream and waits for that stream only)
+int dg_setup_background(jfnk_ctx *c, cudaStream_t s);
+int fv_setup_background(jfnk_ctx *c, cudaStream_t s);
 
 // DG operator modes
 enum DGMode {
@@ -217,7 +220,9 @@ int dg_residual_grouped(jfnk_ctx *const *ctx, int n, const double *const *U, dou
 // reductions / BLAS-1 (blas.cu)
 int red_dot(jfnk_ctx *c, const double *x, const double *y, size_t n, double *out_dev, int op, cudaStream_t s);
 int red_dotf(jfnk_ctx *c, const float *x, const float *y, size_t n, double *out_dev, int op, cudaStream_t s);
-enum { RED_SUM = 0, RED_SQRT = 1, RED_EPS = 2, RED_EPS32 = 3 };
+// RED_EPSP: eps of the preconditioner's FD products, numerator opts.precond_fd_eps
+// (sqrt(eps_mach) when 0)
+enum { RED_SUM = 0, RED_SQRT = 1, RED_EPS = 2, RED_EPS32 = 3, RED_EPSP = 4 };
 int blas_mdot(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *w, size_t n, double *h_dev, cudaStream_t s,
               const double *flag = nullptr);
 int blas_mupdate(jfnk_ctx *c, const double *V, int nv, size_t ldv, const double *h_dev, double *w, size_t n, double sign,
@@ -231,6 +236,7 @@ constexpr int GS_FUSED_MAX = 16;   // basis vectors of the fused CGS2 kernels
 // float copy of the normalised w goes (may be null)
 int blas_cgs2(jfnk_ctx *c, const double *V, const float *V32, int nv, size_t ldv, double *w, float *w32, size_t n,
               double *h1, double *h2, double *w1sq, double *nrm, double *flag, cudaStream_t s);
+int blas_time_cgs2(jfnk_ctx *c, int reps, double *ms, cudaStream_t s);
 int blas_f2d_eps(jfnk_ctx *c, const float *x, double *y, size_t n, double *eps_out, cudaStream_t s);
 int blas_scale_copy(const double *w, const double *nrm_dev, double *v, size_t n, cudaStream_t s);
 int blas_axpby(double a, const double *x, double b, const double *y, double *z, size_t n, cudaStream_t s);
@@ -245,6 +251,7 @@ int mg_linearize(jfnk_ctx *c, const double *U, double adt, cudaStream_t s);
 // are launched or captured directly)
 int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float *r32 = nullptr);
 int mg_graph_prepare(jfnk_ctx *c);
+int mg_time_fv_level0(jfnk_ctx *c, const double *U, const double *y, int reps, double *ms, cudaStream_t s);
 void jf_invalidate_graphs(jfnk_ctx *c);
 int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s);
 int transfer_to_fv64(jfnk_ctx *c, const double *u, double *v, cudaStream_t s);

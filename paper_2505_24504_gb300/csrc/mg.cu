@@ -1064,7 +1064,7 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
         else { JF_FV(D64, 0, FV_RES, false, K, ld, nullptr, nullptr, nullptr, nullptr, 0.0, out); }
     } else {
         double *epsp = c->scal + S_EPSFV + l;
-        JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPS, s));
+        JF_RET(red_dot(c, x, x, L.n, epsp, RED_EPSP, s));
         FLoad<D64, 1> ld{u, x, epsp, n1, 0.0};
         const double *dt = (const double *)L.dtau;
         const double *fu = (const double *)L.fu;
@@ -1167,7 +1167,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     if (!l4 && f2) {
         if (c->prec == 64) {
             double *epsp = c->scal + S_EPSFV + l;
-            JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPS, s));
+            JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPSP, s));
             FLoad<D64, 1> ld{(const double *)L.u, (const double *)x, epsp, n1, 0.0};
             if (visc) JF_DRT(D64, 1, true, ld, (const double *)b, (const double *)L.fu, (double *)bc, (double *)xc, (const double *)dtc, 0);
             else JF_DRT(D64, 1, false, ld, (const double *)b, (const double *)L.fu, (double *)bc, (double *)xc, (const double *)dtc, 0);
@@ -1189,7 +1189,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     } while (0)
     if (c->prec == 64) {
         double *epsp = c->scal + S_EPSFV + l;
-        JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPS, s));
+        JF_RET(red_dot(c, (const double *)x, (const double *)x, L.n, epsp, RED_EPSP, s));
         FLoad<D64, 1> ld{(const double *)L.u, (const double *)x, epsp, n1, 0.0};
         JF_DR4(D64, 1, K, ld, (const double *)b, (const double *)L.fu, c->mg_adt, L.fac, (double *)bc, (double *)xc,
                (const double *)dtc, 0);
@@ -1304,7 +1304,7 @@ int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2
         JF_CK(cudaGetLastError());
         return JFNK_OK;
     }
-    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPS, s));
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPSP, s));
     DGArgs a = {};
     a.U = c->mg_U;
     a.y = z;
@@ -1351,7 +1351,7 @@ int dg_defect(jfnk_ctx *c, const S *r, const S *z, S *d, cudaStream_t s);
 
 template <>
 int dg_defect<double>(jfnk_ctx *c, const double *r, const double *z, double *d, cudaStream_t s) {
-    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPS, s));
+    JF_RET(red_dot(c, z, z, c->N, c->scal + S_EPSDG, RED_EPSP, s));
     DGArgs a = {};
     a.U = c->mg_U;
     a.y = z;
@@ -1414,14 +1414,13 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
 }  // namespace
 
 // ---- entry points used by the API and the solver ---------------------------
-int fv_setup_background(jfnk_ctx *c) {
+int fv_setup_background(jfnk_ctx *c, cudaStream_t s) {
     for (int l = 0; l < c->nlev; ++l) {
         FVK K = make_fvk(c, l);
         const int n = 2 * c->lev[l].NZ + 1;
-        k_bg_fv<<<(n + 127) / 128, 128>>>(K, c->lev[l].hbx, c->lev[l].hbxw, c->lev[l].hbz); jf_launched();
+        k_bg_fv<<<(n + 127) / 128, 128, 0, s>>>(K, c->lev[l].hbx, c->lev[l].hbxw, c->lev[l].hbz); jf_launched();
         JF_CK(cudaGetLastError());
     }
-    JF_CK(cudaDeviceSynchronize());
     return JFNK_OK;
 }
 
@@ -1555,6 +1554,41 @@ int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float 
     }
     JF_CK(cudaMemcpyAsync(z, c->pout, sS * c->N, cudaMemcpyDeviceToDevice, s));
     return JFNK_OK;
+}
+
+// Diagnostic timing of the finest FV level's two FP32 kernels at the
+// linearisation U (alpha dt = 1): one pseudo-time smoothing step and the defect
+// fused with the restriction, x = b = (float) y.  ms[0], ms[1]: mean durations
+// over reps (CUDA events on s).  Overwrites the preconditioner's level vectors.
+int mg_time_fv_level0(jfnk_ctx *c, const double *U, const double *y, int reps, double *ms, cudaStream_t s) {
+    if (c->prec == 64 || !c->mg_on || c->nlev < 2) return JFNK_EINVAL;
+    JF_RET(mg_linearize(c, U, 1.0, s));
+    FVLev &L = c->lev[0];
+    FVLev &C = c->lev[1];
+    if (L.n != c->N) return JFNK_EINVAL;
+    JF_RET(blas_copy_d2f(y, (float *)L.x, L.n, s));
+    JF_RET(blas_copy_d2f(y, (float *)L.b, L.n, s));
+    cudaEvent_t e[3];
+    for (auto &x : e) JF_CK(cudaEventCreate(&x));
+    double t0 = 0.0, t1 = 0.0;
+    int rc = JFNK_OK;
+    for (int r = 0; r < reps && rc == JFNK_OK; ++r) {
+        cudaEventRecord(e[0], s);
+        rc = fv_op32(c, 0, FV_SMOOTH, (const float *)L.x, (const float *)L.b, (float *)L.x2, s);
+        cudaEventRecord(e[1], s);
+        if (rc == JFNK_OK) rc = fv_defect_restrict(c, 0, L.x, L.b, C.b, C.x, C.dtau, s);
+        cudaEventRecord(e[2], s);
+        if (cudaEventSynchronize(e[2]) != cudaSuccess) rc = JFNK_ECUDA;
+        float m0 = 0.f, m1 = 0.f;
+        cudaEventElapsedTime(&m0, e[0], e[1]);
+        cudaEventElapsedTime(&m1, e[1], e[2]);
+        t0 += m0;
+        t1 += m1;
+    }
+    for (auto &x : e) cudaEventDestroy(x);
+    ms[0] = t0 / reps;
+    ms[1] = t1 / reps;
+    return rc;
 }
 
 int fv_rhs64(jfnk_ctx *c, int l, const double *u, double *f, cudaStream_t s) {

@@ -90,7 +90,7 @@ JF_D TL32 jsqrt(TL32 a) {
     const float r = rsqrtf(a.v);
     return TL32{a.v * r, 0.5f * a.d * r};
 }
-JF_D double val(TL32 a) { return (double)a.v; }
+JF_D float val(TL32 a) { return a.v; }   // compared in FP32: no FP64-pipe conversion
 JF_D TL32 jfma(TL32 a, TL32 b, TL32 c) { return a * b + c; }
 
 // Constants held in both precisions: the FP32 tangent takes the float copy, so

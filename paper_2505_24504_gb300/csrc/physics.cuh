@@ -58,8 +58,8 @@ JF_D void hllc(const T UL[4], const T UR[4], const PhysC &P, const PowTab *pt, T
     const T num = (pR - pL) + UL[0] * uL * dL - UR[0] * uR * dR;
     const T den = UL[0] * dL - UR[0] * dR;
     const T Sst = num / den;
-    const bool left = val(Sst) >= 0.0 || val(SL) >= 0.0;
-    const bool pure = val(SL) >= 0.0 || (!left && val(SR) < 0.0);
+    const bool left = val(Sst) >= 0 || val(SL) >= 0;   // integer 0: compared in the scalar's own precision
+    const bool pure = val(SL) >= 0 || (!left && val(SR) < 0);
     T U[4], F[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) U[v] = sel(left, UL[v], UR[v]);

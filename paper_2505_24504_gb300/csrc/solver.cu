@@ -9,9 +9,18 @@
 #include <math.h>
 #include <string.h>
 
+#include <chrono>
+
 #include "internal.h"
 
 namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// the step's wall-clock budget (opts.time_budget_ms) has run out
+bool out_of_time(const jfnk_ctx *c) { return c->deadline > 0.0 && now_s() > c->deadline; }
 
 struct Stats {
     int newton_its = 0, gmres_its = 0;
@@ -204,6 +213,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
         for (int j = 0; j < m; ++j) {
             JF_RET(arnoldi_step(c, U, adt, j, s, ph));
             JF_CK(cudaStreamSynchronize(s));
+            if (out_of_time(c)) return JFNK_ETIMEOUT;
             st.t_pre += ph.ms(0, 1);
             st.t_jv += ph.ms(1, 2);
             st.t_orth += ph.ms(2, 3);
@@ -308,6 +318,7 @@ int newton(jfnk_ctx *c, double *U, double adt, Stats &st, cudaStream_t s) {
         eta_prev = eta;
         ph.mark(2, s);
         JF_RET(eval_G(c, U, adt, &nk, s));   // synchronises
+        if (out_of_time(c)) return JFNK_ETIMEOUT;
         ph.mark(3, s);
         if (ph.on) {
             cudaEventSynchronize(ph.e[3]);
@@ -327,6 +338,7 @@ extern "C" int implicit_step(jfnk_ctx *c, double *U, double dt, int scheme, jfnk
     const size_t N = c->N;
     c->dg_calls = 0;
     c->fv_calls = 0;
+    c->deadline = c->opts.time_budget_ms > 0.0 ? now_s() + 1e-3 * c->opts.time_budget_ms : 0.0;
     Stats st;
     int rc = JFNK_OK;
     JF_CK(cudaMemcpyAsync(c->Usave, U, 8 * N, cudaMemcpyDeviceToDevice, s));

@@ -39,7 +39,8 @@ class Opts(C.Structure):
                 ("fv_levels", C.c_int), ("massfix", C.c_int), ("transfer_l2", C.c_int), ("precond_prec", C.c_int),
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
-                ("tile_fv", C.c_int), ("fv_split_cells", C.c_int), ("profile", C.c_int)]
+                ("tile_fv", C.c_int), ("fv_split_cells", C.c_int), ("profile", C.c_int),
+                ("precond_fd_eps", C.c_double), ("time_budget_ms", C.c_double)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -153,10 +154,22 @@ class Batch:
         _check(_lib().jfnk_batch_dg_residual(self.h, U, f, _stream(stream)), "jfnk_batch_dg_residual")
 
 
+def _check_norm_args(x, out, n):
+    """float64 vectors and 0 <= n <= x.numel(), checked before anything is launched
+    (a wrong dtype or length would make the kernel read past the buffer)."""
+    import torch
+    n = x.numel() if n is None else int(n)
+    if x.dtype != torch.float64 or out.dtype != torch.float64:
+        raise ValueError("x and out must be float64")
+    if n < 0 or n > x.numel() or out.numel() < 1:
+        raise ValueError(f"n = {n} outside [0, {x.numel()}] or empty out")
+    return n
+
+
 def norm2_noalloc(x, out, n=None, stream=None):
     """|x|_2 into out[0] without a context or any device allocation (fixed
     in-library scratch; see include/jfnk.h)."""
-    n = x.numel() if n is None else n
+    n = _check_norm_args(x, out, n)
     _check(_lib().jfnk_norm2_noalloc(_ptr(x), n, _ptr(out), _stream(stream)), "jfnk_norm2_noalloc")
 
 
@@ -241,7 +254,7 @@ class Context:
         return st
 
     def norm2(self, x, out, n=None, stream=None):
-        n = x.numel() if n is None else n
+        n = _check_norm_args(x, out, n)
         _check(_lib().jfnk_norm2(self.h, _ptr(x), n, _ptr(out), _stream(stream)), "jfnk_norm2")
 
     def eos_pressure(self, E, p, stream=None):

@@ -42,6 +42,24 @@ class Bubble:
 
 
 @dataclass(frozen=True)
+class FlattenedGaussian:
+    """theta'(x,z) = A for r < a, A exp(-(r-a)^2/s^2) for 0 <= r-a <= 3s, else 0,
+    r = |(x,z) - (xc,zc)|  (the rising-bubble perturbation of Sec. 4.2)."""
+    amp: float
+    xc: float
+    zc: float
+    a: float
+    s: float
+
+    def theta(self, x, z):
+        x = np.asarray(x, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        d = np.sqrt((x - self.xc) ** 2 + (z - self.zc) ** 2) - self.a
+        g = np.exp(-np.maximum(d, 0.0) ** 2 / self.s ** 2)
+        return self.amp * np.where(d < 0.0, 1.0, np.where(d <= 3.0 * self.s, g, 0.0))
+
+
+@dataclass(frozen=True)
 class Wave:
     """theta'(x,z) = theta_c sin(pi z/Z) / (1 + ((x-xc)/a)^2)  (Sec. 4.1 perturbation)."""
     theta_c: float
@@ -164,6 +182,17 @@ INERTIA_GRAVITY_Q3_80x3 = Workload(
     theta0=250.0, mu=0.0, bubble=Wave(0.01, 100000.0, 5000.0, 10000.0),
     scheme=1, dt_fixed=25.0, steps=120, fv_levels=3, periodic_x=True,
     background=2, ubg=20.0, N_bv=0.01, **PHYS_ROBERT)
+
+
+# Workload 5: rising bubble (Sec. 4.2): [0,1000m]x[0,2000m], neutral atmosphere
+# theta0 = 303.15 K, flattened Gaussian theta' (A = 0.5 K, centre (500 m, 520 m),
+# a = 50 m, s = 100 m), slip walls; DG Q3 on 40 x 80 quads (25 m elements),
+# 5 FV levels, SDIRK2 at the paper's dt = 10 s.
+RISING_BUBBLE_Q3_40x80 = Workload(
+    name="rising bubble Q3 40x80 (204,800 DOF), SDIRK2, dt=10s",
+    nx=40, nz=80, x0=0.0, x1=1000.0, z0=0.0, z1=2000.0, k=3,
+    theta0=303.15, mu=0.0, bubble=FlattenedGaussian(0.5, 500.0, 520.0, 50.0, 100.0),
+    scheme=1, dt_fixed=10.0, steps=120, fv_levels=5, **PHYS_ROBERT)
 
 
 def scaled(w: Workload, nx: int, nz: int, **kw) -> Workload:

@@ -45,3 +45,36 @@ def test_host_only_calls(libpath):
     assert P.Context.workspace_bytes(g2, 2, o) > 3.0 * b20   # 4x the unknowns, fixed scratch aside
     assert P.Context.workspace_bytes(P.Grid(0, 10, 0, 1, 0, 1, 0), 2, o) == 0
     assert P.Context.workspace_bytes(g, 5, o) == 0
+    # the options struct of the binding has the header's size and field order
+    assert o.precond_fd_eps == 0.0 and o.time_budget_ms == 0.0
+    assert ctypes.sizeof(P.Opts) == _c_sizeof_opts()
+
+
+def _c_sizeof_opts():
+    """sizeof(jfnk_opts) as the C compiler lays it out (gcc on the header)."""
+    import subprocess
+    import tempfile
+    src = '#include <stdio.h>\n#include "jfnk.h"\nint main(void){printf("%zu", sizeof(jfnk_opts));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "s.c"), os.path.join(d, "s")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        return int(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+
+
+def test_norm_wrappers_reject_bad_arguments_before_any_launch():
+    # a float32 vector or an n beyond the tensor would make the reduction read
+    # past the buffer: the binding refuses both before the library is called
+    torch = pytest.importorskip("torch")
+    from paper_2505_24504_gb300 import jfnk
+    x32 = torch.zeros(8, dtype=torch.float32)
+    x64 = torch.zeros(8, dtype=torch.float64)
+    out = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        jfnk.norm2_noalloc(x32, out)
+    with pytest.raises(ValueError):
+        jfnk.norm2_noalloc(x64, out, n=9)
+    with pytest.raises(ValueError):
+        jfnk.norm2_noalloc(x64, out, n=-1)
+    with pytest.raises(ValueError):
+        jfnk.norm2_noalloc(x64, torch.zeros(1, dtype=torch.float32))

@@ -236,7 +236,40 @@ def test_preconditioner_parity_at_fd_noise(case, split):
         noise.append(rel(mg.apply(r), ref))
     err = rel(to_cpu(z, dg.shape), ref)
     assert err <= max(10.0 * max(noise), 1e-10), (err, noise)
-    assert err <= 1e-2
+
+
+# FD step numerator of the preconditioner's products in the tight parity tests:
+# eps = C_FD / |x|, so every perturbation eps x_i sits ~C_FD / sqrt(n) above the
+# state instead of ~1e-8 / sqrt(n).  The two sides round u + eps x differently
+# (one FMA rounding against two) by at most one ulp of |u| <= 400, so a product's
+# relative difference is about ulp(400) sqrt(n) / C_FD <= 6e-14 * 1e3 / 1e-2 =
+# 6e-9 per FD product; the preconditioner chains a few tens of them.
+C_FD = 1e-2
+FD_PARITY = 1e-6    # the FP64 mg_precondition bar
+
+
+def _fd_bound(n, products):
+    return min(FD_PARITY, products * 2.0 ** -44 * 400.0 * np.sqrt(n) / C_FD + 1e-12)
+
+
+@pytest.mark.parametrize("key", ["mg111111V", "mg132211V", "mg111111W"])
+def test_preconditioner_parity_fixed_fd_step(case, key):
+    # the whole Q^-1 (DG smoothing, transfers, every FV level, V and W cycles) in
+    # FP64 with the same FD step on both sides: agreement to the FD round-off
+    # bound above, at most 1e-6 relative
+    from oracle.fv import Multigrid
+    w, _, dg = case
+    ctx = gpu_context(w, mg_key=key, precond_fd_eps=C_FD)
+    Up = perturbed_state(w, dg, seed=19)
+    r = synth.random_perturbation(dg.shape[1:], 20)
+    z = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.mg_precondition(to_gpu(Up), w.dt, to_gpu(r), z)
+    mg = Multigrid(dg, w.fv_levels, key, fd_eps=C_FD)
+    mg.linearize(Up, w.dt)
+    ref = mg.apply(r)
+    products = mg.stats["dg_calls"] + sum(mg.stats["fv_calls"])
+    err = rel(to_cpu(z, dg.shape), ref)
+    assert err <= _fd_bound(dg.N, products), (err, products)
 
 
 @pytest.mark.parametrize("prec", [32, 16])
@@ -291,6 +324,25 @@ def test_implicit_step_l2_transfer_parity(name):
     ref = implicit_step(dg, U0, w.dt, scheme=1, tol=w.newton_tol,
                         precond=Multigrid(dg, w.fv_levels, w.mg_key, l2=True))
     got = to_cpu(U, dg.shape)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
+
+
+@pytest.mark.parametrize("name", ["q2-20x10", "q3-11x6", "visc-q2-24x6"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_implicit_step_w_cycle_parity(name, prec):
+    # W cycle (the coarse correction applied twice, Sec. 3.4) inside the
+    # implicit step: same converged answer as the oracle's step with the W cycle
+    w = _cases()[name]
+    dg = oracle_dg(w)
+    ctx = gpu_context(w, mg_key="mg111111W", precond_prec=prec)
+    U0 = initial_state(w, dg)
+    U = to_gpu(U0)
+    st = ctx.implicit_step(U, w.dt, scheme=1)
+    assert st.status == 0
+    ref = _oracle_step(w, dg, U0, 1, key="mg111111W")
+    got = to_cpu(U, dg.shape)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
 
 
