@@ -380,18 +380,20 @@ def time_grouped_residual(batch, ctxs, Us, dof, hbm_peak, reps=10):
             "note": "16 B per unknown algorithmic; FP64-ALU bound, so far below the HBM roof"}
 
 
-def run_serving(seconds, rate, overload_seconds):
+def run_serving(seconds, rate, overload_seconds, rank=0, world=1, dist=None):
     """Poisson arrivals of implicit-step requests on resident states: 16 ensemble
     members (80 %) and 4 viscous density-current states (20 %).  The HBM budget
     is what the device has free, so every state keeps its context (Krylov basis,
     FV levels, graphs) resident across requests.  One run below capacity over the
     full horizon, one short overload run at 200/s, and the same request list
-    stepped serially with plain FP64 contexts for comparison."""
+    stepped serially with plain FP64 contexts for comparison.  With several
+    ranks each GPU serves the states it owns (sid % world == rank) and the
+    ranks pool their latencies at the end (no exchange while serving)."""
     import numpy as np
     import torch
 
     from paper_2505_24504_gb300 import jfnk
-    from paper_2505_24504_gb300.serve import Server, StateSpec
+    from paper_2505_24504_gb300.serve import Server, StateSpec, pooled_summary, shard_requests, shard_states
     ens = synth.ensemble(16)
     visc = [synth.DENSITY_CURRENT_Q2_256x32] * 4
     work = ens + visc
@@ -399,6 +401,8 @@ def run_serving(seconds, rate, overload_seconds):
     def specs_for(prec):
         specs = {}
         for sid, m in enumerate(work):
+            if sid % world != rank:
+                continue
             c = make_context(m, prec)
             specs[sid] = StateSpec(grid=c.grid, k=c.k, phys=c.phys, opts=c.opts, dt=m.dt, scheme=m.scheme,
                                    U=initial_state(c, m))
@@ -408,12 +412,14 @@ def run_serving(seconds, rate, overload_seconds):
     def requests(r, horizon, seed):
         arr = synth.poisson_arrivals(r, horizon, seed=seed)
         rng = np.random.Generator(np.random.Philox(seed + 4))
-        return [(float(t), int(rng.integers(0, 16)) if rng.random() < 0.8 else 16 + int(rng.integers(0, 4)))
+        reqs = [(float(t), int(rng.integers(0, 16)) if rng.random() < 0.8 else 16 + int(rng.integers(0, 4)))
                 for t in arr]
+        return shard_requests(reqs, rank, world)
 
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
-    out = {"states": len(work), "hbm_budget_bytes": budget}
+    out = {"states": len(work), "hbm_budget_bytes": budget, "ranks": world,
+           "sharding": "state sid served by rank sid % world" if world > 1 else "one GPU"}
     for name, r, horizon in (("below_capacity", rate, seconds), ("overload", 200.0, overload_seconds)):
         if horizon <= 0:
             continue
@@ -423,6 +429,8 @@ def run_serving(seconds, rate, overload_seconds):
         rep = srv.run(reqs, timeout_s=max(600.0, 20 * horizon))
         srv.close()
         s = rep.summary()
+        if world > 1:
+            s["pooled_over_ranks"] = pooled_summary(rep, dist)
         s.update({"arrival_rate_per_s": r, "horizon_s": horizon,
                   "basis_rebuilds": rep.contexts_created - len({q[1] for q in reqs}),
                   "footprint_total_bytes": sum(sp.footprint for sp in specs.values())})
@@ -877,7 +885,7 @@ def main():
     if args.ensemble > 0:
         line["batched"] = run_ensemble(args.ensemble, args.ensemble_steps, 1, args.ensemble_threads, hbm_peak)
     if args.serve_seconds > 0 or args.overload_seconds > 0:
-        line["serving"] = run_serving(args.serve_seconds, args.serve_rate, args.overload_seconds)
+        line["serving"] = run_serving(args.serve_seconds, args.serve_rate, args.overload_seconds, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

@@ -128,6 +128,9 @@ typedef struct {
     int profile;         /* 1: time the phases of implicit_step with CUDA events (jfnk_stats) */
     double precond_fd_eps;
     double time_budget_ms;
+    int dg_fused;        /* FP32 tangent DG products of the preconditioner: 0 or 1 one fused
+                            launch per product (faces, volume and epilogue per element strip),
+                            2 a face launch and a volume launch */
 } jfnk_opts;
 
 /* Counters of one implicit_step (Sec. 4.2 counts linear iterations and

@@ -259,6 +259,7 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     if (o.gmres_restart < 1 || o.gmres_restart > 64 || o.gmres_max < 1 || o.newton_max < 1) return JFNK_EINVAL;
     if (o.precond_prec != 64 && o.precond_prec != 32 && o.precond_prec != 16) return JFNK_EINVAL;
     if (!(o.precond_fd_eps >= 0.0) || !(o.time_budget_ms >= 0.0)) return JFNK_EINVAL;
+    if (o.dg_fused < 0 || o.dg_fused > 2) return JFNK_EINVAL;
     if (o.fv_levels < 1) o.fv_levels = 1;
     if (o.tile_faces == 0) o.tile_faces = 128;
     if (o.tile_volume == 0) o.tile_volume = 2;

@@ -526,6 +526,311 @@ __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGA
     volume_body<T, IN, MODE, NP1, VISC, TV>(K, ld0, A, phix, symx, phiz, symz, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 tangent product in ONE launch (the preconditioner's DG smoothing steps
+// and defect).  A block owns a strip of E elements of one element row, one
+// thread per node.  The strip's states go to shared memory; every face point
+// of the strip's elements is evaluated there (x faces between the strip's
+// elements once, the strip's two end faces and the z faces with the neighbour
+// trace read from global memory), then the volume term, the lift of the
+// shared face terms and the mode's epilogue run as in the two-kernel form.  In
+// FP32 the duplicated z faces (each is evaluated by the strips above and below)
+// cost less than a second launch and the face buffers' round trip.
+// FIRST = 1 (defect mode): the direction is the first pseudo-time step from zero,
+// z = dtau_E r, formed on the fly; the epilogue also writes that z to out1f.
+template <int NP1> struct StripOf {
+    static constexpr int NP = NP1 * NP1;
+    static constexpr int E = (128 / NP) > 0 ? 128 / NP : 1;
+};
+
+template <int NP1, bool VISC, int MODE, int FIRST>
+__global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, float *out1f) {
+    jf_pdl_enter();
+    constexpr int NP = NP1 * NP1;
+    constexpr int E = StripOf<NP1>::E;
+    // U' (value, tangent) of the strip's elements [1], of the elements below [0] and
+    // above [2] them, and of the strip's west [0] and east [1] neighbours: every
+    // trace the faces need comes from shared memory, loaded coalesced up front
+    __shared__ TL32 sn[3][E][4][NP];
+    __shared__ TL32 se[2][4][NP];
+    __shared__ float sg[2][E][4][NP];              // volume fluxes (tangent part)
+    __shared__ float sPx[E + 1][4][NP1];           // x-face terms Phi (face f west of strip element f)
+    __shared__ float sPz[2][E][4][NP1];            // z-face terms: [0] bottom, [1] top of element le
+    __shared__ float sSx[VISC ? E + 1 : 1][6][NP1];   // viscous symmetry terms (L side 0..2, R side 3..5)
+    __shared__ float sSz[VISC ? 2 : 1][VISC ? E : 1][6][NP1];
+    __shared__ float sDx[NP1][NP1], sDz[NP1][NP1], sDn[NP1][NP1], sl[8][NP1];
+    const int nx = K.nx, nz = K.nz;
+    const int nstrip = (nx + E - 1) / E;
+    const int ez = (int)blockIdx.x / nstrip, ex0 = ((int)blockIdx.x % nstrip) * E;
+    const int Ev = min(E, nx - ex0);
+    const size_t N1 = (size_t)K.n_el * NP;
+    const size_t nrow = (size_t)nz * NP1;
+    if (threadIdx.x < NP) {
+        const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
+        sDx[r][q] = K.Dxf[r][q];
+        sDz[r][q] = K.Dzf[r][q];
+        sDn[r][q] = K.Dnf[r][q];
+    }
+    if (threadIdx.x < NP1) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sl[r][threadIdx.x] = K.liftf[r][threadIdx.x];
+    }
+    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+    const int a = node % NP1, b = node / NP1;
+    const bool active = le < Ev;
+    const int e = ez * nx + ex0 + le;
+    // direction at a node: y (or dtau_E r for the first step from zero)
+    auto dir = [&](int el, size_t i) -> float { return FIRST ? A.dtauf[el] * A.rf[i] : A.yf[i]; };
+    auto load = [&](int el, TL32 (*dst)[NP]) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const size_t gi = (size_t)v * N1 + (size_t)el * NP + node;
+            dst[v][node] = TL32{A.Uf[gi], dir(el, gi)};
+        }
+    };
+    float ef[4] = {0.f, 0.f, 0.f, 0.f}, edt = 0.0f;
+    if (active) {
+        load(e, sn[1][le]);
+        if (ez > 0) load(e - nx, sn[0][le]);
+        if (ez < nz - 1) load(e + nx, sn[2][le]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
+            if (MODE == DG_TLSMOOTH || (MODE == DG_TLJV && A.rf)) ef[v] = A.rf[gi];
+        }
+        if (MODE == DG_TLSMOOTH) edt = A.dtauf[e];
+    }
+    const bool has_w = ex0 > 0 || K.periodic, has_e = ex0 + Ev < nx || K.periodic;
+    if (le == 0 && has_w) load(ez * nx + (ex0 - 1 + nx) % nx, se[0]);
+    if (le == 1 && has_e) load(ez * nx + (ex0 + Ev) % nx, se[1]);
+    __syncthreads();
+    // ---- volume fluxes (independent of the faces below) -----------------------
+    TL32 Up[4];
+    if (active) {
+        const int J = ez * NP1 + b;
+        TL32 U[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Up[v] = sn[1][le][v][node];
+            U[v] = Up[v] + TL32{K.ubvf[v * nrow + J], 0.0f};
+        }
+        const TL32 ir = mk(1.0, TL32{}) / U[0];
+        const TL32 p = pressure(U[3], K.pc, nullptr);
+        TL32 Fx[4], Fz[4];
+        flux_c<TL32, 0>(U, U[1] * ir, p, Fx);
+        flux_c<TL32, 1>(U, U[2] * ir, p, Fz);
+        if (VISC) {
+            TL32 dx[4], dz[4], Gx[4], Gz[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                TL32 sx = mk(0.0, TL32{}), sz = mk(0.0, TL32{});
+#pragma unroll
+                for (int q = 0; q < NP1; ++q) {
+                    sx = jfma(TL32{sDn[a][q], 0.0f}, sn[1][le][v][b * NP1 + q], sx);
+                    sz = jfma(TL32{sDn[b][q], 0.0f}, sn[1][le][v][q * NP1 + a], sz);
+                }
+                dx[v] = TL32{K.two_hxf, 0.0f} * sx;
+                dz[v] = TL32{K.two_hzf, 0.0f} * sz + TL32{K.dubvf[v * nrow + J], 0.0f};
+            }
+            viscous(U, dx, K.pc, Gx);
+            viscous(U, dz, K.pc, Gz);
+#pragma unroll
+            for (int v = 1; v < 4; ++v) {
+                Fx[v] = Fx[v] - Gx[v];
+                Fz[v] = Fz[v] - Gz[v];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            sg[0][le][v][node] = Fx[v].d;
+            sg[1][le][v][node] = Fz[v].d;
+        }
+    }
+    // ---- faces ------------------------------------------------------------
+    // value and derivative traces of variable v along NP1 nodes i0 + q st of one
+    // element's staged nodes, in the order of line_trace
+    auto trace = [&](const TL32 (*src)[NP], int v, int i0, int st, const float *pa, const float *pd, TL32 &tv,
+                     TL32 &td) {
+        tv = mk(0.0, TL32{});
+        td = mk(0.0, TL32{});
+#pragma unroll
+        for (int q = 0; q < NP1; ++q) {
+            const TL32 u = src[v][i0 + q * st];
+            tv = jfma(TL32{pa[q], 0.0f}, u, tv);
+            if (VISC) td = jfma(TL32{pd[q], 0.0f}, u, td);
+        }
+    };
+    const TL32 half = mk(0.5, TL32{});
+    const int nxf = (Ev + 1) * NP1, nzf = 2 * Ev * NP1;
+    for (int t = threadIdx.x; t < nxf + nzf; t += blockDim.x) {
+        TL32 trL[4], trR[4], gL[4], gR[4], UL[4], UR[4], H[4], Phi[4], sLv[3], sRv[3];
+        if (t < nxf) {
+            const int f = t / NP1, sp = t % NP1;      // face f lies west of strip element f
+            const bool wallL = f == 0 && !has_w, wallR = f == Ev && !has_e;
+            const TL32 (*srcL)[NP] = f > 0 ? sn[1][f - 1] : se[0];
+            const TL32 (*srcR)[NP] = f < Ev ? sn[1][f] : se[1];
+            const int J = ez * NP1 + sp;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                TL32 aL, aR, dL, dR;
+                if (!wallR) trace(srcR, v, sp * NP1, 1, K.tlm, K.tdlm, aR, dR);
+                if (!wallL) trace(srcL, v, sp * NP1, 1, K.tlp, K.tdlp, aL, dL);
+                if (wallL) { aL = aR; dL = dR; }
+                if (wallR) { aR = aL; dR = dL; }
+                trL[v] = aL;
+                trR[v] = aR;
+                gL[v] = TL32{K.two_hxf, 0.0f} * dL;
+                gR[v] = TL32{K.two_hxf, 0.0f} * dR;
+                UL[v] = aL + TL32{K.ubvf[v * nrow + J], 0.0f};
+                UR[v] = aR + TL32{K.ubvf[v * nrow + J], 0.0f};
+            }
+            TL32 Gh[4];
+            if (wallL) {
+                mirror<TL32, 0>(UR, Gh);
+                hllc<TL32, 0>(Gh, UR, K.pc, nullptr, H);
+            } else if (wallR) {
+                mirror<TL32, 0>(UL, Gh);
+                hllc<TL32, 0>(UL, Gh, K.pc, nullptr, H);
+            } else {
+                hllc<TL32, 0>(UL, UR, K.pc, nullptr, H);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Phi[v] = H[v];
+            if (VISC && !wallL && !wallR) {
+                TL32 FL[4], FR[4], Jp[4];
+                viscous(UL, gL, K.pc, FL);
+                viscous(UR, gR, K.pc, FR);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
+#pragma unroll
+                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TL32{K.eta_xf, 0.0f} * Jp[v];
+                TL32 AL[4], AR[4];
+                viscous(UL, Jp, K.pc, AL);
+                viscous(UR, Jp, K.pc, AR);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sLv[q] = half * AL[q + 1];
+                    sRv[q] = half * AR[q + 1];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sPx[f][v][sp] = Phi[v].d;
+            if (VISC) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sSx[f][q][sp] = sLv[q].d;
+                    sSx[f][3 + q][sp] = sRv[q].d;
+                }
+            }
+        } else {
+            const int u = t - nxf;
+            const int top = u / (Ev * NP1), l = (u / NP1) % Ev, sp = u % NP1;   // column a = sp
+            const int fz = ez + top;                 // global horizontal face 0..nz
+            const bool wallB = fz == 0, wallT = fz == nz;
+            TL32 gB[4], gT[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                TL32 aB, aT, dB, dT;
+                if (top) {   // own element below (trace at eta = +1), element ez+1 above
+                    trace(sn[1][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
+                    if (!wallT) trace(sn[2][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
+                    else { aT = aB; dT = dB; }
+                } else {     // element ez-1 below, own element above (trace at eta = -1)
+                    trace(sn[1][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
+                    if (!wallB) trace(sn[0][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
+                    else { aB = aT; dB = dT; }
+                }
+                trL[v] = aB;
+                trR[v] = aT;
+                const TL32 dub = TL32{K.dubhf[(size_t)v * (nz + 1) + fz], 0.0f};
+                gB[v] = TL32{K.two_hzf, 0.0f} * dB + dub;
+                gT[v] = TL32{K.two_hzf, 0.0f} * dT + dub;
+                UL[v] = aB + TL32{K.ubhf[(size_t)v * (nz + 1) + fz], 0.0f};
+                UR[v] = aT + TL32{K.ubhf[(size_t)v * (nz + 1) + fz], 0.0f};
+            }
+            TL32 Gh[4];
+            if (wallB) {
+                mirror<TL32, 1>(UR, Gh);
+                hllc<TL32, 1>(Gh, UR, K.pc, nullptr, H);
+            } else if (wallT) {
+                mirror<TL32, 1>(UL, Gh);
+                hllc<TL32, 1>(UL, Gh, K.pc, nullptr, H);
+            } else {
+                hllc<TL32, 1>(UL, UR, K.pc, nullptr, H);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Phi[v] = H[v];
+            if (VISC && !wallB && !wallT) {
+                TL32 FB[4], FT[4], Jp[4];
+                viscous(UL, gB, K.pc, FB);
+                viscous(UR, gT, K.pc, FT);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
+#pragma unroll
+                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TL32{K.eta_zf, 0.0f} * Jp[v];
+                TL32 AB[4], AT[4];
+                viscous(UL, Jp, K.pc, AB);
+                viscous(UR, Jp, K.pc, AT);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sLv[q] = half * AB[q + 1];
+                    sRv[q] = half * AT[q + 1];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sPz[top][l][v][sp] = Phi[v].d;
+            if (VISC) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sSz[top][l][q][sp] = sLv[q].d;
+                    sSz[top][l][3 + q][sp] = sRv[q].d;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    const float lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
+    const float lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
+    const float adtf = (float)A.adt;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        float f = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NP1; ++q) {
+            f = fmaf(sDx[a][q], sg[0][le][v][b * NP1 + q], f);
+            f = fmaf(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
+        }
+        if (v == 2) f = fmaf(-K.gf, Up[0].d, f);
+        f = fmaf(lmxa, sPx[le][v][b], f);
+        f = fmaf(-lpxa, sPx[le + 1][v][b], f);
+        f = fmaf(lmzb, sPz[0][le][v][a], f);
+        f = fmaf(-lpzb, sPz[1][le][v][a], f);
+        if (VISC && v > 0) {
+            const int q = v - 1;
+            f = fmaf(dlmxa, sSx[le][3 + q][b], f);
+            f = fmaf(dlpxa, sSx[le + 1][q][b], f);
+            f = fmaf(dlmzb, sSz[0][le][3 + q][a], f);
+            f = fmaf(dlpzb, sSz[1][le][q][a], f);
+        }
+        const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
+        const float z = Up[v].d;
+        const float jz = z - adtf * f;
+        if (MODE == DG_TLJV) {
+            ((float *)A.out0)[gi] = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
+            if (FIRST) out1f[gi] = z;
+        } else {  // DG_TLSMOOTH
+            ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
+        }
+    }
+}
+
 // background fluxes at node rows and horizontal faces, with the residual's own
 // D64 functions so that U' = 0 cancels bit for bit
 __global__ void k_bg_dg(DGK K, double *fbx, double *fbz, double *hbx, double *hbxw, double *hbz) {
@@ -673,6 +978,30 @@ int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, 
     return JFNK_OK;
 }
 
+// FP32 tangent modes: one fused launch (k_dgtl); a.first1 selects the defect at
+// the first pseudo-time step from zero, whose z = dtau r is also written to a.out1f
+template <int NP1, bool VISC, int MODE>
+int launch_tl(jfnk_ctx *c, const DGK &K, const DGArgs &a, cudaStream_t s) {
+    constexpr int E = StripOf<NP1>::E;
+    const unsigned nb = (unsigned)(K.nz * ((K.nx + E - 1) / E));
+    const int threads = E * NP1 * NP1;
+    if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
+    if (MODE == DG_TLJV && a.out1f)
+        jf_launch(k_dgtl<NP1, VISC, MODE, 1>, nb, threads, 0, s, K, a, a.out1f);
+    else
+        jf_launch(k_dgtl<NP1, VISC, MODE, 0>, nb, threads, 0, s, K, a, (float *)nullptr);
+    jf_launched();
+    JF_CK(cudaGetLastError());
+    if (c->timing) {
+        JF_CK(cudaEventRecord(c->tev[1], s));
+        JF_CK(cudaEventSynchronize(c->tev[1]));
+        float m0 = 0.f;
+        JF_CK(cudaEventElapsedTime(&m0, c->tev[0], c->tev[1]));
+        c->t_faces_ms += m0;   // the whole fused product; the volume share reads 0
+    }
+    return JFNK_OK;
+}
+
 template <int NP1, bool VISC>
 int dispatch_mode(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
     DGK K = make_K(c);
@@ -682,8 +1011,14 @@ int dispatch_mode(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
         case DG_JV: return launch<D64, 1, DG_JV, NP1, VISC>(c, K, Loader<D64, 1>{a.U, a.y, a.eps, 0.0}, a, s);
         case DG_SMOOTH64:
             return launch<D64, 1, DG_SMOOTH64, NP1, VISC>(c, K, Loader<D64, 1>{a.U, a.y, a.eps, 0.0}, a, s);
-        case DG_TLJV: return launch<TL32, 2, DG_TLJV, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
-        case DG_TLSMOOTH: return launch<TL32, 2, DG_TLSMOOTH, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
+        case DG_TLJV:
+            if (c->opts.dg_fused == 2 && !a.out1f)
+                return launch<TL32, 2, DG_TLJV, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
+            return launch_tl<NP1, VISC, DG_TLJV>(c, K, a, s);
+        case DG_TLSMOOTH:
+            if (c->opts.dg_fused == 2)
+                return launch<TL32, 2, DG_TLSMOOTH, NP1, VISC>(c, K, Loader<TL32, 2>{a.Uf, a.yf}, a, s);
+            return launch_tl<NP1, VISC, DG_TLSMOOTH>(c, K, a, s);
     }
     return JFNK_EINVAL;
 }

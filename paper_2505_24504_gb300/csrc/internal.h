@@ -210,6 +210,8 @@ struct DGArgs {
     double *out1;
     double *tr_out;        // FP64 residual / G: store the face traces of U here (may be null)
     const double *tr_in;   // FP64 FD product: face traces of U from the residual at U (may be null)
+    float *out1f;          // FP32 defect at the first step from zero: z = dtau r is formed from rf and
+                           // dtauf on the fly (yf unused) and written here
 };
 
 int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);

@@ -128,6 +128,15 @@ JF_D void face_flux(const T UL[4], const T UR[4], bool wallL, bool wallR, const 
     }
 }
 
+// the same two-point flux from precomputed sides (1/rho of each side reused)
+template <class T>
+JF_D void visc2_s(const Side<T> &L, const Side<T> &R, T coef, T V[4]) {
+    const T c = coef * (L.U[0] + R.U[0]);
+    V[0] = mk(0.0, T{});
+#pragma unroll
+    for (int v = 1; v < 4; ++v) V[v] = c * (R.U[v] * R.ir - L.U[v] * L.ir);
+}
+
 template <class T>
 JF_D void visc2(const T UL[4], const T UR[4], T coef, T V[4]) {
     const T irL = mk(1.0, T{}) / UL[0], irR = mk(1.0, T{}) / UR[0];
@@ -446,7 +455,10 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     typedef typename SOf<T>::type S;
     constexpr int TX = FV_TX;
     __shared__ PowTab spt;
+    // the tile's cells and a one-cell halo as face sides: state, 1/rho, p, c
+    // (one pressure / sound speed per cell instead of one per face and side)
     __shared__ T sU[4][TZ + 2][TX + 2];
+    __shared__ T sIr[TZ + 2][TX + 2], sP[TZ + 2][TX + 2], sC[TZ + 2][TX + 2];
     __shared__ S sGx[4][TZ][TX + 1];   // net flux H - V through the west face of local cell (i, j)
     __shared__ S sGz[4][TZ + 1][TX];   // ... through the south face
     __shared__ S sD[MODE == FV_DEFRES ? 4 : 1][MODE == FV_DEFRES ? TZ : 1][MODE == FV_DEFRES ? TX : 1];
@@ -475,6 +487,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         up0 = (S)oval(ld(0, c, I, J));
         if (MODE == FV_SMOOTH) dtc = dtau[c];
     }
+    if (IN < 2) __syncthreads();   // the power table
     for (int idx = threadIdx.x; idx < (TZ + 2) * (TX + 2); idx += blockDim.x) {
         const int li = idx % (TX + 2), lj = idx / (TX + 2);
         int I = I0 + li - 1;
@@ -482,11 +495,26 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         if (K.periodic) I = I < 0 ? I + NX : (I >= NX ? I - NX : I);
         if (I >= 0 && I < NX && J >= 0 && J < NZ) {
             const size_t c = (size_t)J * NX + I;
+            T U[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) sU[v][lj][li] = ld(v, c, I, J) + bgs<T>(K.ub, K.ubf, v * NZ + J);
+            for (int v = 0; v < 4; ++v) U[v] = ld(v, c, I, J) + bgs<T>(K.ub, K.ubf, v * NZ + J);
+            Side<T> sd;
+            side_of(U, K.pc, &spt, sd);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sU[v][lj][li] = sd.U[v];
+            sIr[lj][li] = sd.ir;
+            sP[lj][li] = sd.p;
+            sC[lj][li] = sd.c;
         }
     }
     __syncthreads();
+    auto side_at = [&](int lj, int li, Side<T> &sd) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sd.U[v] = sU[v][lj][li];
+        sd.ir = sIr[lj][li];
+        sd.p = sP[lj][li];
+        sd.c = sC[lj][li];
+    };
     const bool sub = (IN < 2);
     const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
     // x face west of local cell (i, j): global face index I0 + i in [0, NX]
@@ -494,18 +522,27 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         const int If = I0 + i, J = J0 + j;
         if (If > NX || J >= NZ) return;
         const bool wl = !K.periodic && If == 0, wr = !K.periodic && If == NX;
-        T UL[4], UR[4], H[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            UL[v] = sU[v][j + 1][i];
-            UR[v] = sU[v][j + 1][i + 1];
+        Side<T> L, R;
+        T H[4];
+        if (wl) {
+            side_at(j + 1, i + 1, R);
+            mirror_side<T, 0>(R, L);
+        } else if (wr) {
+            side_at(j + 1, i, L);
+            mirror_side<T, 0>(L, R);
+        } else {
+            side_at(j + 1, i, L);
+            side_at(j + 1, i + 1, R);
         }
-        if (wl) { for (int v = 0; v < 4; ++v) UL[v] = UR[v]; }
-        if (wr) { for (int v = 0; v < 4; ++v) UR[v] = UL[v]; }
-        face_flux<T, 0>(UL, UR, wl, wr, wl ? K.hbxw : (wr ? K.hbxw + 4 * NZ : K.hbx), NZ, J, sub, K, &spt, H);
+        hllc_s<T, 0>(L, R, H);
+        if (sub) {
+            const double *hb = wl ? K.hbxw : (wr ? K.hbxw + 4 * NZ : K.hbx);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * NZ + J], T{});
+        }
         if (VISC && !wl && !wr) {
             T V[4];
-            visc2(UL, UR, cx, V);
+            visc2_s(L, R, cx, V);
 #pragma unroll
             for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
         }
@@ -517,18 +554,26 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         const int I = I0 + i, Jf = J0 + j;
         if (I >= NX || Jf > NZ) return;
         const bool wl = Jf == 0, wr = Jf == NZ;
-        T UB[4], UT[4], H[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            UB[v] = sU[v][j][i + 1];
-            UT[v] = sU[v][j + 1][i + 1];
+        Side<T> B, Tp;
+        T H[4];
+        if (wl) {
+            side_at(j + 1, i + 1, Tp);
+            mirror_side<T, 1>(Tp, B);
+        } else if (wr) {
+            side_at(j, i + 1, B);
+            mirror_side<T, 1>(B, Tp);
+        } else {
+            side_at(j, i + 1, B);
+            side_at(j + 1, i + 1, Tp);
         }
-        if (wl) { for (int v = 0; v < 4; ++v) UB[v] = UT[v]; }
-        if (wr) { for (int v = 0; v < 4; ++v) UT[v] = UB[v]; }
-        face_flux<T, 1>(UB, UT, wl, wr, K.hbz, NZ + 1, Jf, sub, K, &spt, H);
+        hllc_s<T, 1>(B, Tp, H);
+        if (sub) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(K.hbz[v * (NZ + 1) + Jf], T{});
+        }
         if (VISC && !wl && !wr) {
             T V[4];
-            visc2(UB, UT, cz, V);
+            visc2_s(B, Tp, cz, V);
 #pragma unroll
             for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
         }
@@ -1377,6 +1422,20 @@ int dg_defect<float>(jfnk_ctx *c, const float *r, const float *z, float *d, cuda
     return dg_apply(c, DG_TLJV, a, s);
 }
 
+// FP32: one DG pre-smoothing step from zero (z = dtau_E r) and the defect
+// d = r - G'z in one launch; writes z and d
+int dg_first_step_defect32(jfnk_ctx *c, const float *r, float *z, float *d, cudaStream_t s) {
+    DGArgs a = {};
+    a.U = c->mg_U;
+    a.Uf = c->Usf;
+    a.rf = r;
+    a.dtauf = c->dtau_dgf;
+    a.adt = c->mg_adt;
+    a.out0 = d;
+    a.out1f = z;
+    return dg_apply(c, DG_TLJV, a, s);
+}
+
 template <class S>
 int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     // restore the level double-buffer order at the end so that every
@@ -1388,11 +1447,17 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     }
     S *z = (S *)c->pz, *z2 = (S *)c->pz2;
     bool zero = true;
-    for (int i = 0; i < c->dg_pre; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
     const S *d = r;
-    if (!zero) {
-        JF_RET(dg_defect<S>(c, r, z, (S *)c->pd, s));
+    if (sizeof(S) == 4 && c->dg_pre == 1 && c->opts.dg_fused != 2) {
+        JF_RET(dg_first_step_defect32(c, (const float *)r, (float *)z, (float *)c->pd, s));
+        zero = false;
         d = (const S *)c->pd;
+    } else {
+        for (int i = 0; i < c->dg_pre; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+        if (!zero) {
+            JF_RET(dg_defect<S>(c, r, z, (S *)c->pd, s));
+            d = (const S *)c->pd;
+        }
     }
     const bool fuse0 = c->fine_pre >= 1;
     JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s, fuse0 ? (S *)c->lev[0].x : nullptr, (const S *)c->lev[0].dtau));

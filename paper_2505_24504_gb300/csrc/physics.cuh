@@ -35,6 +35,32 @@ JF_D void flux_c(const T U[4], T un, T p, T F[4]) {
     F[1 + D] = F[1 + D] + p;
 }
 
+// One side of a face: the conserved state and the quantities every face of that
+// cell needs, 1/rho, p and the sound speed c = sqrt(gamma p / rho).  Cell-based
+// kernels compute them once per cell instead of once per face.
+template <class T>
+struct Side {
+    T U[4];
+    T ir, p, c;
+};
+
+template <class T>
+JF_D void side_of(const T U[4], const PhysC &P, const PowTab *pt, Side<T> &S) {
+    const T gam = mkc(P.gamma, P.gammaf, T{});
+#pragma unroll
+    for (int v = 0; v < 4; ++v) S.U[v] = U[v];
+    S.ir = mk(1.0, T{}) / U[0];
+    S.p = pressure(U[3], P, pt);
+    S.c = jsqrt(gam * S.p * S.ir);
+}
+
+// slip-wall ghost of a side: normal momentum reversed, rho, p and c unchanged
+template <class T, int D>
+JF_D void mirror_side(const Side<T> &A, Side<T> &G) {
+    G = A;
+    G.U[1 + D] = -A.U[1 + D];
+}
+
 // HLLC flux in direction e_D, normal from L to R.  Davis wave speeds
 // S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R), c^2 = gamma p / rho;
 // contact speed S*; star states rho*_K = rho_K (S_K - u_K)/(S_K - S*) with normal
@@ -42,27 +68,25 @@ JF_D void flux_c(const T U[4], T un, T p, T F[4]) {
 // Branches 0 <= S_L: F_L; 0 <= S*: F*_L; 0 <= S_R: F*_R; else F_R.  Only the side
 // the branch selects is evaluated.
 template <class T, int D>
-JF_D void hllc(const T UL[4], const T UR[4], const PhysC &P, const PowTab *pt, T H[4]) {
+JF_D void hllc_s(const Side<T> &L, const Side<T> &R, T H[4]) {
     constexpr int iN = 1 + D, iT = 2 - D;
-    const T one = mk(1.0, T{});
-    const T gam = mkc(P.gamma, P.gammaf, T{});
-    const T irL = one / UL[0], irR = one / UR[0];
-    const T uL = UL[iN] * irL, uR = UR[iN] * irR;
-    const T pL = pressure(UL[3], P, pt), pR = pressure(UR[3], P, pt);
-    const T cL = jsqrt(gam * pL * irL), cR = jsqrt(gam * pR * irR);
+    const T irL = L.ir, irR = R.ir;
+    const T uL = L.U[iN] * irL, uR = R.U[iN] * irR;
+    const T pL = L.p, pR = R.p;
+    const T cL = L.c, cR = R.c;
     const T a1 = uL - cL, a2 = uR - cR;
     const T SL = sel(val(a1) <= val(a2), a1, a2);
     const T b1 = uL + cL, b2 = uR + cR;
     const T SR = sel(val(b1) >= val(b2), b1, b2);
     const T dL = SL - uL, dR = SR - uR;
-    const T num = (pR - pL) + UL[0] * uL * dL - UR[0] * uR * dR;
-    const T den = UL[0] * dL - UR[0] * dR;
+    const T num = (pR - pL) + L.U[0] * uL * dL - R.U[0] * uR * dR;
+    const T den = L.U[0] * dL - R.U[0] * dR;
     const T Sst = num / den;
     const bool left = val(Sst) >= 0 || val(SL) >= 0;   // integer 0: compared in the scalar's own precision
     const bool pure = val(SL) >= 0 || (!left && val(SR) < 0);
     T U[4], F[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) U[v] = sel(left, UL[v], UR[v]);
+    for (int v = 0; v < 4; ++v) U[v] = sel(left, L.U[v], R.U[v]);
     const T un = sel(left, uL, uR);
     const T ir = sel(left, irL, irR);
     flux_c<T, D>(U, un, sel(left, pL, pR), F);
@@ -80,6 +104,14 @@ JF_D void hllc(const T UL[4], const T UR[4], const PhysC &P, const PowTab *pt, T
     Us[3] = fac * (U[3] * ir);
 #pragma unroll
     for (int v = 0; v < 4; ++v) H[v] = F[v] + S * (Us[v] - U[v]);
+}
+
+template <class T, int D>
+JF_D void hllc(const T UL[4], const T UR[4], const PhysC &P, const PowTab *pt, T H[4]) {
+    Side<T> L, R;
+    side_of(UL, P, pt, L);
+    side_of(UR, P, pt, R);
+    hllc_s<T, D>(L, R, H);
 }
 
 // Slip-wall ghost: normal momentum reversed.

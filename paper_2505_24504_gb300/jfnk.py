@@ -40,7 +40,7 @@ class Opts(C.Structure):
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
                 ("tile_fv", C.c_int), ("fv_split_cells", C.c_int), ("profile", C.c_int),
-                ("precond_fd_eps", C.c_double), ("time_budget_ms", C.c_double)]
+                ("precond_fd_eps", C.c_double), ("time_budget_ms", C.c_double), ("dg_fused", C.c_int)]
 
     @classmethod
     def defaults(cls, **kw):

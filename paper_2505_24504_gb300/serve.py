@@ -229,3 +229,43 @@ class Server:
                 c.close()
             self._ctx.clear()
             self._bytes = 0
+
+
+# ---- member-sharded serving over several GPUs ---------------------------------
+# States are independent, so N GPUs serve N disjoint partitions of them: rank r
+# owns every state id with sid % world == r and serves only the requests for
+# those states, each rank with its own Server on its own device.  Nothing is
+# exchanged on the data path; the ranks meet once at the end to pool their
+# latency records for the report.
+
+def shard_states(states: dict, rank: int, world: int) -> dict:
+    """The states rank `rank` of `world` owns (sid % world == rank)."""
+    return {sid: st for sid, st in states.items() if sid % world == rank}
+
+
+def shard_requests(arrivals, rank: int, world: int):
+    """The requests for the states rank `rank` owns, arrival times unchanged."""
+    return [(t, sid) for (t, sid) in arrivals if sid % world == rank]
+
+
+def pooled_summary(report: "Report", dist=None) -> dict:
+    """Whole-job summary over all ranks: every rank's latencies pooled (one
+    all_gather_object at the end, outside the data path), steps/s = all requests
+    over the longest rank's wall time.  With dist None: this rank alone."""
+    lat = [r.end - r.arrival for r in report.records]
+    failed = sum(1 for r in report.records if r.status != 0)
+    parts = [(lat, report.wall_s, failed)]
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        parts = [None] * dist.get_world_size()
+        dist.all_gather_object(parts, (lat, report.wall_s, failed))
+    allat = sorted(x for p in parts for x in p[0])
+    wall = max(p[1] for p in parts)
+
+    def pct(q):
+        if not allat:
+            return 0.0
+        return allat[min(len(allat) - 1, max(0, int(round(q / 100.0 * (len(allat) - 1)))))]
+
+    return {"requests": len(allat), "steps_per_s": len(allat) / wall if wall > 0 else 0.0,
+            "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "wall_s": wall,
+            "failed": sum(p[2] for p in parts), "ranks": len(parts)}

@@ -29,7 +29,7 @@ def test_gmres_cap_gives_enotconv_and_restores_the_state(prec):
     U = to_gpu(U0)
     st = ctx.implicit_step(U, w.dt, scheme=1, raise_on_error=False)
     assert st.status == JFNK_ENOTCONV
-    assert np.array_equal(to_cpu(U), U0.ravel())
+    assert np.array_equal(to_cpu(U).ravel(), U0.ravel())
     # the context stays usable: the same state steps normally afterwards
     ok = gpu_context(w, precond_prec=prec)
     st2 = ok.implicit_step(U, w.dt, scheme=1, raise_on_error=False)
@@ -42,7 +42,7 @@ def test_time_budget_gives_etimeout_and_restores_the_state():
     U = to_gpu(U0)
     st = ctx.implicit_step(U, w.dt, scheme=1, raise_on_error=False)
     assert st.status == JFNK_ETIMEOUT
-    assert np.array_equal(to_cpu(U), U0.ravel())
+    assert np.array_equal(to_cpu(U).ravel(), U0.ravel())
     roomy = gpu_context(w, time_budget_ms=60_000.0)
     st2 = roomy.implicit_step(U, w.dt, scheme=1, raise_on_error=False)
     assert st2.status == 0
@@ -68,7 +68,7 @@ def test_nan_in_one_batch_member_fails_only_that_member():
     ctxs = [gpu_context(m, precond_prec=32) for m in ms]
     batch = P.Batch(ctxs, max_threads=3)
     Us = [to_gpu(u) for u in U0]
-    Us[1][17] = float("nan")
+    Us[1].view(-1)[17] = float("nan")
     bad = to_cpu(Us[1])
     status, stats = batch.jfnk_batch_step(Us, [m.dt for m in ms], [1, 1, 1], raise_on_error=False)
     torch.cuda.synchronize()

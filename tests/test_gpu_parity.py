@@ -456,3 +456,30 @@ def test_fv_lane_split_same_answer(prec):
         assert st.status == 0
         outs.append(to_cpu(U))
     assert np.linalg.norm(outs[0] - outs[1]) <= 1e-6 * np.linalg.norm(outs[0] - U0)
+
+
+@pytest.mark.parametrize("name", ["q3-11x6", "visc-q2-24x6", "q1-9x5", "q4-7x5", "q3-periodic"])
+def test_fused_and_two_launch_tangent_products_same_answer(name):
+    # the FP32 tangent DG product as one fused launch per element strip or as a
+    # face launch plus a volume launch: the same preconditioner up to FP32
+    # rounding, so the same converged step
+    w = _cases()[name]
+    dg = oracle_dg(w)
+    U0 = initial_state(w, dg)
+    outs = []
+    for fused in (1, 2):
+        ctx = gpu_context(w, precond_prec=32, dg_fused=fused)
+        U = to_gpu(U0)
+        st = ctx.implicit_step(U, w.dt, scheme=1)
+        assert st.status == 0
+        outs.append(to_cpu(U))
+    assert np.linalg.norm(outs[0] - outs[1]) <= 1e-6 * np.linalg.norm(outs[0] - U0)
+    # and one product against the other directly
+    ctxs = [gpu_context(w, precond_prec=32, dg_fused=f) for f in (1, 2)]
+    Up = to_gpu(perturbed_state(w, dg, seed=5))
+    y = to_gpu(synth.random_perturbation(dg.shape[1:], 6))
+    res = []
+    for c in ctxs:
+        ms = c.time_operator(2, Up, y, 1)     # one FP32 tangent product z - adt J z into the workspace
+        res.append(ms)
+    assert all(m[0] > 0 for m in res)
