@@ -15,8 +15,10 @@
 * MG_l(x, b; u): pre-smooth, restrict the residual R(g'x - b), recurse once (V)
   or twice (W) from v = 0 on the restricted state R u, correct x -= P v,
   post-smooth; zero-initial-guess flag skips products with x = 0 (Sec. 3.4).
-* Smoother: explicit Euler in pseudo time for dw/dtau = -(g'(u) w - b) with the
-  local step dtau = sigma / (1 + alpha dt lambda_c) (Sec. 3.5).
+* Smoother: explicit Runge-Kutta in pseudo time for dw/dtau = -(g'(u) w - b) with
+  the local step dtau = sigma / (1 + alpha dt lambda_c) (Sec. 3.5), in the
+  low-storage form w_k = w_0 + a_k dtau (b - g'(u) w_{k-1}), k = 1..s; the
+  default s = 1, a_1 = 1 is the explicit Euler smoother of the paper's runs.
 * g'(u) x by the finite difference of Sec. 3.1 applied to g(u) = u - alpha dt
   f_low(u) - ubar_s, with eps = sqrt(eps_mach)/|x| over the level's vector
   (`fd_eps` replaces the numerator sqrt(eps_mach) for the preconditioner's FD
@@ -212,7 +214,7 @@ class Multigrid:
     """Q^-1 = T^-1 q^-1 T with DG pre/post smoothing (Sec. 3.2-3.5)."""
 
     def __init__(self, dg: DG, levels: int, mg_key="mg111111V", sigma_fv=1.0, sigma_dg=1.0,
-                 massfix=True, l2=False, fd_eps=None):
+                 massfix=True, l2=False, fd_eps=None, rk_alpha=(1.0,)):
         self.dg = dg
         self.key = parse_mg_key(mg_key)
         sizes, facs = hierarchy(dg.nx, dg.nz, dg.k, levels)
@@ -224,6 +226,8 @@ class Multigrid:
         self.massfix = massfix
         # numerator of eps = c / |x| in the preconditioner's FD products (Sec. 3.1: c = sqrt(eps_mach))
         self.fd_c = np.sqrt(EPS_MACH) if fd_eps is None else float(fd_eps)
+        # stage coefficients a_1..a_s of the pseudo-time smoother (Sec. 3.5)
+        self.rk_alpha = tuple(float(a) for a in rk_alpha)
         self.stats = dict(dg_calls=0, fv_calls=[0] * len(sizes), visits=[0] * len(sizes))
 
     # -- linearisation at the Newton iterate U^k ----------------------------
@@ -251,14 +255,25 @@ class Multigrid:
         self.stats['fv_calls'][l] += 1
         return x - self.alpha_dt * (self.levels[l].rhs(self.u[l] + eps * x) - self.fu[l]) / eps
 
-    def smooth(self, l, x, b, zero, steps):
-        """Explicit-Euler pseudo-time steps x <- x + dtau (b - g'x)."""
-        for _ in range(steps):
-            if zero:
-                x = self.dtau[l][None] * b
-                zero = False
+    def rk_step(self, x, zero, dtau, b, gprime):
+        """One pseudo-time step of the low-storage explicit RK smoother:
+        x_k = x_0 + a_k dtau (b - g' x_{k-1}), k = 1..s, from x_0 = x (x_0 = 0 when
+        `zero`, whose first stage needs no product).  s = 1, a_1 = 1: explicit Euler."""
+        x0, xk = x, x
+        for k, a in enumerate(self.rk_alpha):
+            if zero and k == 0:
+                xk = (a * dtau) * b
+            elif zero:
+                xk = (a * dtau) * (b - gprime(xk))
             else:
-                x = x + self.dtau[l][None] * (b - self.gprime(l, x))
+                xk = x0 + (a * dtau) * (b - gprime(xk))
+        return xk
+
+    def smooth(self, l, x, b, zero, steps):
+        """Pseudo-time smoothing steps on FV level l (explicit Euler by default)."""
+        for _ in range(steps):
+            x = self.rk_step(x, zero, self.dtau[l][None], b, lambda v: self.gprime(l, v))
+            zero = False
         return x, zero
 
     def mg(self, l, x, b, zero):
@@ -300,15 +315,12 @@ class Multigrid:
         z = np.zeros_like(r)
         zero = True
         for _ in range(self.key['dg_pre']):
-            if zero:
-                z = dtau * r
-                zero = False
-            else:
-                z = z + dtau * (r - self.dg_gprime(z))
+            z = self.rk_step(z, zero, dtau, r, self.dg_gprime)
+            zero = False
         d = r if zero else r - self.dg_gprime(z)
         b = self.T.to_fv(d, self.massfix)
         x = self.mg(0, np.zeros_like(b), b, True)
         z = z + self.T.to_dg(x, self.massfix)
         for _ in range(self.key['dg_post']):
-            z = z + dtau * (r - self.dg_gprime(z))
+            z = self.rk_step(z, False, dtau, r, self.dg_gprime)
         return z

@@ -293,3 +293,32 @@ def test_w_cycle_converges_at_least_as_fast_as_v_per_cycle():
     rv, rw = hist["mg001111V"], hist["mg001111W"]
     assert all(r1 < r0 for r0, r1 in zip(rw, rw[1:]))
     assert rw[-1] <= rv[-1] * 1.000001
+
+
+# ---- pin of the multi-stage pseudo-time smoother (Sec. 3.5) ----
+
+@pytest.mark.parametrize("alpha,coef", [
+    ((1.0,), [1, 1]),                                            # explicit Euler: R(z) = 1 + z
+    ((0.25, 1 / 3, 0.5, 1.0), [1, 1, 1 / 2, 1 / 6, 1 / 24]),     # Jameson-Schmidt-Turkel 4 stages
+    ((0.5, 1.0), [1, 1, 1 / 2]),                                 # 2 stages: R(z) = 1 + z + z^2/2
+])
+def test_rk_smoother_amplification_is_the_stability_polynomial(alpha, coef):
+    # on a linear system A x = b the low-storage scheme x_k = x_0 + a_k dtau (b - A x_{k-1})
+    # maps the error e_0 = x_0 - x* to R(-dtau A) e_0, R the stability polynomial fixed
+    # by the stage coefficients (a_s ... a_{s-j+1} for the z^j term); from x_0 = 0 the same
+    # holds with e_0 = -x*
+    rng = np.random.default_rng(3)
+    n = 6
+    A = rng.standard_normal((n, n)) + 4.0 * np.eye(n)
+    b = rng.standard_normal(n)
+    xs = np.linalg.solve(A, b)
+    dtau = 0.07 + 0.02 * rng.random(n)          # a local step per unknown, as per cell
+    mg = Multigrid.__new__(Multigrid)
+    mg.rk_alpha = alpha
+    Z = -dtau[:, None] * A
+    R = sum(c * np.linalg.matrix_power(Z, j) for j, c in enumerate(coef))
+    x0 = rng.standard_normal(n)
+    got = mg.rk_step(x0, False, dtau, b, lambda v: A @ v)
+    np.testing.assert_allclose(got - xs, R @ (x0 - xs), rtol=1e-12, atol=1e-13)
+    got0 = mg.rk_step(np.zeros(n), True, dtau, b, lambda v: A @ v)
+    np.testing.assert_allclose(got0 - xs, R @ (-xs), rtol=1e-12, atol=1e-13)
