@@ -131,6 +131,12 @@ typedef struct {
     int dg_fused;        /* FP32 tangent DG products of the preconditioner: 0 or 1 one fused
                             launch per product (faces, volume and epilogue per element strip),
                             2 a face launch and a volume launch */
+    int rk_stages;       /* stages s of the pseudo-time smoother (Sec. 3.5), 1..4 (0: 1) */
+    double rk_alpha[4];  /* its low-storage coefficients: one smoothing step is
+                            w_k = w_0 + rk_alpha[k-1] dtau (b - g'w_{k-1}), k = 1..s; the
+                            default s = 1, rk_alpha[0] = 1 is the paper's explicit Euler;
+                            e.g. s = 4, (1/4, 1/3, 1/2, 1) is Jameson, Schmidt and Turkel's
+                            four-stage scheme (AIAA 81-1259, 1981) */
 } jfnk_opts;
 
 /* Counters of one implicit_step (Sec. 4.2 counts linear iterations and

@@ -196,6 +196,8 @@ void jfnk_default_opts(jfnk_opts *o) {
     o->tile_volume = 2;
     o->tile_fv = 128;
     o->fv_split_cells = 0;
+    o->rk_stages = 1;
+    o->rk_alpha[0] = 1.0;
 }
 
 const char *jfnk_strerror(int code) {
@@ -260,6 +262,13 @@ static int create_locked(const jfnk_grid *g, int k, const jfnk_physics *ph, cons
     if (o.precond_prec != 64 && o.precond_prec != 32 && o.precond_prec != 16) return JFNK_EINVAL;
     if (!(o.precond_fd_eps >= 0.0) || !(o.time_budget_ms >= 0.0)) return JFNK_EINVAL;
     if (o.dg_fused < 0 || o.dg_fused > 2) return JFNK_EINVAL;
+    if (o.rk_stages == 0) {   // zero-filled options: the explicit Euler smoother
+        o.rk_stages = 1;
+        o.rk_alpha[0] = 1.0;
+    }
+    if (o.rk_stages < 1 || o.rk_stages > 4) return JFNK_EINVAL;
+    for (int k = 0; k < o.rk_stages; ++k)
+        if (!(o.rk_alpha[k] > 0.0)) return JFNK_EINVAL;
     if (o.fv_levels < 1) o.fv_levels = 1;
     if (o.tile_faces == 0) o.tile_faces = 128;
     if (o.tile_volume == 0) o.tile_volume = 2;

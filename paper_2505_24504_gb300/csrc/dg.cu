@@ -72,9 +72,8 @@ __device__ __forceinline__ void load_powtab(PowTab *s, const PowTab *g) {
 }
 
 // background values: FP64 tables for D64, FP32 copies for TL32
-template <class T> JF_D T bgs(const double *d, const float *f, size_t i);
-template <> JF_D D64 bgs<D64>(const double *d, const float *, size_t i) { return D64{d[i]}; }
-template <> JF_D TL32 bgs<TL32>(const double *, const float *f, size_t i) { return TL32{f[i], 0.0f}; }
+JF_D D64 bgs(const double *d, const float *, size_t i, D64) { return D64{d[i]}; }
+JF_D TLc bgs(const double *, const float *f, size_t i, TL32) { return TLc{f[i]}; }
 template <class T>
 JF_D T bg(const double *a, size_t i) { return mk(a[i], T{}); }
 
@@ -132,7 +131,7 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
     const long long t = (long long)blk * blockDim.x + threadIdx.x;
     if (t >= nvert + nhorz) return;
     const T zero = mk(0.0, T{});
-    const T half = mk(0.5, T{});
+    const auto half = mkc(0.5, 0.5f, T{});
     T H[4], Phi[4], sL[3], sR[3];
     if (t < nvert) {
         const int s = (int)(t % NP1);
@@ -191,8 +190,8 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
         T UL[4], UR[4], Gh[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            UL[v] = trL[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
-            UR[v] = trR[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
+            UL[v] = trL[v] + bgs(K.ubv, K.ubvf, v * nrow + J, T{});
+            UR[v] = trR[v] + bgs(K.ubv, K.ubvf, v * nrow + J, T{});
         }
         if (wallL) {
             mirror<T, 0>(UR, Gh);
@@ -280,14 +279,14 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
             }
             trB[v] = aB;
             trT[v] = aT;
-            gB[v] = mkc(K.two_hz, K.two_hzf, T{}) * dB + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
-            gT[v] = mkc(K.two_hz, K.two_hzf, T{}) * dT + bgs<T>(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz);
+            gB[v] = mkc(K.two_hz, K.two_hzf, T{}) * dB + bgs(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz, T{});
+            gT[v] = mkc(K.two_hz, K.two_hzf, T{}) * dT + bgs(K.dubh, K.dubhf, (size_t)v * (nz + 1) + fz, T{});
         }
         T UB[4], UT[4], Gh[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            UB[v] = trB[v] + bgs<T>(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz);
-            UT[v] = trT[v] + bgs<T>(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz);
+            UB[v] = trB[v] + bgs(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz, T{});
+            UT[v] = trT[v] + bgs(K.ubh, K.ubhf, (size_t)v * (nz + 1) + fz, T{});
         }
         if (wallB) {
             mirror<T, 1>(UT, Gh);
@@ -419,13 +418,13 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             Up[v] = ld((size_t)v * N1 + (size_t)e * NP + node);
-            U[v] = Up[v] + bgs<T>(K.ubv, K.ubvf, v * nrow + J);
+            U[v] = Up[v] + bgs(K.ubv, K.ubvf, v * nrow + J, T{});
             if (VISC) su[le][v][node] = Up[v];
         }
     }
     __syncthreads();
     if (active) {
-        const T ir = mk(1.0, T{}) / U[0];
+        const T ir = mkc(1.0, 1.0f, T{}) / U[0];
         const T p = pressure(U[3], K.pc, &spt);
         T Fx[4], Fz[4];
         flux_c<T, 0>(U, U[1] * ir, p, Fx);
@@ -444,11 +443,11 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
                 T sx = mk(0.0, T{}), sz = mk(0.0, T{});
 #pragma unroll
                 for (int q = 0; q < NP1; ++q) {
-                    sx = jfma(T{sDn[a][q]}, su[le][v][b * NP1 + q], sx);
-                    sz = jfma(T{sDn[b][q]}, su[le][v][q * NP1 + a], sz);
+                    sx = jfma(mkc((double)sDn[a][q], (float)sDn[a][q], T{}), su[le][v][b * NP1 + q], sx);
+                    sz = jfma(mkc((double)sDn[b][q], (float)sDn[b][q], T{}), su[le][v][q * NP1 + a], sz);
                 }
                 dx[v] = mkc(K.two_hx, K.two_hxf, T{}) * sx;
-                dz[v] = mkc(K.two_hz, K.two_hzf, T{}) * sz + bgs<T>(K.dubv, K.dubvf, v * nrow + J);
+                dz[v] = mkc(K.two_hz, K.two_hzf, T{}) * sz + bgs(K.dubv, K.dubvf, v * nrow + J, T{});
             }
             viscous(U, dx, K.pc, Gx);
             viscous(U, dz, K.pc, Gz);
@@ -503,7 +502,12 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
         } else if (MODE == DG_SMOOTH64) {
             const double z = A.y[gi];
             const double Jz = (eps == 0.0) ? z : fma(-ceps, (double)f - A.fU[gi], z);
-            ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
+            if (A.z0mode == 0) {
+                ((double *)A.out0)[gi] = z + A.dtau[e] * (A.r[gi] - Jz);
+            } else {
+                const double st = (A.alpha * A.dtau[e]) * (A.r[gi] - Jz);
+                ((double *)A.out0)[gi] = A.z0mode == 1 ? ((const double *)A.z0)[gi] + st : st;
+            }
         } else if (MODE == DG_TLJV) {
             const float z = (float)outv(Up[v]);   // the loader's tangent input is y
             const float jz = z - adtf * (float)f;
@@ -511,7 +515,12 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
         } else {  // DG_TLSMOOTH
             const float z = (float)outv(Up[v]);
             const float Jz = z - adtf * (float)f;
-            ((float *)A.out0)[gi] = z + edt * (ef[v] - Jz);
+            if (A.z0mode == 0) {
+                ((float *)A.out0)[gi] = z + edt * (ef[v] - Jz);
+            } else {
+                const float st = ((float)A.alpha * edt) * (ef[v] - Jz);
+                ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
+            }
         }
     }
 }
@@ -612,9 +621,9 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             Up[v] = sn[1][le][v][node];
-            U[v] = Up[v] + TL32{K.ubvf[v * nrow + J], 0.0f};
+            U[v] = Up[v] + TLc{K.ubvf[v * nrow + J]};
         }
-        const TL32 ir = mk(1.0, TL32{}) / U[0];
+        const TL32 ir = TLc{1.0f} / U[0];
         const TL32 p = pressure(U[3], K.pc, nullptr);
         TL32 Fx[4], Fz[4];
         flux_c<TL32, 0>(U, U[1] * ir, p, Fx);
@@ -626,11 +635,11 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
                 TL32 sx = mk(0.0, TL32{}), sz = mk(0.0, TL32{});
 #pragma unroll
                 for (int q = 0; q < NP1; ++q) {
-                    sx = jfma(TL32{sDn[a][q], 0.0f}, sn[1][le][v][b * NP1 + q], sx);
-                    sz = jfma(TL32{sDn[b][q], 0.0f}, sn[1][le][v][q * NP1 + a], sz);
+                    sx = jfma(TLc{sDn[a][q]}, sn[1][le][v][b * NP1 + q], sx);
+                    sz = jfma(TLc{sDn[b][q]}, sn[1][le][v][q * NP1 + a], sz);
                 }
-                dx[v] = TL32{K.two_hxf, 0.0f} * sx;
-                dz[v] = TL32{K.two_hzf, 0.0f} * sz + TL32{K.dubvf[v * nrow + J], 0.0f};
+                dx[v] = TLc{K.two_hxf} * sx;
+                dz[v] = TLc{K.two_hzf} * sz + TLc{K.dubvf[v * nrow + J]};
             }
             viscous(U, dx, K.pc, Gx);
             viscous(U, dz, K.pc, Gz);
@@ -656,11 +665,11 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
 #pragma unroll
         for (int q = 0; q < NP1; ++q) {
             const TL32 u = src[v][i0 + q * st];
-            tv = jfma(TL32{pa[q], 0.0f}, u, tv);
-            if (VISC) td = jfma(TL32{pd[q], 0.0f}, u, td);
+            tv = jfma(TLc{pa[q]}, u, tv);
+            if (VISC) td = jfma(TLc{pd[q]}, u, td);
         }
     };
-    const TL32 half = mk(0.5, TL32{});
+    const TLc half = TLc{0.5f};
     const int nxf = (Ev + 1) * NP1, nzf = 2 * Ev * NP1;
     for (int t = threadIdx.x; t < nxf + nzf; t += blockDim.x) {
         TL32 trL[4], trR[4], gL[4], gR[4], UL[4], UR[4], H[4], Phi[4], sLv[3], sRv[3];
@@ -679,10 +688,10 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
                 if (wallR) { aR = aL; dR = dL; }
                 trL[v] = aL;
                 trR[v] = aR;
-                gL[v] = TL32{K.two_hxf, 0.0f} * dL;
-                gR[v] = TL32{K.two_hxf, 0.0f} * dR;
-                UL[v] = aL + TL32{K.ubvf[v * nrow + J], 0.0f};
-                UR[v] = aR + TL32{K.ubvf[v * nrow + J], 0.0f};
+                gL[v] = TLc{K.two_hxf} * dL;
+                gR[v] = TLc{K.two_hxf} * dR;
+                UL[v] = aL + TLc{K.ubvf[v * nrow + J]};
+                UR[v] = aR + TLc{K.ubvf[v * nrow + J]};
             }
             TL32 Gh[4];
             if (wallL) {
@@ -703,7 +712,7 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
 #pragma unroll
                 for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
 #pragma unroll
-                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TL32{K.eta_xf, 0.0f} * Jp[v];
+                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TLc{K.eta_xf} * Jp[v];
                 TL32 AL[4], AR[4];
                 viscous(UL, Jp, K.pc, AL);
                 viscous(UR, Jp, K.pc, AR);
@@ -745,11 +754,11 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
                 }
                 trL[v] = aB;
                 trR[v] = aT;
-                const TL32 dub = TL32{K.dubhf[(size_t)v * (nz + 1) + fz], 0.0f};
-                gB[v] = TL32{K.two_hzf, 0.0f} * dB + dub;
-                gT[v] = TL32{K.two_hzf, 0.0f} * dT + dub;
-                UL[v] = aB + TL32{K.ubhf[(size_t)v * (nz + 1) + fz], 0.0f};
-                UR[v] = aT + TL32{K.ubhf[(size_t)v * (nz + 1) + fz], 0.0f};
+                const TLc dub = TLc{K.dubhf[(size_t)v * (nz + 1) + fz]};
+                gB[v] = TLc{K.two_hzf} * dB + dub;
+                gT[v] = TLc{K.two_hzf} * dT + dub;
+                UL[v] = aB + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
+                UR[v] = aT + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
             }
             TL32 Gh[4];
             if (wallB) {
@@ -770,7 +779,7 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
 #pragma unroll
                 for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
 #pragma unroll
-                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TL32{K.eta_zf, 0.0f} * Jp[v];
+                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TLc{K.eta_zf} * Jp[v];
                 TL32 AB[4], AT[4];
                 viscous(UL, Jp, K.pc, AB);
                 viscous(UR, Jp, K.pc, AT);
@@ -826,7 +835,12 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
             ((float *)A.out0)[gi] = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
             if (FIRST) out1f[gi] = z;
         } else {  // DG_TLSMOOTH
-            ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
+            if (A.z0mode == 0) {
+                ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
+            } else {
+                const float st = ((float)A.alpha * edt) * (ef[v] - jz);
+                ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
+            }
         }
     }
 }

@@ -212,6 +212,12 @@ struct DGArgs {
     const double *tr_in;   // FP64 FD product: face traces of U from the residual at U (may be null)
     float *out1f;          // FP32 defect at the first step from zero: z = dtau r is formed from rf and
                            // dtauf on the fly (yf unused) and written here
+    // smoothing modes, one stage of the multi-stage pseudo-time scheme: z0mode 0 explicit
+    // Euler z + dtau (r - G'z); 1 z0 + alpha dtau (r - G'z) (z the previous stage); 2 the
+    // same with z0 = 0
+    const void *z0;
+    int z0mode;
+    double alpha;
 };
 
 int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);

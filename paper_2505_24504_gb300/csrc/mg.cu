@@ -35,9 +35,24 @@ struct FVK {
     const float *ubf;
 };
 
-template <class T> JF_D T bgs(const double *d, const float *f, size_t i);
-template <> JF_D D64 bgs<D64>(const double *d, const float *, size_t i) { return D64{d[i]}; }
-template <> JF_D TL32 bgs<TL32>(const double *, const float *f, size_t i) { return TL32{f[i], 0.0f}; }
+// One stage of the pseudo-time smoother (Sec. 3.5) in the FV smoothing kernels:
+// mode 0 explicit Euler x + dtau (b - g'x); mode 1 x0 + alpha dtau (b - g'x) (a
+// stage of the low-storage multi-stage scheme, x the previous stage); mode 2 the
+// same with x0 = 0.
+struct RKS {
+    const void *x0;
+    int mode;
+    double alpha;
+};
+template <class S>
+JF_D S rk_stage(const RKS &rk, S x, S dt, S bmg, size_t gi) {
+    if (rk.mode == 0) return x + dt * bmg;
+    const S st = ((S)rk.alpha * dt) * bmg;
+    return rk.mode == 1 ? ((const S *)rk.x0)[gi] + st : st;
+}
+
+JF_D D64 bgs(const double *d, const float *, size_t i, D64) { return D64{d[i]}; }
+JF_D TLc bgs(const double *, const float *f, size_t i, TL32) { return TLc{f[i]}; }
 
 __device__ __forceinline__ void load_pt(PowTab *s, const PowTab *g) {
     const double *src = reinterpret_cast<const double *>(g);
@@ -129,17 +144,17 @@ JF_D void face_flux(const T UL[4], const T UR[4], bool wallL, bool wallR, const 
 }
 
 // the same two-point flux from precomputed sides (1/rho of each side reused)
-template <class T>
-JF_D void visc2_s(const Side<T> &L, const Side<T> &R, T coef, T V[4]) {
+template <class T, class C>
+JF_D void visc2_s(const Side<T> &L, const Side<T> &R, C coef, T V[4]) {
     const T c = coef * (L.U[0] + R.U[0]);
     V[0] = mk(0.0, T{});
 #pragma unroll
     for (int v = 1; v < 4; ++v) V[v] = c * (R.U[v] * R.ir - L.U[v] * L.ir);
 }
 
-template <class T>
-JF_D void visc2(const T UL[4], const T UR[4], T coef, T V[4]) {
-    const T irL = mk(1.0, T{}) / UL[0], irR = mk(1.0, T{}) / UR[0];
+template <class T, class C>
+JF_D void visc2(const T UL[4], const T UR[4], C coef, T V[4]) {
+    const T irL = mkc(1.0, 1.0f, T{}) / UL[0], irR = mkc(1.0, 1.0f, T{}) / UR[0];
     const T c = coef * (UL[0] + UR[0]);
     V[0] = mk(0.0, T{});
 #pragma unroll
@@ -164,20 +179,20 @@ JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, si
     if (Jz < NZ - 1) nb[3] = (Jz + 1) * NX + I;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        U[v] = ld(v, c, I, Jz) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
+        U[v] = ld(v, c, I, Jz) + bgs(K.ub, K.ubf, v * NZ + Jz, T{});
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-            Un[q][v] = nb[q] >= 0 ? ld(v, (size_t)nb[q], nI[q], nJ[q]) + bgs<T>(K.ub, K.ubf, v * NZ + nJ[q]) : U[v];
+            Un[q][v] = nb[q] >= 0 ? ld(v, (size_t)nb[q], nI[q], nJ[q]) + bgs(K.ub, K.ubf, v * NZ + nJ[q], T{}) : U[v];
     }
     T HW[4], HE[4], HS[4], HN[4];
     face_flux<T, 0>(Un[0], U, nb[0] < 0, false, nb[0] < 0 ? K.hbxw : K.hbx, NZ, Jz, sub, K, spt, HW);
     face_flux<T, 0>(U, Un[1], false, nb[1] < 0, nb[1] < 0 ? K.hbxw + 4 * NZ : K.hbx, NZ, Jz, sub, K, spt, HE);
     face_flux<T, 1>(Un[2], U, nb[2] < 0, false, K.hbz, NZ + 1, Jz, sub, K, spt, HS);
     face_flux<T, 1>(U, Un[3], false, nb[3] < 0, K.hbz, NZ + 1, Jz + 1, sub, K, spt, HN);
-    const T iHx = mkc(K.iHx, K.iHxf, T{}), iHz = mkc(K.iHz, K.iHzf, T{});
+    const auto iHx = mkc(K.iHx, K.iHxf, T{}), iHz = mkc(K.iHz, K.iHzf, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v) f[v] = -((HE[v] - HW[v]) * iHx + (HN[v] - HS[v]) * iHz);
     const T up0 = ld(0, c, I, Jz);
@@ -185,7 +200,7 @@ JF_D void fv_cell_op(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, si
     if (VISC) {
         T VW[4], VE[4], VS[4], VN[4];
         const T zero = mk(0.0, T{});
-        const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
+        const auto cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
         if (nb[0] >= 0) visc2(Un[0], U, cx, VW); else { for (int v = 0; v < 4; ++v) VW[v] = zero; }
         if (nb[1] >= 0) visc2(U, Un[1], cx, VE); else { for (int v = 0; v < 4; ++v) VE[v] = zero; }
         if (nb[2] >= 0) visc2(Un[2], U, cz, VS); else { for (int v = 0; v < 4; ++v) VS[v] = zero; }
@@ -247,10 +262,10 @@ JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size
     T U[4], N[4];
     const T up0 = ld(0, c, I, Jz);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) U[v] = (v == 0 ? up0 : ld(v, c, I, Jz)) + bgs<T>(K.ub, K.ubf, v * NZ + Jz);
+    for (int v = 0; v < 4; ++v) U[v] = (v == 0 ? up0 : ld(v, c, I, Jz)) + bgs(K.ub, K.ubf, v * NZ + Jz, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v)
-        N[v] = wall ? U[v] : ld(v, (size_t)nb, nI, nJ) + bgs<T>(K.ub, K.ubf, v * NZ + nJ);
+        N[v] = wall ? U[v] : ld(v, (size_t)nb, nI, nJ) + bgs(K.ub, K.ubf, v * NZ + nJ, T{});
     if (zf) {
         swap12(U);
         swap12(N);
@@ -289,7 +304,7 @@ JF_D T fv_cell_op4(const FVK &K, const FLoad<T, IN> &ld, const PowTab *spt, size
 #pragma unroll
         for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * hs + hi], T{});
     }
-    const T ih = zf ? mkc(K.iHz, K.iHzf, T{}) : mkc(K.iHx, K.iHxf, T{});
+    const auto ih = zf ? mkc(K.iHz, K.iHzf, T{}) : mkc(K.iHx, K.iHxf, T{});
     T f[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -316,7 +331,7 @@ template <class T, int IN, int MODE, bool VISC, int L>
 __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
                                             const double *fu, double adt, typename SOf<T>::type *out,
-                                            int bf16 = 0) {
+                                            int bf16, RKS rk) {
     jf_pdl_enter();
     typedef typename SOf<T>::type S;
     __shared__ PowTab spt;
@@ -347,7 +362,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
             const S x = (S)ld.dir(v, c, I, Jz);
             const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, adtf, ld.step());
             if (MODE == FV_SMOOTH)
-                out[gi] = store_round<S>(x + dtau[c] * (b[gi] - gx), bf16);
+                out[gi] = store_round<S>(rk_stage<S>(rk, x, dtau[c], b[gi] - gx, gi), bf16);
             else
                 out[gi] = gx - b[gi];
         }
@@ -450,11 +465,13 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
                                                       const typename SOf<T>::type *dtau, const double *fu,
                                                       double adt, typename SOf<T>::type *out,
                                                       typename SOf<T>::type *xc,
-                                                      const typename SOf<T>::type *dtau_c, int bf16) {
+                                                      const typename SOf<T>::type *dtau_c, int bf16, RKS rk) {
     jf_pdl_enter();
     typedef typename SOf<T>::type S;
     constexpr int TX = FV_TX;
-    __shared__ PowTab spt;
+    // the FP64 power table (the FP32 tangent power needs none)
+    __shared__ double spt_raw[IN < 2 ? sizeof(PowTab) / sizeof(double) : 1];
+    PowTab &spt = *reinterpret_cast<PowTab *>(spt_raw);
     // the tile's cells and a one-cell halo as face sides: state, 1/rho, p, c
     // (one pressure / sound speed per cell instead of one per face and side)
     __shared__ T sU[4][TZ + 2][TX + 2];
@@ -497,7 +514,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
             const size_t c = (size_t)J * NX + I;
             T U[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) U[v] = ld(v, c, I, J) + bgs<T>(K.ub, K.ubf, v * NZ + J);
+            for (int v = 0; v < 4; ++v) U[v] = ld(v, c, I, J) + bgs(K.ub, K.ubf, v * NZ + J, T{});
             Side<T> sd;
             side_of(U, K.pc, &spt, sd);
 #pragma unroll
@@ -516,7 +533,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
         sd.c = sC[lj][li];
     };
     const bool sub = (IN < 2);
-    const T cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
+    const auto cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
     // x face west of local cell (i, j): global face index I0 + i in [0, NX]
     auto xface = [&](int i, int j) {
         const int If = I0 + i, J = J0 + j;
@@ -602,7 +619,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
             S gx;
             if (IN == 1) gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)f - fuv[v]) / eps);
             else gx = x - (S)adtf * f;
-            if (MODE == FV_SMOOTH) out[gi] = store_round<S>(x + dtc * (bv[v] - gx), bf16);
+            if (MODE == FV_SMOOTH) out[gi] = store_round<S>(rk_stage<S>(rk, x, dtc, bv[v] - gx, gi), bf16);
             else if (MODE == FV_DEFECT) out[gi] = gx - bv[v];
             else sD[v][tz][tx] = gx - bv[v];
         }
@@ -918,19 +935,19 @@ __global__ void k_prolong(S *x, const S *vc, int NXf, int NZf, int fac, int zero
 
 // x = dtau b (first smoothing step from zero)
 template <class S>
-__global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1) {
+__global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1, double alpha) {
     jf_pdl_enter();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * n1) return;
-    x[t] = dtau[t % n1] * b[t];
+    x[t] = ((S)alpha * dtau[t % n1]) * b[t];   // alpha = 1: dtau b exactly
 }
 
 template <class S>
-__global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int NP) {
+__global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int NP, double alpha) {
     jf_pdl_enter();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * N1) return;
-    z[t] = dtau[(t % N1) / NP] * r[t];
+    z[t] = ((S)alpha * dtau[(t % N1) / NP]) * r[t];   // alpha = 1: dtau r exactly
 }
 
 template <class S>
@@ -1078,15 +1095,18 @@ inline bool fv_four_lanes(const jfnk_ctx *c, size_t cells) {
 template <class T, int IN, int MODE, bool V>
 void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const FLoad<T, IN> &ld,
                const typename SOf<T>::type *x, const typename SOf<T>::type *b, const typename SOf<T>::type *dt,
-               const double *fu, double adt, typename SOf<T>::type *out, int bf = 0) {
+               const double *fu, double adt, typename SOf<T>::type *out, int bf = 0,
+               RKS rk = RKS{nullptr, 0, 1.0}) {
     if (l4) {
-        jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf);
+        jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf, rk);
     } else if (tb >= 256) {   // tile rows follow the block size: 32 x 8 or 32 x 4 cells
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 7) / 8));
-        jf_launch(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
+        jf_launch(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
+                  rk);
     } else {
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 3) / 4));
-        jf_launch(k_fv_tile<T, IN, MODE, V, 4>, gt, FV_TX * 4, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf);
+        jf_launch(k_fv_tile<T, IN, MODE, V, 4>, gt, FV_TX * 4, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
+                  rk);
     }
     jf_launched();
 }
@@ -1094,7 +1114,7 @@ void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const 
 // FV_RES: out = f_low(u) (FP64 only).  FV_SMOOTH / FV_DEFECT use the FD quotient
 // (prec 64, eps = sqrt(eps_mach)/|x| from an on-device norm) or the tangent (prec 32).
 int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, const double *b, double *out,
-            cudaStream_t s) {
+            cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0}) {
     FVLev &L = c->lev[l];
     FVK K = make_fvk(c, l);
     const size_t n1 = (size_t)L.NX * L.NZ;
@@ -1115,8 +1135,8 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
         const double *fu = (const double *)L.fu;
         const double adt = c->mg_adt;
         if (mode == FV_SMOOTH) {
-            if (visc) { JF_FV(D64, 1, FV_SMOOTH, true, K, ld, x, b, dt, fu, adt, out); }
-            else { JF_FV(D64, 1, FV_SMOOTH, false, K, ld, x, b, dt, fu, adt, out); }
+            if (visc) { JF_FV(D64, 1, FV_SMOOTH, true, K, ld, x, b, dt, fu, adt, out, 0, rk); }
+            else { JF_FV(D64, 1, FV_SMOOTH, false, K, ld, x, b, dt, fu, adt, out, 0, rk); }
         } else {
             if (visc) { JF_FV(D64, 1, FV_DEFECT, true, K, ld, x, b, dt, fu, adt, out); }
             else { JF_FV(D64, 1, FV_DEFECT, false, K, ld, x, b, dt, fu, adt, out); }
@@ -1126,7 +1146,8 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
     return JFNK_OK;
 }
 
-int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float *out, cudaStream_t s) {
+int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float *out, cudaStream_t s,
+            RKS rk = RKS{nullptr, 0, 1.0}) {
     FVLev &L = c->lev[l];
     FVK K = make_fvk(c, l);
     const size_t n1 = (size_t)L.NX * L.NZ;
@@ -1140,8 +1161,8 @@ int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float 
     const double adt = c->mg_adt;
     const int bf = (c->prec == 16 && l == c->nlev - 1) ? 1 : 0;   // BF16 coarsest level
     if (mode == FV_SMOOTH) {
-        if (visc) { JF_FV(TL32, 2, FV_SMOOTH, true, K, ld, x, b, dt, nullptr, adt, out, bf); }
-        else { JF_FV(TL32, 2, FV_SMOOTH, false, K, ld, x, b, dt, nullptr, adt, out, bf); }
+        if (visc) { JF_FV(TL32, 2, FV_SMOOTH, true, K, ld, x, b, dt, nullptr, adt, out, bf, rk); }
+        else { JF_FV(TL32, 2, FV_SMOOTH, false, K, ld, x, b, dt, nullptr, adt, out, bf, rk); }
     } else {
         if (visc) { JF_FV(TL32, 2, FV_DEFECT, true, K, ld, x, b, dt, nullptr, adt, out); }
         else { JF_FV(TL32, 2, FV_DEFECT, false, K, ld, x, b, dt, nullptr, adt, out); }
@@ -1204,10 +1225,10 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     do {                                                                                                        \
         if (tz == 8)                                                                                            \
             jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
-                      outc, xcc, dtc_, bff);                                                                    \
+                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0});                                                                    \
         else                                                                                                    \
             jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 4>, gt, FV_TX * 4, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
-                      outc, xcc, dtc_, bff);                                                                    \
+                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0});                                                                    \
     } while (0)
     if (!l4 && f2) {
         if (c->prec == 64) {
@@ -1253,12 +1274,15 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
 }
 
 inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, const void *b, void *out,
-                               cudaStream_t s) {
+                               cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0}) {
     if (c->prec == 64)
         return fv_op64(c, l, mode, (const double *)c->lev[l].u, (const double *)x, (const double *)b,
-                       (double *)out, s);
-    return fv_op32(c, l, mode, (const float *)x, (const float *)b, (float *)out, s);
+                       (double *)out, s, rk);
+    return fv_op32(c, l, mode, (const float *)x, (const float *)b, (float *)out, s, rk);
 }
+
+// more than one stage per pseudo-time step (opts.rk_stages > 1)
+inline bool rk_multi(const jfnk_ctx *c) { return c->opts.rk_stages > 1 || c->opts.rk_alpha[0] != 1.0; }
 
 // MG_l(x, b; u) of Sec. 3.4 on level l (0 = finest subgrid).  `zero`: x = 0 on
 // entry (products with x are skipped).  `first_done`: the caller already made
@@ -1275,9 +1299,39 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
         zero = false;
     }
     auto smooth = [&](int steps) -> int {
+        const bool rk = rk_multi(c);
+        const int ns = c->opts.rk_stages;
         for (int i = 0; i < steps; ++i) {
-            if (zero) {
-                jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)L.b, (const S *)L.dtau, n1);
+            if (rk) {
+                // stages x_k = x_0 + a_k dtau (b - g'x_{k-1}) through the level's x2 and r
+                // buffers (x_0 = L.x is kept until the last stage)
+                void *in = L.x, *out = L.x2, *spare = L.r;
+                for (int k = 0; k < ns; ++k) {
+                    const double a = c->opts.rk_alpha[k];
+                    if (zero && k == 0) {
+                        jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)out, (const S *)L.b,
+                                  (const S *)L.dtau, n1, a);
+                        jf_launched();
+                    } else {
+                        JF_RET(fv_smooth_or_defect(c, l, FV_SMOOTH, in, L.b, out, s,
+                                                   RKS{zero ? nullptr : L.x, zero ? 2 : 1, a}));
+                    }
+                    void *prev = in;
+                    in = out;
+                    out = (k == 0) ? spare : prev;   // alternate x2 / r; x_0 stays intact
+                }
+                // the result is `in`; the other two buffers become x2 and r
+                void *bufs[3] = {L.x, L.x2, L.r}, *rest[2];
+                int q = 0;
+                for (void *bp : bufs)
+                    if (bp != in) rest[q++] = bp;
+                L.x = in;
+                L.x2 = rest[0];
+                L.r = rest[1];
+                zero = false;
+            } else if (zero) {
+                jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)L.b, (const S *)L.dtau, n1,
+                          1.0);
                 jf_launched();
                 zero = false;
             } else {
@@ -1293,7 +1347,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     JF_RET(smooth(pre));
     if (l < c->nlev - 1) {
         FVLev &C = c->lev[l + 1];
-        const bool fuse = c->mid_pre >= 1;
+        const bool fuse = c->mid_pre >= 1 && !rk_multi(c);
         if (zero || c->prec == 64) {
             // FP64: separate defect and restriction (one thread per fine cell keeps the
             // FP64-bound defect kernel occupied)
@@ -1317,7 +1371,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             vz = false;
             fd = false;
         }
-        if (sizeof(S) == 4 && post >= 1) {
+        if (sizeof(S) == 4 && post >= 1 && !rk_multi(c)) {
             // FP32: the correction x - P v_c is formed inside the first post-smoothing step
             JF_RET(fv_smooth32_corrected(c, l, (const float *)L.x, zero, (const float *)L.b, (float *)L.x2, s));
             void *t = L.x;
@@ -1344,7 +1398,7 @@ template <>
 int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        jf_launch(k_scale_dtau_dg<double>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dg, c->npt, NP); jf_launched();
+        jf_launch(k_scale_dtau_dg<double>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dg, c->npt, NP, 1.0); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1370,7 +1424,7 @@ template <>
 int dg_smooth_step<float>(jfnk_ctx *c, const float *r, float *&z, float *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        jf_launch(k_scale_dtau_dg<float>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dgf, c->npt, NP); jf_launched();
+        jf_launch(k_scale_dtau_dg<float>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dgf, c->npt, NP, 1.0); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1436,35 +1490,100 @@ int dg_first_step_defect32(jfnk_ctx *c, const float *r, float *z, float *d, cuda
     return dg_apply(c, DG_TLJV, a, s);
 }
 
+// One multi-stage pseudo-time step on the DG level (opts.rk_stages > 1):
+// z_k = z_0 + a_k dtau_E (r - G'z_{k-1}), k = 1..s, from z_0 = z (0 when `zero`).
+// Stages alternate between z2 and z3 (z_0 is kept); the last stage writes
+// last_out when given.  On return z points at the result and z2, z3 at the two
+// free buffers.
+template <class S>
+int dg_rk_step(jfnk_ctx *c, const S *r, S *&z, S *&z2, S *&z3, bool &zero, cudaStream_t s, S *last_out) {
+    const int ns = c->opts.rk_stages, NP = c->np1 * c->np1;
+    S *in = z, *out = z2;
+    for (int k = 0; k < ns; ++k) {
+        if (k == ns - 1 && last_out) out = last_out;
+        const double a = c->opts.rk_alpha[k];
+        if (zero && k == 0) {
+            jf_launch(k_scale_dtau_dg<S>, nblk(c->N, 256), 256, 0, s, out, r,
+                      sizeof(S) == 8 ? (const S *)c->dtau_dg : (const S *)c->dtau_dgf, c->npt, NP, a);
+            jf_launched();
+            JF_CK(cudaGetLastError());
+        } else {
+            DGArgs A = {};
+            A.U = c->mg_U;
+            A.adt = c->mg_adt;
+            A.out0 = out;
+            A.z0 = zero ? nullptr : z;
+            A.z0mode = zero ? 2 : 1;
+            A.alpha = a;
+            if (sizeof(S) == 8) {
+                JF_RET(red_dot(c, (const double *)in, (const double *)in, c->N, c->scal + S_EPSDG, RED_EPSP, s));
+                A.y = (const double *)in;
+                A.fU = c->fU;
+                A.r = (const double *)r;
+                A.eps = c->scal + S_EPSDG;
+                A.dtau = c->dtau_dg;
+                JF_RET(dg_apply(c, DG_SMOOTH64, A, s));
+            } else {
+                A.Uf = c->Usf;
+                A.yf = (const float *)in;
+                A.rf = (const float *)r;
+                A.dtauf = c->dtau_dgf;
+                JF_RET(dg_apply(c, DG_TLSMOOTH, A, s));
+            }
+        }
+        S *prev = in;
+        in = out;
+        out = (k == 0) ? z3 : prev;
+    }
+    S *bufs[3] = {z, z2, z3}, *rest[2] = {nullptr, nullptr};
+    int q = 0;
+    for (S *bp : bufs)
+        if (bp != in && q < 2) rest[q++] = bp;
+    z = in;
+    z2 = rest[0];
+    z3 = rest[1];
+    zero = false;
+    return JFNK_OK;
+}
+
 template <class S>
 int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     // restore the level double-buffer order at the end so that every
     // application issues the same launches on the same pointers
-    void *sx[JF_MAXLEV], *sx2[JF_MAXLEV];
+    void *sx[JF_MAXLEV], *sx2[JF_MAXLEV], *sr[JF_MAXLEV];
     for (int l = 0; l < c->nlev; ++l) {
         sx[l] = c->lev[l].x;
         sx2[l] = c->lev[l].x2;
+        sr[l] = c->lev[l].r;
     }
-    S *z = (S *)c->pz, *z2 = (S *)c->pz2;
+    const bool rk = rk_multi(c);
+    S *z = (S *)c->pz, *z2 = (S *)c->pz2, *z3 = (S *)c->pr;
     bool zero = true;
     const S *d = r;
-    if (sizeof(S) == 4 && c->dg_pre == 1 && c->opts.dg_fused != 2) {
+    if (sizeof(S) == 4 && c->dg_pre == 1 && c->opts.dg_fused != 2 && !rk) {
         JF_RET(dg_first_step_defect32(c, (const float *)r, (float *)z, (float *)c->pd, s));
         zero = false;
         d = (const S *)c->pd;
     } else {
-        for (int i = 0; i < c->dg_pre; ++i) JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+        for (int i = 0; i < c->dg_pre; ++i) {
+            if (rk) JF_RET(dg_rk_step<S>(c, r, z, z2, z3, zero, s, nullptr));
+            else JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
+        }
         if (!zero) {
             JF_RET(dg_defect<S>(c, r, z, (S *)c->pd, s));
             d = (const S *)c->pd;
         }
     }
-    const bool fuse0 = c->fine_pre >= 1;
+    const bool fuse0 = c->fine_pre >= 1 && !rk;
     JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s, fuse0 ? (S *)c->lev[0].x : nullptr, (const S *)c->lev[0].dtau));
     JF_RET(mg_cycle_t<S>(c, 0, true, fuse0, s));
     JF_RET(to_dg<S, S>(c, (const S *)c->lev[0].x, z, zero ? 0 : 1, s));
     zero = false;
     for (int i = 0; i < c->dg_post; ++i) {
+        if (rk) {
+            JF_RET(dg_rk_step<S>(c, r, z, z2, z3, zero, s, i == c->dg_post - 1 ? zout : nullptr));
+            continue;
+        }
         if (i == c->dg_post - 1) z2 = zout;   // the last step writes the output itself
         JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
     }
@@ -1472,6 +1591,7 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     for (int l = 0; l < c->nlev; ++l) {
         c->lev[l].x = sx[l];
         c->lev[l].x2 = sx2[l];
+        c->lev[l].r = sr[l];
     }
     return JFNK_OK;
 }

@@ -93,10 +93,31 @@ JF_D TL32 jsqrt(TL32 a) {
 JF_D float val(TL32 a) { return a.v; }   // compared in FP32: no FP64-pipe conversion
 JF_D TL32 jfma(TL32 a, TL32 b, TL32 c) { return a * b + c; }
 
+// An FP32 constant in tangent-linear arithmetic (its tangent is zero): products,
+// sums and quotients with a TL32 drop the tangent terms that are known to vanish
+// (a TL32 with a zero tangent would still multiply and add them).  Converts to
+// TL32 where a dual number is needed.
+struct TLc {
+    float v;
+    JF_D operator TL32() const { return TL32{v, 0.0f}; }
+};
+JF_D TL32 operator*(TLc a, TL32 b) { return TL32{a.v * b.v, a.v * b.d}; }
+JF_D TL32 operator*(TL32 a, TLc b) { return TL32{a.v * b.v, a.d * b.v}; }
+JF_D TL32 operator+(TL32 a, TLc b) { return TL32{a.v + b.v, a.d}; }
+JF_D TL32 operator+(TLc a, TL32 b) { return TL32{a.v + b.v, b.d}; }
+JF_D TL32 operator-(TL32 a, TLc b) { return TL32{a.v - b.v, a.d}; }
+JF_D TL32 operator-(TLc a, TL32 b) { return TL32{a.v - b.v, -b.d}; }
+JF_D TL32 operator/(TLc a, TL32 b) {
+    const float ib = frcp(b.v);
+    const float q = a.v * ib;
+    return TL32{q, -(q * b.d) * ib};
+}
+JF_D TL32 jfma(TLc a, TL32 b, TL32 c) { return TL32{fmaf(a.v, b.v, c.v), fmaf(a.v, b.d, c.d)}; }
+
 // Constants held in both precisions: the FP32 tangent takes the float copy, so
 // no double-to-float conversion (an FP64-pipe instruction) runs per use.
 JF_D D64 mkc(double d, float, D64) { return D64{d}; }
-JF_D TL32 mkc(double, float f, TL32) { return TL32{f, 0.0f}; }
+JF_D TLc mkc(double, float f, TL32) { return TLc{f}; }
 template <class S> JF_D S pick(double d, float f);
 template <> JF_D double pick<double>(double d, float) { return d; }
 template <> JF_D float pick<float>(double, float f) { return f; }

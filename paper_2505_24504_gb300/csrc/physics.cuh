@@ -46,10 +46,10 @@ struct Side {
 
 template <class T>
 JF_D void side_of(const T U[4], const PhysC &P, const PowTab *pt, Side<T> &S) {
-    const T gam = mkc(P.gamma, P.gammaf, T{});
+    const auto gam = mkc(P.gamma, P.gammaf, T{});
 #pragma unroll
     for (int v = 0; v < 4; ++v) S.U[v] = U[v];
-    S.ir = mk(1.0, T{}) / U[0];
+    S.ir = mkc(1.0, 1.0f, T{}) / U[0];
     S.p = pressure(U[3], P, pt);
     S.c = jsqrt(gam * S.p * S.ir);
 }
@@ -128,8 +128,8 @@ JF_D void mirror(const T U[4], T G[4]) {
 // mu rho (0, d u, d w, d theta) for dU the derivative of U along one direction.
 template <class T>
 JF_D void viscous(const T U[4], const T dU[4], const PhysC &P, T F[4]) {
-    const T m = mkc(P.mu, P.muf, T{});
-    const T ir = mk(1.0, T{}) / U[0];
+    const auto m = mkc(P.mu, P.muf, T{});
+    const T ir = mkc(1.0, 1.0f, T{}) / U[0];
     F[0] = mk(0.0, T{});
     F[1] = m * (dU[1] - (U[1] * ir) * dU[0]);
     F[2] = m * (dU[2] - (U[2] * ir) * dU[0]);

@@ -40,7 +40,8 @@ class Opts(C.Structure):
                 ("sigma_fv", C.c_double), ("sigma_dg", C.c_double), ("c_ip", C.c_double),
                 ("use_graphs", C.c_int), ("tile_faces", C.c_int), ("tile_volume", C.c_int),
                 ("tile_fv", C.c_int), ("fv_split_cells", C.c_int), ("profile", C.c_int),
-                ("precond_fd_eps", C.c_double), ("time_budget_ms", C.c_double), ("dg_fused", C.c_int)]
+                ("precond_fd_eps", C.c_double), ("time_budget_ms", C.c_double), ("dg_fused", C.c_int),
+                ("rk_stages", C.c_int), ("rk_alpha", C.c_double * 4)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -49,6 +50,8 @@ class Opts(C.Structure):
         for k, v in kw.items():
             if k == "mg_key":
                 v = v.encode() if isinstance(v, str) else v
+            if k == "rk_alpha":
+                v = (C.c_double * 4)(*(list(v) + [0.0] * (4 - len(v))))
             setattr(o, k, v)
         return o
 

@@ -483,3 +483,46 @@ def test_fused_and_two_launch_tangent_products_same_answer(name):
         ms = c.time_operator(2, Up, y, 1)     # one FP32 tangent product z - adt J z into the workspace
         res.append(ms)
     assert all(m[0] > 0 for m in res)
+
+
+JST4 = (0.25, 1.0 / 3.0, 0.5, 1.0)   # Jameson-Schmidt-Turkel four-stage coefficients
+
+
+@pytest.mark.parametrize("key", ["mg111111V", "mg132211V"])
+def test_preconditioner_parity_multistage_smoother(case, key):
+    # Q^-1 with the four-stage low-storage pseudo-time smoother (Sec. 3.5) on the
+    # FV levels and the DG level: FP64 at the fixed FD step against the oracle, and
+    # the FP32 form against the same oracle at FP32 rounding
+    from oracle.fv import Multigrid
+    w, _, dg = case
+    Up = perturbed_state(w, dg, seed=23)
+    r = synth.random_perturbation(dg.shape[1:], 24)
+    mg = Multigrid(dg, w.fv_levels, key, fd_eps=C_FD, rk_alpha=JST4)
+    mg.linearize(Up, w.dt)
+    ref = mg.apply(r)
+    products = mg.stats["dg_calls"] + sum(mg.stats["fv_calls"])
+    for prec, bound in ((64, _fd_bound(dg.N, products)), (32, 2e-3)):
+        ctx = gpu_context(w, mg_key=key, precond_prec=prec, precond_fd_eps=C_FD, rk_stages=4, rk_alpha=JST4)
+        z = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+        ctx.mg_precondition(to_gpu(Up), w.dt, to_gpu(r), z)
+        err = rel(to_cpu(z, dg.shape), ref)
+        assert err <= bound, (prec, err, bound)
+
+
+@pytest.mark.parametrize("name", ["q2-20x10", "q3-11x6", "visc-q2-24x6", "igw-q3-20x3"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_implicit_step_multistage_smoother_parity(name, prec):
+    w = _cases()[name]
+    dg = oracle_dg(w)
+    from oracle.fv import Multigrid
+    from oracle.solver import implicit_step
+    ctx = gpu_context(w, precond_prec=prec, rk_stages=4, rk_alpha=JST4)
+    U0 = initial_state(w, dg)
+    U = to_gpu(U0)
+    st = ctx.implicit_step(U, w.dt, scheme=1)
+    assert st.status == 0
+    ref = implicit_step(dg, U0, w.dt, scheme=1, tol=w.newton_tol,
+                        precond=Multigrid(dg, w.fv_levels, w.mg_key, rk_alpha=JST4))
+    got = to_cpu(U, dg.shape)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
