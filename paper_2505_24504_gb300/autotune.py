@@ -5,8 +5,10 @@ threads per block of the DG face kernel, elements per DG volume block, threads
 per block of the FV cell kernels and the level size below which FV levels run
 four lanes per cell.  This module keys the winners by GPU name,
 order, grid, viscosity, preconditioner precision and mg key, stores them in a
-JSON file (default: _tune_cache.json next to this module, not versioned) and
-applies them to the options of new contexts of the same shape.
+JSON file and applies them to the options of new contexts of the same shape.
+The cache file
+is $JFNK_TUNE_CACHE when set, else tune_cache.json in $XDG_CACHE_HOME/jfnk
+(default ~/.cache/jfnk), never inside the package.
 """
 from __future__ import annotations
 
@@ -17,7 +19,17 @@ import threading
 from . import jfnk
 
 _LOCK = threading.Lock()
-DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json")
+
+
+def _default_cache() -> str:
+    env = os.environ.get("JFNK_TUNE_CACHE")
+    if env:
+        return env
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "jfnk", "tune_cache.json")
+
+
+DEFAULT_CACHE = _default_cache()
 
 
 def _gpu_name() -> str:
@@ -40,6 +52,7 @@ def load(path: str = DEFAULT_CACHE) -> dict:
 
 
 def save(cache: dict, path: str = DEFAULT_CACHE) -> None:
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
     tmp = path + ".tmp"
     with open(tmp, "w") as fh:
         json.dump(cache, fh, indent=1, sort_keys=True)

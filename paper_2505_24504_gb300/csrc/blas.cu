@@ -603,9 +603,16 @@ __global__ void k_f2d(const float *x, double *y, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = f2d_bits(x[i]);
 }
 
+// grid-stride launches of 256 threads: at most 16 blocks per SM of the current device
 inline unsigned grid_for(size_t n) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm < 1) {
+        cudaGetLastError();
+        nsm = 1;
+    }
     size_t g = (n + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
+    if (g > (size_t)nsm * 16) g = (size_t)nsm * 16;
     if (g < 1) g = 1;
     return (unsigned)g;
 }

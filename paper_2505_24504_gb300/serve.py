@@ -14,6 +14,8 @@
 * A state's requests run in arrival order and one at a time, and every
   kernel is deterministic, so each result is bit-identical to stepping that
   state alone.
+* A step that does not converge (the library restores U^n) is retried over the
+  same interval as 2, then 4 substeps; the report counts such requests.
 
 Latency = completion - arrival (wall clock); the report gives p50 / p99 and the
 sustained steps/s.  Scheduling is host logic; every solve runs in libjfnk.so.
@@ -21,11 +23,24 @@ sustained steps/s.  Scheduling is host logic; every solve runs in libjfnk.so.
 from __future__ import annotations
 
 import collections
+import copy
 import threading
 import time
 from dataclasses import dataclass, field
 
 from . import jfnk
+
+
+def _copy_state(U):
+    return U.clone() if hasattr(U, "clone") else copy.deepcopy(U)
+
+
+def _restore_state(U, snap):
+    if hasattr(U, "copy_"):
+        U.copy_(snap)
+    else:
+        U.clear()
+        U.update(copy.deepcopy(snap))
 
 
 @dataclass
@@ -53,6 +68,7 @@ class Record:
     end: float = 0.0
     status: int = 0
     gmres_its: int = 0
+    substeps: int = 1
 
 
 @dataclass
@@ -82,7 +98,18 @@ class Report:
                 "wall_s": self.wall_s, "peak_context_bytes": self.peak_bytes,
                 "contexts_created": self.contexts_created, "contexts_evicted": self.contexts_evicted,
                 "max_concurrent": self.max_concurrent,
-                "failed": sum(1 for r in self.records if r.status != 0)}
+                "failed": sum(1 for r in self.records if r.status != 0),
+                "failed_by_state": self.failures(),
+                "retried_with_substeps": sum(1 for r in self.records if r.substeps > 1)}
+
+    def failures(self):
+        """{state id: {status code: requests}} of the requests that did not succeed."""
+        out = {}
+        for r in self.records:
+            if r.status != 0:
+                d = out.setdefault(r.sid, {})
+                d[r.status] = d.get(r.status, 0) + 1
+        return out
 
 
 class Server:
@@ -136,6 +163,37 @@ class Server:
             self.peak = max(self.peak, self._bytes)
         self._busy.add(sid)
         return ctx
+
+    # Step-size fallback: when a step fails to converge (Newton or GMRES cap, a
+    # non-finite norm) the library has restored U^n, and the request is retried as
+    # 2, then 4 substeps of dt/2, dt/4 (the same time interval); the record keeps
+    # the number of substeps it took.
+    RETRY_CODES = (-4, -6)          # JFNK_ENOTCONV, JFNK_ENAN
+    MAX_HALVINGS = 2
+
+    def _step(self, ctx, st, stream):
+        """One request: returns (status, GMRES iterations, substeps).  A failed
+        substep sequence is undone from a copy of U^n before the next try."""
+        snap = None
+        for h in range(self.MAX_HALVINGS + 1):
+            n = 1 << h
+            if h == 1:
+                snap = _copy_state(st.U)
+            elif h > 1:
+                _restore_state(st.U, snap)
+            its, status = 0, 0
+            for _ in range(n):
+                s = ctx.implicit_step(st.U, st.dt / n, scheme=st.scheme, raise_on_error=False)
+                stream.synchronize()
+                its += s.gmres_its
+                status = s.status
+                if status != 0:
+                    break
+            if status == 0 or status not in self.RETRY_CODES:
+                return status, its, n
+        if snap is not None:
+            _restore_state(st.U, snap)
+        return status, its, n
 
     def run(self, arrivals, timeout_s: float = 600.0):
         """Replay (arrival_time_s, sid) requests in real time; returns a Report.
@@ -195,10 +253,7 @@ class Server:
                     st = self.states[rec.sid]
                     rec.start = time.perf_counter() - t0
                     try:
-                        s = ctx.implicit_step(st.U, st.dt, scheme=st.scheme, raise_on_error=False)
-                        stream.synchronize()
-                        rec.status = s.status
-                        rec.gmres_its = s.gmres_its
+                        rec.status, rec.gmres_its, rec.substeps = self._step(ctx, st, stream)
                     except Exception as exc:   # a failed request must not stop the loop
                         rec.status = getattr(exc, "code", -3)
                     rec.end = time.perf_counter() - t0

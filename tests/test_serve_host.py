@@ -105,3 +105,36 @@ def test_contexts_kept_when_budget_allows(fakes):
 def test_state_larger_than_budget_is_rejected(fakes):
     with pytest.raises(ValueError):
         serve.Server(_states(3), hbm_budget=250, workers=2)   # state 2 needs 300 bytes
+
+
+def test_failed_step_is_retried_with_substeps(fakes, monkeypatch):
+    # a step longer than 0.3 fails with ENAN (state untouched, as the library
+    # restores U^n): the server retries the request as 2, then 4 substeps
+    class _Stats:
+        def __init__(self, status):
+            self.status = status
+            self.gmres_its = 1
+
+    def step(self, U, dt, scheme=1, raise_on_error=True):
+        # state 3 fails on its second substep at dt/2: the partial progress must be undone
+        if dt > 0.3 or (U.get("flaky") and U["n"] == 1 and dt > 0.3 / 2):
+            return _Stats(-6)
+        U["n"] += 1
+        return _Stats(0)
+
+    monkeypatch.setattr(_FakeContext, "implicit_step", step)
+    states = {0: serve.StateSpec(grid=0, k=1, phys=None, opts=None, dt=1.0, scheme=1, U={"n": 0}),
+              1: serve.StateSpec(grid=1, k=1, phys=None, opts=None, dt=0.25, scheme=1, U={"n": 0}),
+              2: serve.StateSpec(grid=2, k=1, phys=None, opts=None, dt=8.0, scheme=1, U={"n": 0}),
+              3: serve.StateSpec(grid=3, k=1, phys=None, opts=None, dt=0.5, scheme=1, U={"n": 0, "flaky": 1})}
+    srv = serve.Server(states, hbm_budget=10_000, workers=2)
+    rep = srv.run([(0.0, 0), (0.0, 1), (0.0, 2), (0.0, 3)], timeout_s=30.0)
+    srv.close()
+    by = {r.sid: r for r in rep.records}
+    assert by[0].status == 0 and by[0].substeps == 4 and states[0].U["n"] == 4
+    assert by[1].status == 0 and by[1].substeps == 1 and states[1].U["n"] == 1
+    assert by[2].status == -6 and states[2].U["n"] == 0          # dt/4 = 2 still too long: reported
+    s = rep.summary()
+    # state 3: dt = 0.5 fails, 2 x 0.25 fails at the second substep (undone), 4 x 0.125 succeeds
+    assert by[3].status == 0 and by[3].substeps == 4 and states[3].U["n"] == 4
+    assert s["failed"] == 1 and s["failed_by_state"] == {2: {-6: 1}} and s["retried_with_substeps"] == 3
