@@ -54,7 +54,7 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_FLOP_PER_SM_CLK = 4.0
 # DRAM bytes (read + write) of one FP64 FD-product face launch on this workload,
 # ncu, cold L2 (writes stay in L2)
-TRAFFIC_FACE = 13_339_904
+TRAFFIC_FACE = 13_339_136
 
 
 def parse():

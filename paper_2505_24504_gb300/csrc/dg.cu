@@ -469,7 +469,7 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
     const O lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
     const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
     const double ceps = eps != 0.0 ? A.adt / eps : 0.0;   // adt / eps once per thread
-    const float adtf = (MODE == DG_TLJV || MODE == DG_TLSMOOTH) ? (float)A.adt : 0.0f;
+    const float adtf = (MODE == DG_TLJV || MODE == DG_TLSMOOTH) ? A.adtf : 0.0f;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         O f = 0;
@@ -518,7 +518,7 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
             if (A.z0mode == 0) {
                 ((float *)A.out0)[gi] = z + edt * (ef[v] - Jz);
             } else {
-                const float st = ((float)A.alpha * edt) * (ef[v] - Jz);
+                const float st = (A.alphaf * edt) * (ef[v] - Jz);
                 ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
             }
         }
@@ -552,8 +552,70 @@ template <int NP1> struct StripOf {
     static constexpr int E = (128 / NP) > 0 ? 128 / NP : 1;
 };
 
+// T^mf of the strip's defect (in sd) to the finest FV level: the 1D transfer
+// matrix along x, then along z (through the scratch st), the mass fix from the
+// subcell values (mean against the modified Newton-Cotes quadrature), written to
+// b and, when x0 is given, x0 = dtau b.  The arithmetic and its order are those of
+// the stand-alone transfer kernel.  All threads of the block call it.
+template <int NP1, int E>
+__device__ __forceinline__ void dgtl_transfer(const TransferOut &TR, float (*sd)[4][NP1 * NP1], float (*smf)[4],
+                                              float (*st)[4][NP1 * NP1], int le, int node, int ez, int ex,
+                                              bool active) {
+    constexpr int NP = NP1 * NP1;
+    const int i = node % NP1, j = node / NP1;
+    __syncthreads();   // sd complete; sg (scratch st) no longer read
+    if (active) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // t1(i, b) = sum_a V[i][a] d(a, b), at [b][i]
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < NP1; ++a) acc = fmaf(TR.V[i][a], sd[le][q][j * NP1 + a], acc);
+            st[le][q][j * NP1 + i] = acc;
+        }
+    }
+    __syncthreads();
+    float Tu[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NP1; ++b) acc = fmaf(TR.V[j][b], st[le][q][b * NP1 + i], acc);
+            Tu[q] = acc;
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sd[le][q][node] = Tu[q];
+    }
+    __syncthreads();
+    if (active && node < 4) {
+        const int q = node;
+        float mfv = 0.0f, mnc = 0.0f;
+        for (int jj = 0; jj < NP1; ++jj)
+            for (int ii = 0; ii < NP1; ++ii) {
+                const float x = sd[le][q][jj * NP1 + ii];
+                mfv += x;
+                mnc = fmaf(TR.om[ii] * TR.om[jj], x, mnc);
+            }
+        smf[le][q] = TR.massfix ? (mfv / (float)NP - mnc) : 0.0f;
+    }
+    __syncthreads();
+    if (!active) return;
+    const size_t I = (size_t)ex * NP1 + i, Jr = (size_t)ez * NP1 + j;
+    const size_t cell = Jr * TR.NX + I, ncell = (size_t)TR.NX * TR.NZ;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float val = Tu[q] - smf[le][q];
+        const size_t gi = (size_t)q * ncell + cell;
+        TR.b[gi] = val;
+        if (TR.x0) TR.x0[gi] = TR.dtau0[cell] * val;   // first pseudo-time step from zero
+    }
+}
+
 template <int NP1, bool VISC, int MODE, int FIRST>
-__global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, float *out1f) {
+__global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, float *out1f, TransferOut TR) {
     jf_pdl_enter();
     constexpr int NP = NP1 * NP1;
     constexpr int E = StripOf<NP1>::E;
@@ -568,6 +630,8 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
     __shared__ float sSx[VISC ? E + 1 : 1][6][NP1];   // viscous symmetry terms (L side 0..2, R side 3..5)
     __shared__ float sSz[VISC ? 2 : 1][VISC ? E : 1][6][NP1];
     __shared__ float sDx[NP1][NP1], sDz[NP1][NP1], sDn[NP1][NP1], sl[8][NP1];
+    __shared__ float sdf[FIRST ? E : 1][4][NP];    // the defect, for the transfer (FIRST)
+    __shared__ float smf[FIRST ? E : 1][4];        // mass-fix shift per element and variable
     const int nx = K.nx, nz = K.nz;
     const int nstrip = (nx + E - 1) / E;
     const int ez = (int)blockIdx.x / nstrip, ex0 = ((int)blockIdx.x % nstrip) * E;
@@ -804,12 +868,12 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
         }
     }
     __syncthreads();
-    if (!active) return;
+    if (!active && !(FIRST && TR.b)) return;
     const float lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
     const float lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
-    const float adtf = (float)A.adt;
+    const float adtf = A.adtf;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 4 && active; ++v) {
         float f = 0.0f;
 #pragma unroll
         for (int q = 0; q < NP1; ++q) {
@@ -832,17 +896,20 @@ __global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, flo
         const float z = Up[v].d;
         const float jz = z - adtf * f;
         if (MODE == DG_TLJV) {
-            ((float *)A.out0)[gi] = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
+            const float dv = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
+            if (FIRST && TR.b) sdf[le][v][node] = dv;
+            else ((float *)A.out0)[gi] = dv;
             if (FIRST) out1f[gi] = z;
         } else {  // DG_TLSMOOTH
             if (A.z0mode == 0) {
                 ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
             } else {
-                const float st = ((float)A.alpha * edt) * (ef[v] - jz);
+                const float st = (A.alphaf * edt) * (ef[v] - jz);
                 ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
             }
         }
     }
+    if (FIRST && TR.b) dgtl_transfer<NP1, E>(TR, sdf, smf, sg[0], le, node, ez, ex0 + le, active);
 }
 
 // background fluxes at node rows and horizontal faces, with the residual's own
@@ -1001,9 +1068,10 @@ int launch_tl(jfnk_ctx *c, const DGK &K, const DGArgs &a, cudaStream_t s) {
     const int threads = E * NP1 * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
     if (MODE == DG_TLJV && a.out1f)
-        jf_launch(k_dgtl<NP1, VISC, MODE, 1>, nb, threads, 0, s, K, a, a.out1f);
+        jf_launch(k_dgtl<NP1, VISC, MODE, 1>, nb, threads, 0, s, K, a, a.out1f,
+                  a.tro ? *a.tro : TransferOut{});
     else
-        jf_launch(k_dgtl<NP1, VISC, MODE, 0>, nb, threads, 0, s, K, a, (float *)nullptr);
+        jf_launch(k_dgtl<NP1, VISC, MODE, 0>, nb, threads, 0, s, K, a, (float *)nullptr, TransferOut{});
     jf_launched();
     JF_CK(cudaGetLastError());
     if (c->timing) {
@@ -1090,7 +1158,10 @@ int dg_setup_background(jfnk_ctx *c, cudaStream_t s) {
     return JFNK_OK;
 }
 
-int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s) {
+int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a_in, cudaStream_t s) {
+    DGArgs a = a_in;
+    a.adtf = (float)a.adt;
+    a.alphaf = (float)a.alpha;
     c->dg_calls++;
     // the stored traces belong to the cached f(U): any other writer of the cache drops them
     if (a.out0 == c->fU || a.out1 == c->fU) c->tr_valid = a.tr_out == c->trU ? 1 : 0;

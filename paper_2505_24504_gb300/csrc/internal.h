@@ -193,6 +193,19 @@ enum DGMode {
     DG_TLSMOOTH = 5  // out0 = z + dtau (r - (z - adt J z))            (FP32 tangent)
 };
 
+// DG -> finest-FV transfer T^mf folded into the FP32 defect kernel: the 1D
+// transfer matrix (interpolation at the subcell centres or subcell means), the
+// modified Newton-Cotes weights of the mass fix, the level's b (and x = dtau b, the
+// first pseudo-time step from zero, when x0 is given)
+struct TransferOut {
+    float V[5][5];
+    float om[5];
+    int massfix;
+    int NX, NZ;
+    float *b, *x0;
+    const float *dtau0;
+};
+
 struct DGArgs {
     const double *U;       // state U' (FP64)
     const float *Uf;       // state U' (FP32, tangent modes)
@@ -206,12 +219,16 @@ struct DGArgs {
     const double *dtau;    // [n_el] (smoothing)
     const float *dtauf;    // [n_el] (FP32 smoothing)
     double adt;
+    float adtf;            // FP32 copies of adt and alpha for the tangent kernels (set by dg_apply)
+    float alphaf;
     void *out0;
     double *out1;
     double *tr_out;        // FP64 residual / G: store the face traces of U here (may be null)
     const double *tr_in;   // FP64 FD product: face traces of U from the residual at U (may be null)
     float *out1f;          // FP32 defect at the first step from zero: z = dtau r is formed from rf and
                            // dtauf on the fly (yf unused) and written here
+    const TransferOut *tro;   // with out1f: also T^mf of the defect to the finest FV level (host struct,
+                              // passed by value to the kernel; null: the defect goes to out0)
     // smoothing modes, one stage of the multi-stage pseudo-time scheme: z0mode 0 explicit
     // Euler z + dtau (r - G'z); 1 z0 + alpha dtau (r - G'z) (z the previous stage); 2 the
     // same with z0 = 0

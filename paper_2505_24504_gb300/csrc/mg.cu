@@ -29,6 +29,7 @@ struct FVK {
     double iHx, iHz, g, mu;
     double vcx, vcz;                     // mu / (2 H) of the two-point viscous flux
     float iHxf, iHzf, gf, vcxf, vczf;    // float copies for the FP32 tangent
+    float adtf;                          // alpha dt of the linearisation in FP32
     PhysC pc;
     const PowTab *pt;
     const double *ub, *hbx, *hbxw, *hbz;
@@ -43,11 +44,12 @@ struct RKS {
     const void *x0;
     int mode;
     double alpha;
+    float alphaf;   // FP32 copy: no per-thread conversion (an FP64-pipe instruction)
 };
 template <class S>
 JF_D S rk_stage(const RKS &rk, S x, S dt, S bmg, size_t gi) {
     if (rk.mode == 0) return x + dt * bmg;
-    const S st = ((S)rk.alpha * dt) * bmg;
+    const S st = (pick<S>(rk.alpha, rk.alphaf) * dt) * bmg;
     return rk.mode == 1 ? ((const S *)rk.x0)[gi] + st : st;
 }
 
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
     FLoad<T, IN> ld = ld0;
     ld.prepare();
     __syncthreads();
-    const float adtf = IN >= 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? K.adtf : 0.0f;
     const size_t n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = L == 4 ? (int)(t & 3) : 0;
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> 
     const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double eps = ld.step();
-    const float adtf = IN >= 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? K.adtf : 0.0f;
     if (L == 1) {
         if (t >= nc) return;
         const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0,
     else if (tz == 1 && tx < TZ) xface(TX, tx);   // east edge of the tile
     __syncthreads();
     const S iHx = pick<S>(K.iHx, K.iHxf), iHz = pick<S>(K.iHz, K.iHzf);
-    const float adtf = IN >= 2 ? (float)adt : 0.0f;
+    const float adtf = IN >= 2 ? K.adtf : 0.0f;
     const double eps = ld.step();
     if (live) {
 #pragma unroll
@@ -1022,6 +1024,7 @@ FVK make_fvk(jfnk_ctx *c, int l) {
     K.gf = (float)K.g;
     K.vcxf = (float)K.vcx;
     K.vczf = (float)K.vcz;
+    K.adtf = (float)c->mg_adt;
     K.pc = c->pc;
     K.pt = c->powtab;
     K.ub = L.ub;
@@ -1096,7 +1099,7 @@ template <class T, int IN, int MODE, bool V>
 void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const FLoad<T, IN> &ld,
                const typename SOf<T>::type *x, const typename SOf<T>::type *b, const typename SOf<T>::type *dt,
                const double *fu, double adt, typename SOf<T>::type *out, int bf = 0,
-               RKS rk = RKS{nullptr, 0, 1.0}) {
+               RKS rk = RKS{nullptr, 0, 1.0, 1.0f}) {
     if (l4) {
         jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf, rk);
     } else if (tb >= 256) {   // tile rows follow the block size: 32 x 8 or 32 x 4 cells
@@ -1114,7 +1117,7 @@ void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const 
 // FV_RES: out = f_low(u) (FP64 only).  FV_SMOOTH / FV_DEFECT use the FD quotient
 // (prec 64, eps = sqrt(eps_mach)/|x| from an on-device norm) or the tangent (prec 32).
 int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, const double *b, double *out,
-            cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0}) {
+            cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0, 1.0f}) {
     FVLev &L = c->lev[l];
     FVK K = make_fvk(c, l);
     const size_t n1 = (size_t)L.NX * L.NZ;
@@ -1147,7 +1150,7 @@ int fv_op64(jfnk_ctx *c, int l, int mode, const double *u, const double *x, cons
 }
 
 int fv_op32(jfnk_ctx *c, int l, int mode, const float *x, const float *b, float *out, cudaStream_t s,
-            RKS rk = RKS{nullptr, 0, 1.0}) {
+            RKS rk = RKS{nullptr, 0, 1.0, 1.0f}) {
     FVLev &L = c->lev[l];
     FVK K = make_fvk(c, l);
     const size_t n1 = (size_t)L.NX * L.NZ;
@@ -1225,10 +1228,10 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     do {                                                                                                        \
         if (tz == 8)                                                                                            \
             jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
-                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0});                                                                    \
+                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0, 1.0f});                                                                    \
         else                                                                                                    \
             jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 4>, gt, FV_TX * 4, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
-                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0});                                                                    \
+                      outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0, 1.0f});                                                                    \
     } while (0)
     if (!l4 && f2) {
         if (c->prec == 64) {
@@ -1274,7 +1277,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
 }
 
 inline int fv_smooth_or_defect(jfnk_ctx *c, int l, int mode, const void *x, const void *b, void *out,
-                               cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0}) {
+                               cudaStream_t s, RKS rk = RKS{nullptr, 0, 1.0, 1.0f}) {
     if (c->prec == 64)
         return fv_op64(c, l, mode, (const double *)c->lev[l].u, (const double *)x, (const double *)b,
                        (double *)out, s, rk);
@@ -1314,7 +1317,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
                         jf_launched();
                     } else {
                         JF_RET(fv_smooth_or_defect(c, l, FV_SMOOTH, in, L.b, out, s,
-                                                   RKS{zero ? nullptr : L.x, zero ? 2 : 1, a}));
+                                                   RKS{zero ? nullptr : L.x, zero ? 2 : 1, a, (float)a}));
                     }
                     void *prev = in;
                     in = out;
@@ -1478,8 +1481,10 @@ int dg_defect<float>(jfnk_ctx *c, const float *r, const float *z, float *d, cuda
 
 // FP32: one DG pre-smoothing step from zero (z = dtau_E r) and the defect
 // d = r - G'z in one launch; writes z and d
-int dg_first_step_defect32(jfnk_ctx *c, const float *r, float *z, float *d, cudaStream_t s) {
+int dg_first_step_defect32(jfnk_ctx *c, const float *r, float *z, float *d, cudaStream_t s,
+                           const TransferOut *tro = nullptr) {
     DGArgs a = {};
+    a.tro = tro;
     a.U = c->mg_U;
     a.Uf = c->Usf;
     a.rf = r;
@@ -1560,10 +1565,26 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
     S *z = (S *)c->pz, *z2 = (S *)c->pz2, *z3 = (S *)c->pr;
     bool zero = true;
     const S *d = r;
+    const bool fuse0 = c->fine_pre >= 1 && !rk;
+    bool transferred = false;
     if (sizeof(S) == 4 && c->dg_pre == 1 && c->opts.dg_fused != 2 && !rk) {
-        JF_RET(dg_first_step_defect32(c, (const float *)r, (float *)z, (float *)c->pd, s));
+        // the defect kernel also transfers the defect to the finest FV level (T^mf, and
+        // the first FV smoothing step from zero), so no transfer launch follows
+        TransferOut tro = {};
+        TK K = make_tk(c);
+        for (int i = 0; i < 5; ++i) {
+            for (int a = 0; a < 5; ++a) tro.V[i][a] = (float)K.tab.V[i][a];
+            tro.om[i] = (float)K.tab.om[i];
+        }
+        tro.massfix = c->opts.massfix && !c->opts.transfer_l2;
+        tro.NX = c->lev[0].NX;
+        tro.NZ = c->lev[0].NZ;
+        tro.b = (float *)c->lev[0].b;
+        tro.x0 = fuse0 ? (float *)c->lev[0].x : nullptr;
+        tro.dtau0 = (const float *)c->lev[0].dtau;
+        JF_RET(dg_first_step_defect32(c, (const float *)r, (float *)z, (float *)c->pd, s, &tro));
         zero = false;
-        d = (const S *)c->pd;
+        transferred = true;
     } else {
         for (int i = 0; i < c->dg_pre; ++i) {
             if (rk) JF_RET(dg_rk_step<S>(c, r, z, z2, z3, zero, s, nullptr));
@@ -1574,8 +1595,8 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
             d = (const S *)c->pd;
         }
     }
-    const bool fuse0 = c->fine_pre >= 1 && !rk;
-    JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s, fuse0 ? (S *)c->lev[0].x : nullptr, (const S *)c->lev[0].dtau));
+    if (!transferred)
+        JF_RET(to_fv<S, S>(c, d, (S *)c->lev[0].b, s, fuse0 ? (S *)c->lev[0].x : nullptr, (const S *)c->lev[0].dtau));
     JF_RET(mg_cycle_t<S>(c, 0, true, fuse0, s));
     JF_RET(to_dg<S, S>(c, (const S *)c->lev[0].x, z, zero ? 0 : 1, s));
     zero = false;
