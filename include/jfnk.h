@@ -266,6 +266,41 @@ void jfnk_batch_destroy(jfnk_batch *batch);
 int jfnk_batch_step(jfnk_batch *batch, double *const *U_dev, const double *dt, const int *scheme,
                     int *status, jfnk_stats *stats);
 
+/* How jfnk_batch_step runs the members (the result of every member is the same
+ * in both, bit for bit):
+ *  JFNK_BATCH_STREAMS (default): concurrently on their own streams from the host
+ *    thread pool, each member with its own launches and graphs.
+ *  JFNK_BATCH_LOCKSTEP: members of the same order k form a class.  One host
+ *    thread per member runs the member's solver with its kernel launches and
+ *    stream operations recorded; whenever every unfinished member of a class waits
+ *    for a value from the device (a norm, a Hessenberg column), the recorded work
+ *    of the class is replayed on the stream of its first member, and members whose
+ *    next launch is the same operator kernel (same precision and mode, same block
+ *    shape) share ONE launch whose blocks are dealt out to them.  The classes run
+ *    concurrently.  No graphs in this mode.  Needs 64 MiB of device memory and
+ *    64 MiB of pinned host memory for the replay's argument tables (JFNK_ENOMEM if
+ *    they cannot be had; the mode is then unchanged).
+ * JFNK_EINVAL for another mode or a null batch. */
+#define JFNK_BATCH_STREAMS 0
+#define JFNK_BATCH_LOCKSTEP 1
+#define JFNK_BATCH_LOCKSTEP_UNGROUPED 2   /* lock-step rounds, every launch replayed alone (for comparison) */
+int jfnk_batch_set_mode(jfnk_batch *batch, int mode);
+
+/* Launch counts of the last lock-step jfnk_batch_step: kernel launches issued,
+ * how many of them were grouped over two or more members, the launches the
+ * members would have issued alone (all summed over the classes), and the replay
+ * rounds (synchronisation points) of the class with the most.  Any pointer may be
+ * NULL.  JFNK_EINVAL for a null batch. */
+int jfnk_batch_last_launches(const jfnk_batch *batch, unsigned long long *launches, unsigned long long *grouped,
+                             unsigned long long *member_launches, unsigned long long *rounds);
+
+/* Host wall-clock milliseconds of the last lock-step jfnk_batch_step, summed
+ * over the rounds of a class (the largest over the classes): ms3[0] waiting for
+ * the members to reach their next synchronisation point (host solver work and
+ * recording), ms3[1] issuing the replay, ms3[2] waiting for the device to finish
+ * it.  JFNK_EINVAL for null arguments. */
+int jfnk_batch_last_times(const jfnk_batch *batch, double *ms3);
+
 /* f_m = M^-1 L_h(U'_m) (the residual of dg_residual, Sec. 2.1 and Sec. 4) for every
  * member m at once, on `stream`: members are grouped by (order k, viscous or
  * not), and each group takes ONE face launch and ONE volume launch whose blocks

@@ -34,6 +34,11 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".cu", ".cpp")))
 
 
+# Translation units compiled more than once with different defines: the DG
+# operator kernels once per order k = 1..4 (in parallel).
+VARIANTS = {"dg.cu": [("k%d" % (n - 1), ["-DJF_DG_NP1=%d" % n]) for n in (2, 3, 4, 5)]}
+
+
 def _deps():
     files = [os.path.join(SRC, f) for f in os.listdir(SRC)]
     files.append(os.path.join(ROOT, "include", "jfnk.h"))
@@ -56,11 +61,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     objs = []
     cmds = []
     for s in sources():
-        o = os.path.join(OUT, os.path.basename(s) + ".o")
-        objs.append(o)
         lang = ["-x", "cu"]   # every unit sees the device headers
-        cmds.append([cc, *ARCH, *FLAGS, *extra, *lang, "-c", s, "-o", o])
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        for tag, defs in VARIANTS.get(os.path.basename(s), [("", [])]):
+            o = os.path.join(OUT, os.path.basename(s) + (("." + tag) if tag else "") + ".o")
+            objs.append(o)
+            cmds.append([cc, *ARCH, *FLAGS, *defs, *extra, *lang, "-c", s, "-o", o])
+    with cf.ThreadPoolExecutor(max_workers=min(12, os.cpu_count() or 4)) as ex:
         res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), cmds))
     for c, r in zip(cmds, res):
         if verbose and r.stderr:

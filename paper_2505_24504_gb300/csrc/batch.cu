@@ -1,20 +1,181 @@
 // Batched implicit steps over ensemble members of uneven grids and orders.
 //
-// Each member is a jfnk context with its own non-blocking stream.  A pool of
-// host threads takes members from a shared counter, largest first, and drives
-// each member's implicit step (Newton, FGMRES, preconditioner graph) on the
-// member's stream, so the GPU runs the members' kernels concurrently: small
-// members fill the SMs that large members leave idle between their launches
-// and synchronisations.  Members share nothing on the device (own buffers,
-// fixed-order reductions), so a member's result is bit-identical alone and in
+// Two modes.  Streams: each member is a jfnk context with its own non-blocking
+// stream; a pool of host threads takes members from a shared counter, largest
+// first, and drives each member's implicit step (Newton, FGMRES, preconditioner
+// graph) on the member's stream, so the GPU runs the members' kernels
+// concurrently.  Lock-step: one host thread per member runs the same solver
+// code, but its launches and stream operations are recorded, not issued
+// (t_jf_rec); whenever every unfinished member waits at a synchronisation
+// point (a norm or a Hessenberg column read back), the recorded operations of
+// all members are replayed on one stream, and at each step of the replay the
+// members whose next operation is the same kernel (same body and argument
+// types, block shape and shared memory) run it in ONE grouped launch
+// (k_grouped): each block finds its member in a table of argument records.
+// Members share nothing on the device (own buffers, fixed-order reductions) and
+// a grouped block runs the body with its member's arguments, block index and
+// block count, so in both modes a member's result is bit-identical alone and in
 // any batch.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <map>
+#include <memory>
 #include <new>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
+
+thread_local JfRecorder *t_jf_rec = nullptr;
+
+// ---- stream operations of the solver path (recorded while t_jf_rec is set) ----
+cudaError_t jf_memcpy(void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t s) {
+    if (!t_jf_rec) return cudaMemcpyAsync(dst, src, n, kind, s);
+    JfOp op;
+    op.glaunch = nullptr;
+    op.kernel = false;
+    if (kind == cudaMemcpyHostToDevice) {   // the source may be the caller's stack: keep a copy
+        auto buf = std::make_shared<std::vector<unsigned char>>((const unsigned char *)src,
+                                                                (const unsigned char *)src + n);
+        op.run = [=](cudaStream_t st) { return cudaMemcpyAsync(dst, buf->data(), n, kind, st); };
+    } else {
+        op.run = [=](cudaStream_t st) { return cudaMemcpyAsync(dst, src, n, kind, st); };
+    }
+    t_jf_rec->ops.push_back(std::move(op));
+    return cudaSuccess;
+}
+
+cudaError_t jf_memset(void *dst, int v, size_t n, cudaStream_t s) {
+    if (!t_jf_rec) return cudaMemsetAsync(dst, v, n, s);
+    JfOp op;
+    op.glaunch = nullptr;
+    op.kernel = false;
+    op.run = [=](cudaStream_t st) { return cudaMemsetAsync(dst, v, n, st); };
+    t_jf_rec->ops.push_back(std::move(op));
+    return cudaSuccess;
+}
+
+// Shared state of one lock-step batch step: member states, their recorders and
+// the replay's table memory (device tables filled from pinned staging).
+struct JfLockstep {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<int> state;   // 0 running, 1 waiting at a synchronisation, 2 finished
+    std::vector<JfRecorder> rec;
+    unsigned gen = 0;
+    cudaError_t err = cudaSuccess;
+    cudaStream_t s = nullptr;
+    char *dtab = nullptr;
+    unsigned char *htab = nullptr;
+    size_t cap = 0;
+    unsigned long long launches = 0, grouped = 0, member_launches = 0, rounds = 0;
+    double ms_members = 0, ms_issue = 0, ms_device = 0;   // host wall clock per phase of the rounds
+    bool group = true;   // false: every recorded launch replays alone (the same order)
+};
+
+cudaError_t jf_sync(cudaStream_t s) {
+    JfRecorder *r = t_jf_rec;
+    if (!r) return cudaStreamSynchronize(s);
+    JfLockstep *L = r->ls;
+    std::unique_lock<std::mutex> lk(L->mu);
+    const unsigned g = L->gen;
+    L->state[r->member] = 1;
+    L->cv.notify_all();
+    L->cv.wait(lk, [&] { return L->gen != g; });
+    return L->err;
+}
+
+namespace {
+
+constexpr size_t TAB_ALIGN = 256;
+
+// Replay every member's recorded operations on L->s.  Operations that are not
+// launches run as soon as they reach the head of their member's queue; then the
+// launch kind found at the most heads runs once for all those members (the
+// first member in member order breaks ties), until every queue is empty.
+cudaError_t replay(JfLockstep *L) {
+    const int n = (int)L->rec.size();
+    std::vector<size_t> h(n, 0);
+    size_t off = 0;
+    std::vector<int> sel;
+    for (;;) {
+        bool any = false;
+        for (int m = 0; m < n; ++m) {
+            std::vector<JfOp> &ops = L->rec[m].ops;
+            while (h[m] < ops.size() && !ops[h[m]].glaunch) {
+                const cudaError_t e = ops[h[m]].run(L->s);
+                if (e != cudaSuccess) return e;
+                if (ops[h[m]].kernel) {
+                    ++L->launches;
+                    ++L->member_launches;
+                }
+                ++h[m];
+            }
+            if (h[m] < ops.size()) any = true;
+        }
+        if (!any) return cudaSuccess;
+        using Key = std::tuple<const void *, unsigned, unsigned, unsigned, size_t>;
+        auto key_of = [&](const JfOp &o) {
+            return Key{(const void *)o.glaunch, o.block.x, o.block.y, o.block.z, o.smem};
+        };
+        std::map<Key, int> count;
+        int best = -1, best_n = 0;
+        for (int m = 0; m < n; ++m) {
+            if (h[m] >= L->rec[m].ops.size()) continue;
+            const int c = ++count[key_of(L->rec[m].ops[h[m]])];
+            if (c > best_n) {
+                best_n = c;
+                best = m;
+            }
+        }
+        // the earliest member holding the winning kind
+        const Key k = key_of(L->rec[best].ops[h[best]]);
+        for (int m = 0; m < n; ++m)
+            if (h[m] < L->rec[m].ops.size() && key_of(L->rec[m].ops[h[m]]) == k) {
+                best = m;
+                break;
+            }
+        sel.clear();
+        for (int m = best; m < n; ++m)
+            if (h[m] < L->rec[m].ops.size() && key_of(L->rec[m].ops[h[m]]) == k) sel.push_back(m);
+        L->member_launches += sel.size();
+        ++L->launches;
+        const JfOp &o0 = L->rec[sel[0]].ops[h[sel[0]]];
+        if (!L->group) sel.resize(1);
+        if (sel.size() == 1) {   // alone: the member's own launch
+            const cudaError_t e = o0.run(L->s);
+            if (e != cudaSuccess) return e;
+            ++h[sel[0]];
+            continue;
+        }
+        const size_t es = o0.ent.size(), bytes = es * sel.size();
+        if (bytes > L->cap) return cudaErrorInvalidValue;
+        if (off + bytes > L->cap) {   // staging full: let the queued copies drain
+            const cudaError_t e = cudaStreamSynchronize(L->s);
+            if (e != cudaSuccess) return e;
+            off = 0;
+        }
+        unsigned total = 0;
+        for (size_t q = 0; q < sel.size(); ++q) {
+            const JfOp &o = L->rec[sel[q]].ops[h[sel[q]]];
+            unsigned char *dst = L->htab + off + q * es;
+            memcpy(dst, o.ent.data(), es);
+            memcpy(dst, &total, sizeof(unsigned));   // JfEnt::b0
+            total += o.nb;
+        }
+        cudaError_t e = cudaMemcpyAsync(L->dtab + off, L->htab + off, bytes, cudaMemcpyHostToDevice, L->s);
+        if (e == cudaSuccess) e = o0.glaunch(L->dtab + off, (int)sel.size(), total, o0.block, o0.smem, L->s);
+        if (e != cudaSuccess) return e;
+        ++L->grouped;
+        off += (bytes + TAB_ALIGN - 1) / TAB_ALIGN * TAB_ALIGN;
+        for (int m : sel) ++h[m];
+    }
+}
+
+}  // namespace
 
 struct jfnk_batch {
     int n;
@@ -23,7 +184,128 @@ struct jfnk_batch {
     std::vector<int> order;      // members, largest first
     int threads;
     void *desc;                  // device room for the grouped-operator descriptors
+    int mode;                    // JFNK_BATCH_STREAMS / JFNK_BATCH_LOCKSTEP
+    char *dtab;                  // lock-step replay tables (device) and their pinned staging
+    unsigned char *htab;
+    size_t tab_cap;
+    unsigned long long last_launches, last_grouped, last_member_launches, last_rounds;
+    double last_ms[3];
 };
+
+namespace {
+
+// One class of members (one order k) in lock-step: wait until none of them is
+// running, replay what they recorded, wait for the device, release them.
+void coordinate(JfLockstep &L) {
+    using clk = std::chrono::steady_clock;
+    auto ms = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+    for (;;) {
+        const auto t0 = clk::now();
+        std::unique_lock<std::mutex> lk(L.mu);
+        L.cv.wait(lk, [&] {
+            for (int x : L.state)
+                if (x == 0) return false;
+            return true;
+        });
+        bool done = true;
+        for (int x : L.state)
+            if (x != 2) done = false;
+        lk.unlock();
+        const auto t1 = clk::now();
+        cudaError_t e = L.err == cudaSuccess ? replay(&L) : L.err;
+        const auto t2 = clk::now();
+        const cudaError_t es = cudaStreamSynchronize(L.s);
+        const auto t3 = clk::now();
+        L.ms_members += ms(t0, t1);
+        L.ms_issue += ms(t1, t2);
+        L.ms_device += ms(t2, t3);
+        if (e == cudaSuccess) e = es;
+        ++L.rounds;
+        lk.lock();
+        for (auto &r : L.rec) r.ops.clear();
+        L.err = e;
+        if (done) return;
+        for (int &x : L.state)
+            if (x == 1) x = 0;
+        ++L.gen;
+        L.cv.notify_all();
+    }
+}
+
+// Members of the same order share the grouped launches of their class; the
+// classes run concurrently, each replayed on its own stream by its own
+// coordinator thread (the stream of its first member).
+int lockstep_step(jfnk_batch *b, double *const *U, const double *dt, const int *scheme, std::vector<int> &rc,
+                  jfnk_stats *stats) {
+    const int n = b->n;
+    std::vector<int> cls_of(n);
+    std::vector<std::vector<int>> cls;
+    for (int np1 = 2; np1 <= 5; ++np1) {
+        std::vector<int> m;
+        for (int i = 0; i < n; ++i)
+            if (b->ctx[i]->np1 == np1) m.push_back(i);
+        if (m.empty()) continue;
+        for (int i : m) cls_of[i] = (int)cls.size();
+        cls.push_back(m);
+    }
+    const int nc = (int)cls.size();
+    const size_t cap = b->tab_cap / (size_t)nc / 256 * 256;
+    std::vector<std::unique_ptr<JfLockstep>> Ls;
+    for (int q = 0; q < nc; ++q) {
+        Ls.emplace_back(new JfLockstep());
+        JfLockstep &L = *Ls.back();
+        const int nm = (int)cls[q].size();
+        L.state.assign(nm, 0);
+        L.rec.resize(nm);
+        L.s = b->streams[cls[q][0]];
+        L.dtab = b->dtab + (size_t)q * cap;
+        L.htab = b->htab + (size_t)q * cap;
+        L.cap = cap;
+        L.group = b->mode == JFNK_BATCH_LOCKSTEP;
+        for (int j = 0; j < nm; ++j) {
+            L.rec[j].ls = &L;
+            L.rec[j].member = j;
+        }
+    }
+    std::vector<std::thread> pool;
+    for (int i = 0; i < n; ++i) {
+        JfLockstep &L = *Ls[cls_of[i]];
+        const int j = (int)(std::find(cls[cls_of[i]].begin(), cls[cls_of[i]].end(), i) - cls[cls_of[i]].begin());
+        pool.emplace_back([&, i, j]() {
+            t_jf_rec = &L.rec[j];
+            jfnk_stats st;
+            rc[i] = implicit_step(b->ctx[i], U[i], dt[i], scheme[i], &st, b->streams[i]);
+            t_jf_rec = nullptr;
+            if (stats) stats[i] = st;
+            std::lock_guard<std::mutex> lk(L.mu);
+            L.state[j] = 2;
+            L.cv.notify_all();
+        });
+    }
+    std::vector<std::thread> coords;
+    for (int q = 1; q < nc; ++q) coords.emplace_back([&, q]() { coordinate(*Ls[q]); });
+    coordinate(*Ls[0]);
+    for (auto &t : coords) t.join();
+    for (auto &t : pool) t.join();
+    b->last_launches = b->last_grouped = b->last_member_launches = b->last_rounds = 0;
+    b->last_ms[0] = b->last_ms[1] = b->last_ms[2] = 0.0;
+    int rcode = JFNK_OK;
+    for (auto &Lp : Ls) {
+        const JfLockstep &L = *Lp;
+        b->last_launches += L.launches;
+        b->last_grouped += L.grouped;
+        b->last_member_launches += L.member_launches;
+        b->last_rounds = std::max(b->last_rounds, L.rounds);
+        b->last_ms[0] = std::max(b->last_ms[0], L.ms_members);
+        b->last_ms[1] = std::max(b->last_ms[1], L.ms_issue);
+        b->last_ms[2] = std::max(b->last_ms[2], L.ms_device);
+        if (L.err != cudaSuccess) rcode = JFNK_ECUDA;
+    }
+    __atomic_fetch_add(&g_jf_launches, b->last_launches, __ATOMIC_RELAXED);
+    return rcode;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -51,6 +333,12 @@ int jfnk_batch_create(jfnk_ctx *const *ctxs, int n, int max_threads, jfnk_batch 
                      [&](int x, int y) { return b->ctx[x]->N > b->ctx[y]->N; });
     b->threads = max_threads > 0 ? std::min(max_threads, n) : std::min(n, 16);
     b->desc = nullptr;
+    b->mode = JFNK_BATCH_STREAMS;
+    b->dtab = nullptr;
+    b->htab = nullptr;
+    b->tab_cap = 0;
+    b->last_launches = b->last_grouped = b->last_member_launches = b->last_rounds = 0;
+    b->last_ms[0] = b->last_ms[1] = b->last_ms[2] = 0.0;
     {
         std::lock_guard<std::mutex> lock(g_jf_device_mu);   // no allocation during another thread's capture
         if (cudaMalloc(&b->desc, dg_member_bytes() * (size_t)n) != cudaSuccess) {
@@ -68,11 +356,54 @@ void jfnk_batch_destroy(jfnk_batch *b) {
     if (!b) return;
     for (cudaStream_t s : b->streams)
         if (s) cudaStreamDestroy(s);
-    if (b->desc) {
+    {
         std::lock_guard<std::mutex> lock(g_jf_device_mu);
-        cudaFree(b->desc);
+        if (b->desc) cudaFree(b->desc);
+        if (b->dtab) cudaFree(b->dtab);
+        if (b->htab) cudaFreeHost(b->htab);
     }
     delete b;
+}
+
+int jfnk_batch_set_mode(jfnk_batch *b, int mode) {
+    if (!b || mode < JFNK_BATCH_STREAMS || mode > JFNK_BATCH_LOCKSTEP_UNGROUPED) return JFNK_EINVAL;
+    if (mode != JFNK_BATCH_STREAMS && !b->dtab) {
+        // room for the argument tables of one replay round: every member's
+        // recorded launches between two synchronisation points
+        const size_t cap = (size_t)64 << 20;
+        std::lock_guard<std::mutex> lock(g_jf_device_mu);
+        if (cudaMalloc(&b->dtab, cap) != cudaSuccess) {
+            cudaGetLastError();
+            b->dtab = nullptr;
+            return JFNK_ENOMEM;
+        }
+        if (cudaMallocHost(&b->htab, cap) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(b->dtab);
+            b->dtab = nullptr;
+            b->htab = nullptr;
+            return JFNK_ENOMEM;
+        }
+        b->tab_cap = cap;
+    }
+    b->mode = mode;
+    return JFNK_OK;
+}
+
+int jfnk_batch_last_launches(const jfnk_batch *b, unsigned long long *launches, unsigned long long *grouped,
+                             unsigned long long *member_launches, unsigned long long *rounds) {
+    if (!b) return JFNK_EINVAL;
+    if (launches) *launches = b->last_launches;
+    if (grouped) *grouped = b->last_grouped;
+    if (member_launches) *member_launches = b->last_member_launches;
+    if (rounds) *rounds = b->last_rounds;
+    return JFNK_OK;
+}
+
+int jfnk_batch_last_times(const jfnk_batch *b, double *ms3) {
+    if (!b || !ms3) return JFNK_EINVAL;
+    for (int i = 0; i < 3; ++i) ms3[i] = b->last_ms[i];
+    return JFNK_OK;
 }
 
 int jfnk_batch_step(jfnk_batch *b, double *const *U, const double *dt, const int *scheme, int *status,
@@ -80,8 +411,17 @@ int jfnk_batch_step(jfnk_batch *b, double *const *U, const double *dt, const int
     if (!b || !U || !dt || !scheme) return JFNK_EINVAL;
     for (int i = 0; i < b->n; ++i)
         if (!U[i]) return JFNK_EINVAL;
-    std::atomic<int> next(0);
     std::vector<int> rc(b->n, JFNK_OK);
+    if (b->mode != JFNK_BATCH_STREAMS) {
+        const int lr = lockstep_step(b, U, dt, scheme, rc, stats);
+        int first = lr;
+        for (int i = 0; i < b->n; ++i) {
+            if (status) status[i] = rc[i];
+            if (rc[i] != JFNK_OK && first == JFNK_OK) first = rc[i];
+        }
+        return first;
+    }
+    std::atomic<int> next(0);
     auto worker = [&]() {
         for (;;) {
             const int q = next.fetch_add(1);

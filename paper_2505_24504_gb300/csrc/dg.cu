@@ -336,11 +336,24 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
 }
 
 template <class T, int IN, int NP1, bool VISC>
+struct k_faces_b {
+    static constexpr int TPB = 256, MINB = 4;
+    static constexpr bool GROUP = !VISC && std::is_same<T, D64>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<DGK> K,
+                                               JfArg<Loader<T, IN>> ld0, JfArg<typename OutT<T>::type *> phix,
+                                               JfArg<typename OutT<T>::type *> symx,
+                                               JfArg<typename OutT<T>::type *> phiz,
+                                               JfArg<typename OutT<T>::type *> symz, JfArg<double *> tr_out,
+                                               JfArg<const double *> tr_in) {
+        jf_pdl_enter();
+        faces_body<T, IN, NP1, VISC>(K, ld0, phix, symx, phiz, symz, jf_bid, tr_out, tr_in);
+    }
+};
+template <class T, int IN, int NP1, bool VISC>
 __global__ void __launch_bounds__(256, 4) k_faces(DGK K, Loader<T, IN> ld0, typename OutT<T>::type *phix,
                                                typename OutT<T>::type *symx, typename OutT<T>::type *phiz,
                                                typename OutT<T>::type *symz, double *tr_out, const double *tr_in) {
-    jf_pdl_enter();
-    faces_body<T, IN, NP1, VISC>(K, ld0, phix, symx, phiz, symz, blockIdx.x, tr_out, tr_in);
+    k_faces_b<T, IN, NP1, VISC>::run(blockIdx.x, gridDim.x, K, ld0, phix, symx, phiz, symz, tr_out, tr_in);
 }
 
 // ---------------------------------------------------------------------------
@@ -526,13 +539,26 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
 }
 
 template <class T, int IN, int MODE, int NP1, bool VISC, int TV>
+struct k_volume_b {
+    static constexpr int TPB = 128, MINB = 8;
+    static constexpr bool GROUP = !VISC && std::is_same<T, D64>::value && MODE != DG_SMOOTH64;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<DGK> K,
+                                               JfArg<Loader<T, IN>> ld0, JfArg<DGArgs> A,
+                                               JfArg<const typename OutT<T>::type *> phix,
+                                               JfArg<const typename OutT<T>::type *> symx,
+                                               JfArg<const typename OutT<T>::type *> phiz,
+                                               JfArg<const typename OutT<T>::type *> symz) {
+        jf_pdl_enter();
+        volume_body<T, IN, MODE, NP1, VISC, TV>(K, ld0, A, phix, symx, phiz, symz, jf_bid);
+    }
+};
+template <class T, int IN, int MODE, int NP1, bool VISC, int TV>
 __global__ void __launch_bounds__(128, 8) k_volume(DGK K, Loader<T, IN> ld0, DGArgs A,
                                                    const typename OutT<T>::type *phix,
                                                    const typename OutT<T>::type *symx,
                                                    const typename OutT<T>::type *phiz,
                                                    const typename OutT<T>::type *symz) {
-    jf_pdl_enter();
-    volume_body<T, IN, MODE, NP1, VISC, TV>(K, ld0, A, phix, symx, phiz, symz, blockIdx.x);
+    k_volume_b<T, IN, MODE, NP1, VISC, TV>::run(blockIdx.x, gridDim.x, K, ld0, A, phix, symx, phiz, symz);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,301 +641,310 @@ __device__ __forceinline__ void dgtl_transfer(const TransferOut &TR, float (*sd)
 }
 
 template <int NP1, bool VISC, int MODE, int FIRST>
-__global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, float *out1f, TransferOut TR) {
-    jf_pdl_enter();
-    constexpr int NP = NP1 * NP1;
-    constexpr int E = StripOf<NP1>::E;
-    // U' (value, tangent) of the strip's elements [1], of the elements below [0] and
-    // above [2] them, and of the strip's west [0] and east [1] neighbours: every
-    // trace the faces need comes from shared memory, loaded coalesced up front
-    __shared__ TL32 sn[3][E][4][NP];
-    __shared__ TL32 se[2][4][NP];
-    __shared__ float sg[2][E][4][NP];              // volume fluxes (tangent part)
-    __shared__ float sPx[E + 1][4][NP1];           // x-face terms Phi (face f west of strip element f)
-    __shared__ float sPz[2][E][4][NP1];            // z-face terms: [0] bottom, [1] top of element le
-    __shared__ float sSx[VISC ? E + 1 : 1][6][NP1];   // viscous symmetry terms (L side 0..2, R side 3..5)
-    __shared__ float sSz[VISC ? 2 : 1][VISC ? E : 1][6][NP1];
-    __shared__ float sDx[NP1][NP1], sDz[NP1][NP1], sDn[NP1][NP1], sl[8][NP1];
-    __shared__ float sdf[FIRST ? E : 1][4][NP];    // the defect, for the transfer (FIRST)
-    __shared__ float smf[FIRST ? E : 1][4];        // mass-fix shift per element and variable
-    const int nx = K.nx, nz = K.nz;
-    const int nstrip = (nx + E - 1) / E;
-    const int ez = (int)blockIdx.x / nstrip, ex0 = ((int)blockIdx.x % nstrip) * E;
-    const int Ev = min(E, nx - ex0);
-    const size_t N1 = (size_t)K.n_el * NP;
-    const size_t nrow = (size_t)nz * NP1;
-    if (threadIdx.x < NP) {
-        const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
-        sDx[r][q] = K.Dxf[r][q];
-        sDz[r][q] = K.Dzf[r][q];
-        sDn[r][q] = K.Dnf[r][q];
-    }
-    if (threadIdx.x < NP1) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) sl[r][threadIdx.x] = K.liftf[r][threadIdx.x];
-    }
-    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
-    const int a = node % NP1, b = node / NP1;
-    const bool active = le < Ev;
-    const int e = ez * nx + ex0 + le;
-    // direction at a node: y (or dtau_E r for the first step from zero)
-    auto dir = [&](int el, size_t i) -> float { return FIRST ? A.dtauf[el] * A.rf[i] : A.yf[i]; };
-    auto load = [&](int el, TL32 (*dst)[NP]) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const size_t gi = (size_t)v * N1 + (size_t)el * NP + node;
-            dst[v][node] = TL32{A.Uf[gi], dir(el, gi)};
+struct k_dgtl_b {
+    static constexpr int TPB = 128, MINB = VISC ? 5 : 8;
+    static constexpr bool GROUP = !VISC;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<DGK> K, JfArg<DGArgs> A,
+                                               JfArg<float *> out1f, JfArg<TransferOut> TR) {
+        jf_pdl_enter();
+        constexpr int NP = NP1 * NP1;
+        constexpr int E = StripOf<NP1>::E;
+        // U' (value, tangent) of the strip's elements [1], of the elements below [0] and
+        // above [2] them, and of the strip's west [0] and east [1] neighbours: every
+        // trace the faces need comes from shared memory, loaded coalesced up front
+        __shared__ TL32 sn[3][E][4][NP];
+        __shared__ TL32 se[2][4][NP];
+        __shared__ float sg[2][E][4][NP];              // volume fluxes (tangent part)
+        __shared__ float sPx[E + 1][4][NP1];           // x-face terms Phi (face f west of strip element f)
+        __shared__ float sPz[2][E][4][NP1];            // z-face terms: [0] bottom, [1] top of element le
+        __shared__ float sSx[VISC ? E + 1 : 1][6][NP1];   // viscous symmetry terms (L side 0..2, R side 3..5)
+        __shared__ float sSz[VISC ? 2 : 1][VISC ? E : 1][6][NP1];
+        __shared__ float sDx[NP1][NP1], sDz[NP1][NP1], sDn[NP1][NP1], sl[8][NP1];
+        __shared__ float sdf[FIRST ? E : 1][4][NP];    // the defect, for the transfer (FIRST)
+        __shared__ float smf[FIRST ? E : 1][4];        // mass-fix shift per element and variable
+        const int nx = K.nx, nz = K.nz;
+        const int nstrip = (nx + E - 1) / E;
+        const int ez = (int)jf_bid / nstrip, ex0 = ((int)jf_bid % nstrip) * E;
+        const int Ev = min(E, nx - ex0);
+        const size_t N1 = (size_t)K.n_el * NP;
+        const size_t nrow = (size_t)nz * NP1;
+        if (threadIdx.x < NP) {
+            const int r = threadIdx.x / NP1, q = threadIdx.x % NP1;
+            sDx[r][q] = K.Dxf[r][q];
+            sDz[r][q] = K.Dzf[r][q];
+            sDn[r][q] = K.Dnf[r][q];
         }
-    };
-    float ef[4] = {0.f, 0.f, 0.f, 0.f}, edt = 0.0f;
-    if (active) {
-        load(e, sn[1][le]);
-        if (ez > 0) load(e - nx, sn[0][le]);
-        if (ez < nz - 1) load(e + nx, sn[2][le]);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        if (threadIdx.x < NP1) {
+    #pragma unroll
+            for (int r = 0; r < 8; ++r) sl[r][threadIdx.x] = K.liftf[r][threadIdx.x];
+        }
+        const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+        const int a = node % NP1, b = node / NP1;
+        const bool active = le < Ev;
+        const int e = ez * nx + ex0 + le;
+        // direction at a node: y (or dtau_E r for the first step from zero)
+        auto dir = [&](int el, size_t i) -> float { return FIRST ? A.dtauf[el] * A.rf[i] : A.yf[i]; };
+        auto load = [&](int el, TL32 (*dst)[NP]) {
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const size_t gi = (size_t)v * N1 + (size_t)el * NP + node;
+                dst[v][node] = TL32{A.Uf[gi], dir(el, gi)};
+            }
+        };
+        float ef[4] = {0.f, 0.f, 0.f, 0.f}, edt = 0.0f;
+        if (active) {
+            load(e, sn[1][le]);
+            if (ez > 0) load(e - nx, sn[0][le]);
+            if (ez < nz - 1) load(e + nx, sn[2][le]);
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
+                if (MODE == DG_TLSMOOTH || (MODE == DG_TLJV && A.rf)) ef[v] = A.rf[gi];
+            }
+            if (MODE == DG_TLSMOOTH) edt = A.dtauf[e];
+        }
+        const bool has_w = ex0 > 0 || K.periodic, has_e = ex0 + Ev < nx || K.periodic;
+        if (le == 0 && has_w) load(ez * nx + (ex0 - 1 + nx) % nx, se[0]);
+        if (le == 1 && has_e) load(ez * nx + (ex0 + Ev) % nx, se[1]);
+        __syncthreads();
+        // ---- volume fluxes (independent of the faces below) -----------------------
+        TL32 Up[4];
+        if (active) {
+            const int J = ez * NP1 + b;
+            TL32 U[4];
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                Up[v] = sn[1][le][v][node];
+                U[v] = Up[v] + TLc{K.ubvf[v * nrow + J]};
+            }
+            const TL32 ir = TLc{1.0f} / U[0];
+            const TL32 p = pressure(U[3], K.pc, nullptr);
+            TL32 Fx[4], Fz[4];
+            flux_c<TL32, 0>(U, U[1] * ir, p, Fx);
+            flux_c<TL32, 1>(U, U[2] * ir, p, Fz);
+            if (VISC) {
+                TL32 dx[4], dz[4], Gx[4], Gz[4];
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    TL32 sx = mk(0.0, TL32{}), sz = mk(0.0, TL32{});
+    #pragma unroll
+                    for (int q = 0; q < NP1; ++q) {
+                        sx = jfma(TLc{sDn[a][q]}, sn[1][le][v][b * NP1 + q], sx);
+                        sz = jfma(TLc{sDn[b][q]}, sn[1][le][v][q * NP1 + a], sz);
+                    }
+                    dx[v] = TLc{K.two_hxf} * sx;
+                    dz[v] = TLc{K.two_hzf} * sz + TLc{K.dubvf[v * nrow + J]};
+                }
+                viscous(U, dx, K.pc, Gx);
+                viscous(U, dz, K.pc, Gz);
+    #pragma unroll
+                for (int v = 1; v < 4; ++v) {
+                    Fx[v] = Fx[v] - Gx[v];
+                    Fz[v] = Fz[v] - Gz[v];
+                }
+            }
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                sg[0][le][v][node] = Fx[v].d;
+                sg[1][le][v][node] = Fz[v].d;
+            }
+        }
+        // ---- faces ------------------------------------------------------------
+        // value and derivative traces of variable v along NP1 nodes i0 + q st of one
+        // element's staged nodes, in the order of line_trace
+        auto trace = [&](const TL32 (*src)[NP], int v, int i0, int st, const float *pa, const float *pd, TL32 &tv,
+                         TL32 &td) {
+            tv = mk(0.0, TL32{});
+            td = mk(0.0, TL32{});
+    #pragma unroll
+            for (int q = 0; q < NP1; ++q) {
+                const TL32 u = src[v][i0 + q * st];
+                tv = jfma(TLc{pa[q]}, u, tv);
+                if (VISC) td = jfma(TLc{pd[q]}, u, td);
+            }
+        };
+        const TLc half = TLc{0.5f};
+        const int nxf = (Ev + 1) * NP1, nzf = 2 * Ev * NP1;
+        for (int t = threadIdx.x; t < nxf + nzf; t += blockDim.x) {
+            TL32 trL[4], trR[4], gL[4], gR[4], UL[4], UR[4], H[4], Phi[4], sLv[3], sRv[3];
+            if (t < nxf) {
+                const int f = t / NP1, sp = t % NP1;      // face f lies west of strip element f
+                const bool wallL = f == 0 && !has_w, wallR = f == Ev && !has_e;
+                const TL32 (*srcL)[NP] = f > 0 ? sn[1][f - 1] : se[0];
+                const TL32 (*srcR)[NP] = f < Ev ? sn[1][f] : se[1];
+                const int J = ez * NP1 + sp;
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    TL32 aL, aR, dL, dR;
+                    if (!wallR) trace(srcR, v, sp * NP1, 1, K.tlm, K.tdlm, aR, dR);
+                    if (!wallL) trace(srcL, v, sp * NP1, 1, K.tlp, K.tdlp, aL, dL);
+                    if (wallL) { aL = aR; dL = dR; }
+                    if (wallR) { aR = aL; dR = dL; }
+                    trL[v] = aL;
+                    trR[v] = aR;
+                    gL[v] = TLc{K.two_hxf} * dL;
+                    gR[v] = TLc{K.two_hxf} * dR;
+                    UL[v] = aL + TLc{K.ubvf[v * nrow + J]};
+                    UR[v] = aR + TLc{K.ubvf[v * nrow + J]};
+                }
+                TL32 Gh[4];
+                if (wallL) {
+                    mirror<TL32, 0>(UR, Gh);
+                    hllc<TL32, 0>(Gh, UR, K.pc, nullptr, H);
+                } else if (wallR) {
+                    mirror<TL32, 0>(UL, Gh);
+                    hllc<TL32, 0>(UL, Gh, K.pc, nullptr, H);
+                } else {
+                    hllc<TL32, 0>(UL, UR, K.pc, nullptr, H);
+                }
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) Phi[v] = H[v];
+                if (VISC && !wallL && !wallR) {
+                    TL32 FL[4], FR[4], Jp[4];
+                    viscous(UL, gL, K.pc, FL);
+                    viscous(UR, gR, K.pc, FR);
+    #pragma unroll
+                    for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
+    #pragma unroll
+                    for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TLc{K.eta_xf} * Jp[v];
+                    TL32 AL[4], AR[4];
+                    viscous(UL, Jp, K.pc, AL);
+                    viscous(UR, Jp, K.pc, AR);
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sLv[q] = half * AL[q + 1];
+                        sRv[q] = half * AR[q + 1];
+                    }
+                } else {
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
+                }
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) sPx[f][v][sp] = Phi[v].d;
+                if (VISC) {
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sSx[f][q][sp] = sLv[q].d;
+                        sSx[f][3 + q][sp] = sRv[q].d;
+                    }
+                }
+            } else {
+                const int u = t - nxf;
+                const int top = u / (Ev * NP1), l = (u / NP1) % Ev, sp = u % NP1;   // column a = sp
+                const int fz = ez + top;                 // global horizontal face 0..nz
+                const bool wallB = fz == 0, wallT = fz == nz;
+                TL32 gB[4], gT[4];
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    TL32 aB, aT, dB, dT;
+                    if (top) {   // own element below (trace at eta = +1), element ez+1 above
+                        trace(sn[1][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
+                        if (!wallT) trace(sn[2][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
+                        else { aT = aB; dT = dB; }
+                    } else {     // element ez-1 below, own element above (trace at eta = -1)
+                        trace(sn[1][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
+                        if (!wallB) trace(sn[0][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
+                        else { aB = aT; dB = dT; }
+                    }
+                    trL[v] = aB;
+                    trR[v] = aT;
+                    const TLc dub = TLc{K.dubhf[(size_t)v * (nz + 1) + fz]};
+                    gB[v] = TLc{K.two_hzf} * dB + dub;
+                    gT[v] = TLc{K.two_hzf} * dT + dub;
+                    UL[v] = aB + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
+                    UR[v] = aT + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
+                }
+                TL32 Gh[4];
+                if (wallB) {
+                    mirror<TL32, 1>(UR, Gh);
+                    hllc<TL32, 1>(Gh, UR, K.pc, nullptr, H);
+                } else if (wallT) {
+                    mirror<TL32, 1>(UL, Gh);
+                    hllc<TL32, 1>(UL, Gh, K.pc, nullptr, H);
+                } else {
+                    hllc<TL32, 1>(UL, UR, K.pc, nullptr, H);
+                }
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) Phi[v] = H[v];
+                if (VISC && !wallB && !wallT) {
+                    TL32 FB[4], FT[4], Jp[4];
+                    viscous(UL, gB, K.pc, FB);
+                    viscous(UR, gT, K.pc, FT);
+    #pragma unroll
+                    for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
+    #pragma unroll
+                    for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TLc{K.eta_zf} * Jp[v];
+                    TL32 AB[4], AT[4];
+                    viscous(UL, Jp, K.pc, AB);
+                    viscous(UR, Jp, K.pc, AT);
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sLv[q] = half * AB[q + 1];
+                        sRv[q] = half * AT[q + 1];
+                    }
+                } else {
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
+                }
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) sPz[top][l][v][sp] = Phi[v].d;
+                if (VISC) {
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sSz[top][l][q][sp] = sLv[q].d;
+                        sSz[top][l][3 + q][sp] = sRv[q].d;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!active && !(FIRST && TR.b)) return;
+        const float lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
+        const float lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
+        const float adtf = A.adtf;
+    #pragma unroll
+        for (int v = 0; v < 4 && active; ++v) {
+            float f = 0.0f;
+    #pragma unroll
+            for (int q = 0; q < NP1; ++q) {
+                f = fmaf(sDx[a][q], sg[0][le][v][b * NP1 + q], f);
+                f = fmaf(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
+            }
+            if (v == 2) f = fmaf(-K.gf, Up[0].d, f);
+            f = fmaf(lmxa, sPx[le][v][b], f);
+            f = fmaf(-lpxa, sPx[le + 1][v][b], f);
+            f = fmaf(lmzb, sPz[0][le][v][a], f);
+            f = fmaf(-lpzb, sPz[1][le][v][a], f);
+            if (VISC && v > 0) {
+                const int q = v - 1;
+                f = fmaf(dlmxa, sSx[le][3 + q][b], f);
+                f = fmaf(dlpxa, sSx[le + 1][q][b], f);
+                f = fmaf(dlmzb, sSz[0][le][3 + q][a], f);
+                f = fmaf(dlpzb, sSz[1][le][q][a], f);
+            }
             const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
-            if (MODE == DG_TLSMOOTH || (MODE == DG_TLJV && A.rf)) ef[v] = A.rf[gi];
+            const float z = Up[v].d;
+            const float jz = z - adtf * f;
+            if (MODE == DG_TLJV) {
+                const float dv = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
+                if (FIRST && TR.b) sdf[le][v][node] = dv;
+                else ((float *)A.out0)[gi] = dv;
+                if (FIRST) out1f[gi] = z;
+            } else {  // DG_TLSMOOTH
+                if (A.z0mode == 0) {
+                    ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
+                } else {
+                    const float st = (A.alphaf * edt) * (ef[v] - jz);
+                    ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
+                }
+            }
         }
-        if (MODE == DG_TLSMOOTH) edt = A.dtauf[e];
+        if (FIRST && TR.b) dgtl_transfer<NP1, E>(TR, sdf, smf, sg[0], le, node, ez, ex0 + le, active);
     }
-    const bool has_w = ex0 > 0 || K.periodic, has_e = ex0 + Ev < nx || K.periodic;
-    if (le == 0 && has_w) load(ez * nx + (ex0 - 1 + nx) % nx, se[0]);
-    if (le == 1 && has_e) load(ez * nx + (ex0 + Ev) % nx, se[1]);
-    __syncthreads();
-    // ---- volume fluxes (independent of the faces below) -----------------------
-    TL32 Up[4];
-    if (active) {
-        const int J = ez * NP1 + b;
-        TL32 U[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            Up[v] = sn[1][le][v][node];
-            U[v] = Up[v] + TLc{K.ubvf[v * nrow + J]};
-        }
-        const TL32 ir = TLc{1.0f} / U[0];
-        const TL32 p = pressure(U[3], K.pc, nullptr);
-        TL32 Fx[4], Fz[4];
-        flux_c<TL32, 0>(U, U[1] * ir, p, Fx);
-        flux_c<TL32, 1>(U, U[2] * ir, p, Fz);
-        if (VISC) {
-            TL32 dx[4], dz[4], Gx[4], Gz[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                TL32 sx = mk(0.0, TL32{}), sz = mk(0.0, TL32{});
-#pragma unroll
-                for (int q = 0; q < NP1; ++q) {
-                    sx = jfma(TLc{sDn[a][q]}, sn[1][le][v][b * NP1 + q], sx);
-                    sz = jfma(TLc{sDn[b][q]}, sn[1][le][v][q * NP1 + a], sz);
-                }
-                dx[v] = TLc{K.two_hxf} * sx;
-                dz[v] = TLc{K.two_hzf} * sz + TLc{K.dubvf[v * nrow + J]};
-            }
-            viscous(U, dx, K.pc, Gx);
-            viscous(U, dz, K.pc, Gz);
-#pragma unroll
-            for (int v = 1; v < 4; ++v) {
-                Fx[v] = Fx[v] - Gx[v];
-                Fz[v] = Fz[v] - Gz[v];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            sg[0][le][v][node] = Fx[v].d;
-            sg[1][le][v][node] = Fz[v].d;
-        }
-    }
-    // ---- faces ------------------------------------------------------------
-    // value and derivative traces of variable v along NP1 nodes i0 + q st of one
-    // element's staged nodes, in the order of line_trace
-    auto trace = [&](const TL32 (*src)[NP], int v, int i0, int st, const float *pa, const float *pd, TL32 &tv,
-                     TL32 &td) {
-        tv = mk(0.0, TL32{});
-        td = mk(0.0, TL32{});
-#pragma unroll
-        for (int q = 0; q < NP1; ++q) {
-            const TL32 u = src[v][i0 + q * st];
-            tv = jfma(TLc{pa[q]}, u, tv);
-            if (VISC) td = jfma(TLc{pd[q]}, u, td);
-        }
-    };
-    const TLc half = TLc{0.5f};
-    const int nxf = (Ev + 1) * NP1, nzf = 2 * Ev * NP1;
-    for (int t = threadIdx.x; t < nxf + nzf; t += blockDim.x) {
-        TL32 trL[4], trR[4], gL[4], gR[4], UL[4], UR[4], H[4], Phi[4], sLv[3], sRv[3];
-        if (t < nxf) {
-            const int f = t / NP1, sp = t % NP1;      // face f lies west of strip element f
-            const bool wallL = f == 0 && !has_w, wallR = f == Ev && !has_e;
-            const TL32 (*srcL)[NP] = f > 0 ? sn[1][f - 1] : se[0];
-            const TL32 (*srcR)[NP] = f < Ev ? sn[1][f] : se[1];
-            const int J = ez * NP1 + sp;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                TL32 aL, aR, dL, dR;
-                if (!wallR) trace(srcR, v, sp * NP1, 1, K.tlm, K.tdlm, aR, dR);
-                if (!wallL) trace(srcL, v, sp * NP1, 1, K.tlp, K.tdlp, aL, dL);
-                if (wallL) { aL = aR; dL = dR; }
-                if (wallR) { aR = aL; dR = dL; }
-                trL[v] = aL;
-                trR[v] = aR;
-                gL[v] = TLc{K.two_hxf} * dL;
-                gR[v] = TLc{K.two_hxf} * dR;
-                UL[v] = aL + TLc{K.ubvf[v * nrow + J]};
-                UR[v] = aR + TLc{K.ubvf[v * nrow + J]};
-            }
-            TL32 Gh[4];
-            if (wallL) {
-                mirror<TL32, 0>(UR, Gh);
-                hllc<TL32, 0>(Gh, UR, K.pc, nullptr, H);
-            } else if (wallR) {
-                mirror<TL32, 0>(UL, Gh);
-                hllc<TL32, 0>(UL, Gh, K.pc, nullptr, H);
-            } else {
-                hllc<TL32, 0>(UL, UR, K.pc, nullptr, H);
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) Phi[v] = H[v];
-            if (VISC && !wallL && !wallR) {
-                TL32 FL[4], FR[4], Jp[4];
-                viscous(UL, gL, K.pc, FL);
-                viscous(UR, gR, K.pc, FR);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
-#pragma unroll
-                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TLc{K.eta_xf} * Jp[v];
-                TL32 AL[4], AR[4];
-                viscous(UL, Jp, K.pc, AL);
-                viscous(UR, Jp, K.pc, AR);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    sLv[q] = half * AL[q + 1];
-                    sRv[q] = half * AR[q + 1];
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sPx[f][v][sp] = Phi[v].d;
-            if (VISC) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    sSx[f][q][sp] = sLv[q].d;
-                    sSx[f][3 + q][sp] = sRv[q].d;
-                }
-            }
-        } else {
-            const int u = t - nxf;
-            const int top = u / (Ev * NP1), l = (u / NP1) % Ev, sp = u % NP1;   // column a = sp
-            const int fz = ez + top;                 // global horizontal face 0..nz
-            const bool wallB = fz == 0, wallT = fz == nz;
-            TL32 gB[4], gT[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                TL32 aB, aT, dB, dT;
-                if (top) {   // own element below (trace at eta = +1), element ez+1 above
-                    trace(sn[1][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
-                    if (!wallT) trace(sn[2][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
-                    else { aT = aB; dT = dB; }
-                } else {     // element ez-1 below, own element above (trace at eta = -1)
-                    trace(sn[1][l], v, sp, NP1, K.tlm, K.tdlm, aT, dT);
-                    if (!wallB) trace(sn[0][l], v, sp, NP1, K.tlp, K.tdlp, aB, dB);
-                    else { aB = aT; dB = dT; }
-                }
-                trL[v] = aB;
-                trR[v] = aT;
-                const TLc dub = TLc{K.dubhf[(size_t)v * (nz + 1) + fz]};
-                gB[v] = TLc{K.two_hzf} * dB + dub;
-                gT[v] = TLc{K.two_hzf} * dT + dub;
-                UL[v] = aB + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
-                UR[v] = aT + TLc{K.ubhf[(size_t)v * (nz + 1) + fz]};
-            }
-            TL32 Gh[4];
-            if (wallB) {
-                mirror<TL32, 1>(UR, Gh);
-                hllc<TL32, 1>(Gh, UR, K.pc, nullptr, H);
-            } else if (wallT) {
-                mirror<TL32, 1>(UL, Gh);
-                hllc<TL32, 1>(UL, Gh, K.pc, nullptr, H);
-            } else {
-                hllc<TL32, 1>(UL, UR, K.pc, nullptr, H);
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) Phi[v] = H[v];
-            if (VISC && !wallB && !wallT) {
-                TL32 FB[4], FT[4], Jp[4];
-                viscous(UL, gB, K.pc, FB);
-                viscous(UR, gT, K.pc, FT);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
-#pragma unroll
-                for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TLc{K.eta_zf} * Jp[v];
-                TL32 AB[4], AT[4];
-                viscous(UL, Jp, K.pc, AB);
-                viscous(UR, Jp, K.pc, AT);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    sLv[q] = half * AB[q + 1];
-                    sRv[q] = half * AT[q + 1];
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) sLv[q] = sRv[q] = mk(0.0, TL32{});
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sPz[top][l][v][sp] = Phi[v].d;
-            if (VISC) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    sSz[top][l][q][sp] = sLv[q].d;
-                    sSz[top][l][3 + q][sp] = sRv[q].d;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (!active && !(FIRST && TR.b)) return;
-    const float lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
-    const float lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
-    const float adtf = A.adtf;
-#pragma unroll
-    for (int v = 0; v < 4 && active; ++v) {
-        float f = 0.0f;
-#pragma unroll
-        for (int q = 0; q < NP1; ++q) {
-            f = fmaf(sDx[a][q], sg[0][le][v][b * NP1 + q], f);
-            f = fmaf(sDz[b][q], sg[1][le][v][q * NP1 + a], f);
-        }
-        if (v == 2) f = fmaf(-K.gf, Up[0].d, f);
-        f = fmaf(lmxa, sPx[le][v][b], f);
-        f = fmaf(-lpxa, sPx[le + 1][v][b], f);
-        f = fmaf(lmzb, sPz[0][le][v][a], f);
-        f = fmaf(-lpzb, sPz[1][le][v][a], f);
-        if (VISC && v > 0) {
-            const int q = v - 1;
-            f = fmaf(dlmxa, sSx[le][3 + q][b], f);
-            f = fmaf(dlpxa, sSx[le + 1][q][b], f);
-            f = fmaf(dlmzb, sSz[0][le][3 + q][a], f);
-            f = fmaf(dlpzb, sSz[1][le][q][a], f);
-        }
-        const size_t gi = (size_t)v * N1 + (size_t)e * NP + node;
-        const float z = Up[v].d;
-        const float jz = z - adtf * f;
-        if (MODE == DG_TLJV) {
-            const float dv = A.rf ? ef[v] - jz : jz;   // with r given: the defect r - G'z
-            if (FIRST && TR.b) sdf[le][v][node] = dv;
-            else ((float *)A.out0)[gi] = dv;
-            if (FIRST) out1f[gi] = z;
-        } else {  // DG_TLSMOOTH
-            if (A.z0mode == 0) {
-                ((float *)A.out0)[gi] = z + edt * (ef[v] - jz);
-            } else {
-                const float st = (A.alphaf * edt) * (ef[v] - jz);
-                ((float *)A.out0)[gi] = A.z0mode == 1 ? ((const float *)A.z0)[gi] + st : st;
-            }
-        }
-    }
-    if (FIRST && TR.b) dgtl_transfer<NP1, E>(TR, sdf, smf, sg[0], le, node, ez, ex0 + le, active);
+};
+template <int NP1, bool VISC, int MODE, int FIRST>
+__global__ void __launch_bounds__(128, VISC ? 5 : 8) k_dgtl(DGK K, DGArgs A, float *out1f, TransferOut TR) {
+    k_dgtl_b<NP1, VISC, MODE, FIRST>::run(blockIdx.x, gridDim.x, K, A, out1f, TR);
 }
 
 // background fluxes at node rows and horizontal faces, with the residual's own
@@ -1033,17 +1068,17 @@ int launch(jfnk_ctx *c, const DGK &K, const Loader<T, IN> &ld, const DGArgs &a, 
     const long long nf = (long long)K.nz * (K.nx + 1) * NP1 + (long long)(K.nz + 1) * K.nx * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
     const int tf = c->opts.tile_faces;
-    jf_launch(k_faces<T, IN, NP1, VISC>, (unsigned)((nf + tf - 1) / tf), tf, 0, s, K, ld, phix, symx, phiz, symz,
+    jf_launch<k_faces_b<T, IN, NP1, VISC>>(k_faces<T, IN, NP1, VISC>, (unsigned)((nf + tf - 1) / tf), tf, 0, s, K, ld, phix, symx, phiz, symz,
               a.tr_out, a.tr_in); jf_launched();
     if (c->timing) JF_CK(cudaEventRecord(c->tev[1], s));
     if (c->opts.tile_volume == 1) {
         constexpr int EPB = EPBOf<NP1, 1>::value;
         const int nb = (K.n_el + EPB - 1) / EPB;
-        jf_launch(k_volume<T, IN, MODE, NP1, VISC, 1>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
+        jf_launch<k_volume_b<T, IN, MODE, NP1, VISC, 1>>(k_volume<T, IN, MODE, NP1, VISC, 1>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
     } else {
         constexpr int EPB = EPBOf<NP1, 2>::value;
         const int nb = (K.n_el + EPB - 1) / EPB;
-        jf_launch(k_volume<T, IN, MODE, NP1, VISC, 2>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
+        jf_launch<k_volume_b<T, IN, MODE, NP1, VISC, 2>>(k_volume<T, IN, MODE, NP1, VISC, 2>, nb, EPB * NP1 * NP1, 0, s, K, ld, a, phix, symx, phiz, symz);
     }
     jf_launched();
     JF_CK(cudaGetLastError());
@@ -1068,10 +1103,10 @@ int launch_tl(jfnk_ctx *c, const DGK &K, const DGArgs &a, cudaStream_t s) {
     const int threads = E * NP1 * NP1;
     if (c->timing) JF_CK(cudaEventRecord(c->tev[0], s));
     if (MODE == DG_TLJV && a.out1f)
-        jf_launch(k_dgtl<NP1, VISC, MODE, 1>, nb, threads, 0, s, K, a, a.out1f,
+        jf_launch<k_dgtl_b<NP1, VISC, MODE, 1>>(k_dgtl<NP1, VISC, MODE, 1>, nb, threads, 0, s, K, a, a.out1f,
                   a.tro ? *a.tro : TransferOut{});
     else
-        jf_launch(k_dgtl<NP1, VISC, MODE, 0>, nb, threads, 0, s, K, a, (float *)nullptr, TransferOut{});
+        jf_launch<k_dgtl_b<NP1, VISC, MODE, 0>>(k_dgtl<NP1, VISC, MODE, 0>, nb, threads, 0, s, K, a, (float *)nullptr, TransferOut{});
     jf_launched();
     JF_CK(cudaGetLastError());
     if (c->timing) {
@@ -1143,12 +1178,37 @@ void launch_grp(const DGMember *dmem, const std::vector<DGMember> &h, int first,
     const unsigned fb = last.fb0 + (unsigned)((nfl + GRP_FACE_THREADS - 1) / GRP_FACE_THREADS);
     constexpr int EPB = EPBOf<NP1, 2>::value;
     const unsigned vb = last.vb0 + (unsigned)((last.K.n_el + EPB - 1) / EPB);
-    jf_launch(k_faces_grp<NP1, VISC>, fb, GRP_FACE_THREADS, 0, s, dmem + first, cnt);
-    jf_launch(k_volume_grp<NP1, VISC>, vb, EPB * NP1 * NP1, 0, s, dmem + first, cnt);
+    jf_launch_now(k_faces_grp<NP1, VISC>, fb, GRP_FACE_THREADS, 0, s, dmem + first, cnt);
+    jf_launch_now(k_volume_grp<NP1, VISC>, vb, EPB * NP1 * NP1, 0, s, dmem + first, cnt);
     jf_launched(2);
 }
 
 }  // namespace
+
+// The operator kernels of one order k = NP1 - 1.  The library compiles this
+// file once per order (JF_DG_NP1 = 2..5, in parallel); the order-independent
+// functions below come with the first.  Compiled without JF_DG_NP1, one unit
+// holds every order.
+template <int NP1>
+int dg_dispatch(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+#if !defined(JF_DG_NP1)
+#define JF_DG_ORDERS(X) X(2) X(3) X(4) X(5)
+#else
+#define JF_DG_ORDERS(X) X(JF_DG_NP1)
+#endif
+#define JF_DG_DEFINE(n)                                                                              \
+    template <>                                                                                     \
+    int dg_dispatch<n>(jfnk_ctx * c, int mode, const DGArgs &a, cudaStream_t s) {                   \
+        return c->phys.mu != 0.0 ? dispatch_mode<n, true>(c, mode, a, s) : dispatch_mode<n, false>(c, mode, a, s); \
+    }
+JF_DG_ORDERS(JF_DG_DEFINE)
+
+#if !defined(JF_DG_NP1) || JF_DG_NP1 == 2
+#if defined(JF_DG_NP1)
+template <> int dg_dispatch<3>(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+template <> int dg_dispatch<4>(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+template <> int dg_dispatch<5>(jfnk_ctx *c, int mode, const DGArgs &a, cudaStream_t s);
+#endif
 
 int dg_setup_background(jfnk_ctx *c, cudaStream_t s) {
     DGK K = make_K(c);
@@ -1165,12 +1225,11 @@ int dg_apply(jfnk_ctx *c, int mode, const DGArgs &a_in, cudaStream_t s) {
     c->dg_calls++;
     // the stored traces belong to the cached f(U): any other writer of the cache drops them
     if (a.out0 == c->fU || a.out1 == c->fU) c->tr_valid = a.tr_out == c->trU ? 1 : 0;
-    const bool visc = c->phys.mu != 0.0;
     switch (c->np1) {
-        case 2: return visc ? dispatch_mode<2, true>(c, mode, a, s) : dispatch_mode<2, false>(c, mode, a, s);
-        case 3: return visc ? dispatch_mode<3, true>(c, mode, a, s) : dispatch_mode<3, false>(c, mode, a, s);
-        case 4: return visc ? dispatch_mode<4, true>(c, mode, a, s) : dispatch_mode<4, false>(c, mode, a, s);
-        case 5: return visc ? dispatch_mode<5, true>(c, mode, a, s) : dispatch_mode<5, false>(c, mode, a, s);
+        case 2: return dg_dispatch<2>(c, mode, a, s);
+        case 3: return dg_dispatch<3>(c, mode, a, s);
+        case 4: return dg_dispatch<4>(c, mode, a, s);
+        case 5: return dg_dispatch<5>(c, mode, a, s);
     }
     return JFNK_EINVAL;
 }
@@ -1236,3 +1295,4 @@ int dg_residual_grouped(jfnk_ctx *const *ctx, int n, const double *const *U, dou
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
+#endif  // order-independent part

@@ -6,8 +6,13 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <string.h>
+
+#include <functional>
+#include <type_traits>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "../../include/jfnk.h"
 #include "physics.cuh"
@@ -29,8 +34,8 @@ __device__ __forceinline__ void jf_pdl_enter() {
 #endif
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t jf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                             Args &&...args) {
+inline cudaError_t jf_launch_now(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -47,6 +52,132 @@ inline cudaError_t jf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, si
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
+
+// ---- lock-step replay of several contexts' launches (ensembles) -----------
+// Every kernel of the solver path is a body struct B (B::run(bid, nblk, args...),
+// B::TPB / B::MINB its launch bounds) wrapped by a __global__ kernel that passes
+// blockIdx.x and gridDim.x.  While a host thread records (t_jf_rec set, see
+// batch.cu), jf_launch stores the launch instead of issuing it: its argument
+// record and the grouped twin k_grouped<B, A...>, which runs the same body for
+// the blocks of several members in one launch -- each block finds its member in
+// a table of (first block, block count, argument record) and runs the body with
+// the member's own block index and count, so every member computes exactly what
+// its own launch computes.
+// Bodies take their arguments by const reference, so that a grouped block reads
+// its member's arguments where they lie in the table (no per-thread copy).
+template <class T> using JfArg = const T &;
+
+template <class... A> struct JfPack;
+template <> struct JfPack<> {};
+template <class H, class... R> struct JfPack<H, R...> {
+    H h;
+    JfPack<R...> r;
+};
+inline JfPack<> jf_pack() { return {}; }
+template <class H, class... R>
+inline JfPack<H, R...> jf_pack(H h, R... r) {
+    return JfPack<H, R...>{h, jf_pack(r...)};
+}
+template <class... A> struct JfEnt {
+    unsigned b0, nb;     // the member's first block in the grouped launch, its block count
+    JfPack<A...> a;
+};
+
+constexpr int jf_tpb(int tpb) { return tpb > 0 ? tpb : 1024; }
+constexpr int jf_minb(int tpb, int minb) { return minb > 0 ? minb : (tpb > 0 ? 1024 / tpb : 1); }
+
+#ifdef __CUDACC__
+template <class B, class... Done>
+__device__ __forceinline__ void jf_call(unsigned bid, unsigned nb, const JfPack<> &, const Done &...d) {
+    B::run(bid, nb, d...);
+}
+template <class B, class H, class... R, class... Done>
+__device__ __forceinline__ void jf_call(unsigned bid, unsigned nb, const JfPack<H, R...> &p, const Done &...d) {
+    jf_call<B>(bid, nb, p.r, d..., p.h);
+}
+template <class B, class... A>
+// (register target of the twin: the body's own bounds, else 64 registers a thread)
+__global__ void __launch_bounds__(jf_tpb(B::TPB), jf_minb(B::TPB, B::MINB))
+    k_grouped(const JfEnt<A...> *__restrict__ t, int n) {
+    const unsigned b = blockIdx.x;
+    int lo = 0, hi = n - 1;   // last member whose first block is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t[mid].b0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    jf_call<B>(b - t[lo].b0, t[lo].nb, t[lo].a);
+}
+#endif
+
+// One recorded operation of a member: a launch that can join a grouped launch
+// (glaunch set: the same body and argument types, block shape and shared memory
+// join), or any other stream operation replayed as is (run).
+struct JfOp {
+    std::function<cudaError_t(cudaStream_t)> run;
+    cudaError_t (*glaunch)(const void *dtab, int n, unsigned total, dim3 block, size_t smem, cudaStream_t s);
+    std::vector<unsigned char> ent;   // the member's JfEnt (b0 filled in at replay)
+    unsigned nb;
+    dim3 block;
+    size_t smem;
+    bool kernel;   // a kernel launch (counted in the launch statistics)
+};
+struct JfLockstep;   // batch.cu
+struct JfRecorder {
+    std::vector<JfOp> ops;
+    JfLockstep *ls;
+    int member;
+};
+extern thread_local JfRecorder *t_jf_rec;
+
+template <class B, class... A>
+cudaError_t jf_group_launch(const void *dtab, int n, unsigned total, dim3 block, size_t smem, cudaStream_t s) {
+#ifdef __CUDACC__
+    return jf_launch_now(k_grouped<B, A...>, dim3(total), block, smem, s, (const JfEnt<A...> *)dtab, n);
+#else
+    return cudaErrorNotSupported;
+#endif
+}
+
+// B::GROUP (default true): whether body B has a grouped twin; without one its
+// recorded launches replay one member at a time
+template <class B, class = void> struct JfGroupOk { static constexpr bool value = true; };
+template <class B> struct JfGroupOk<B, std::void_t<decltype(B::GROUP)>> { static constexpr bool value = B::GROUP; };
+
+template <class B, class... KArgs>
+cudaError_t jf_record(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, KArgs... a) {
+    JfOp op;
+    op.run = [=](cudaStream_t s) { return jf_launch_now(kernel, grid, block, smem, s, a...); };
+    op.glaunch = nullptr;
+    op.kernel = true;
+    if constexpr (JfGroupOk<B>::value) {
+        op.glaunch = &jf_group_launch<B, KArgs...>;
+        JfEnt<KArgs...> e{0u, grid.x, jf_pack(a...)};
+        op.ent.resize(sizeof(e));
+        memcpy(op.ent.data(), &e, sizeof(e));
+    }
+    op.nb = grid.x;
+    op.block = block;
+    op.smem = smem;
+    t_jf_rec->ops.push_back(std::move(op));
+    return cudaSuccess;
+}
+
+// Launch kernel (the wrapper of body B) on s, or record it (lock-step replay).
+template <class B, typename... KArgs, typename... Args>
+inline cudaError_t jf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+    if (t_jf_rec) return jf_record<B, KArgs...>(kernel, grid, block, smem, KArgs(std::forward<Args>(args))...);
+    return jf_launch_now(kernel, grid, block, smem, s, std::forward<Args>(args)...);
+}
+
+// Stream operations of the solver path: issued on s, or recorded in order with
+// the member's launches.  jf_sync waits for the stream (recording: for the
+// replay of everything recorded so far).  A host-to-device copy is recorded with
+// a copy of its source bytes.
+cudaError_t jf_memcpy(void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t s);
+cudaError_t jf_memset(void *dst, int v, size_t n, cudaStream_t s);
+cudaError_t jf_sync(cudaStream_t s);
 
 // Fixed 1D tables of the nodal Q_k space on Gauss-Legendre nodes (k <= 4).
 struct DGTab {
@@ -167,6 +298,7 @@ enum { S_NORM = 0, S_EPS = 1, S_W1 = 2, S_FLAG = 3, S_INV = 4, S_EPSDG = 5, S_EP
 extern unsigned long long g_jf_launches;
 extern thread_local unsigned long long t_jf_launches;
 inline void jf_launched(unsigned n = 1) {
+    if (t_jf_rec) return;   // recorded launches are counted when they are replayed
     __atomic_fetch_add(&g_jf_launches, (unsigned long long)n, __ATOMIC_RELAXED);
     t_jf_launches += n;
 }

@@ -330,45 +330,58 @@ JF_D S gprime_of(const FLoad<T, IN> &ld, S x, T f, const double *fu, size_t gi, 
 // One thread (L = 1) or four lanes (L = 4, lane q owns variable q) per cell of
 // an NX x NZ level.
 template <class T, int IN, int MODE, bool VISC, int L>
+struct k_fv_b {
+    static constexpr int TPB = 256, MINB = 0;
+    static constexpr bool GROUP = !VISC && std::is_same<T, TL32>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<FVK> K,
+                                               JfArg<FLoad<T, IN>> ld0, JfArg<const typename SOf<T>::type *> xin,
+                                               JfArg<const typename SOf<T>::type *> b,
+                                               JfArg<const typename SOf<T>::type *> dtau, JfArg<const double *> fu,
+                                               JfArg<double> adt, JfArg<typename SOf<T>::type *> out, JfArg<int> bf16,
+                                               JfArg<RKS> rk) {
+        jf_pdl_enter();
+        typedef typename SOf<T>::type S;
+        __shared__ PowTab spt;
+        if (IN < 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
+        FLoad<T, IN> ld = ld0;
+        ld.prepare();
+        __syncthreads();
+        const float adtf = IN >= 2 ? K.adtf : 0.0f;
+        const size_t n1 = (size_t)K.NX * K.NZ;
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        const int q = L == 4 ? (int)(t & 3) : 0;
+        const size_t cell = L == 4 ? (t >> 2) : t;
+        const bool live = cell < n1;
+        if (L == 1 && !live) return;
+        const size_t c = live ? cell : n1 - 1;   // idle lanes still join the shuffles
+        const int I = (int)(c % K.NX), Jz = (int)(c / K.NX);
+        T f[4];
+        if (L == 4) f[0] = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+        else fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
+        if (!live) return;
+    #pragma unroll
+        for (int k = 0; k < (L == 4 ? 1 : 4); ++k) {
+            const int v = L == 4 ? q : k;
+            const size_t gi = (size_t)v * n1 + c;
+            if (MODE == FV_RES) {
+                out[gi] = (S)oval(f[k]);
+            } else {
+                const S x = (S)ld.dir(v, c, I, Jz);
+                const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, adtf, ld.step());
+                if (MODE == FV_SMOOTH)
+                    out[gi] = store_round<S>(rk_stage<S>(rk, x, dtau[c], b[gi] - gx, gi), bf16);
+                else
+                    out[gi] = gx - b[gi];
+            }
+        }
+    }
+};
+template <class T, int IN, int MODE, bool VISC, int L>
 __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *xin,
                                             const typename SOf<T>::type *b, const typename SOf<T>::type *dtau,
                                             const double *fu, double adt, typename SOf<T>::type *out,
                                             int bf16, RKS rk) {
-    jf_pdl_enter();
-    typedef typename SOf<T>::type S;
-    __shared__ PowTab spt;
-    if (IN < 2) load_pt(&spt, K.pt);   // the FP32 tangent power needs no table
-    FLoad<T, IN> ld = ld0;
-    ld.prepare();
-    __syncthreads();
-    const float adtf = IN >= 2 ? K.adtf : 0.0f;
-    const size_t n1 = (size_t)K.NX * K.NZ;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int q = L == 4 ? (int)(t & 3) : 0;
-    const size_t cell = L == 4 ? (t >> 2) : t;
-    const bool live = cell < n1;
-    if (L == 1 && !live) return;
-    const size_t c = live ? cell : n1 - 1;   // idle lanes still join the shuffles
-    const int I = (int)(c % K.NX), Jz = (int)(c / K.NX);
-    T f[4];
-    if (L == 4) f[0] = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
-    else fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
-    if (!live) return;
-#pragma unroll
-    for (int k = 0; k < (L == 4 ? 1 : 4); ++k) {
-        const int v = L == 4 ? q : k;
-        const size_t gi = (size_t)v * n1 + c;
-        if (MODE == FV_RES) {
-            out[gi] = (S)oval(f[k]);
-        } else {
-            const S x = (S)ld.dir(v, c, I, Jz);
-            const S gx = gprime_of<T, IN, S>(ld, x, f[k], fu, gi, adt, adtf, ld.step());
-            if (MODE == FV_SMOOTH)
-                out[gi] = store_round<S>(rk_stage<S>(rk, x, dtau[c], b[gi] - gx, gi), bf16);
-            else
-                out[gi] = gx - b[gi];
-        }
-    }
+    k_fv_b<T, IN, MODE, VISC, L>::run(blockIdx.x, gridDim.x, K, ld0, xin, b, dtau, fu, adt, out, bf16, rk);
 }
 
 // Defect and restriction in one pass: the defect g'x - b of every child cell of
@@ -378,77 +391,89 @@ __global__ void __launch_bounds__(256) k_fv(FVK K, FLoad<T, IN> ld0, const typen
 // sixteen lanes per coarse cell (four lanes per child, children summed by
 // shuffles); L = 4 otherwise: four lanes per coarse cell loop over the children.
 template <class T, int IN, bool VISC, int L, bool FAC2>
+struct k_fv_defect_restrict_b {
+    static constexpr int TPB = 256, MINB = 0;
+    static constexpr bool GROUP = !VISC && std::is_same<T, TL32>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<FVK> K,
+                                               JfArg<FLoad<T, IN>> ld0, JfArg<const typename SOf<T>::type *> b,
+                                               JfArg<const double *> fu, JfArg<double> adt, JfArg<int> fac,
+                                               JfArg<typename SOf<T>::type *> bc, JfArg<typename SOf<T>::type *> xc,
+                                               JfArg<const typename SOf<T>::type *> dtau_c, JfArg<int> bf16) {
+        jf_pdl_enter();
+        typedef typename SOf<T>::type S;
+        __shared__ PowTab spt;
+        if (IN < 2) load_pt(&spt, K.pt);
+        FLoad<T, IN> ld = ld0;
+        ld.prepare();
+        __syncthreads();
+        const int NXc = K.NX / fac, NZc = K.NZ / fac;
+        const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        const double eps = ld.step();
+        const float adtf = IN >= 2 ? K.adtf : 0.0f;
+        if (L == 1) {
+            if (t >= nc) return;
+            const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
+            S acc[4] = {0, 0, 0, 0};
+            for (int jj = 0; jj < fac; ++jj)
+                for (int ii = 0; ii < fac; ++ii) {
+                    const int I = Ic * fac + ii, Jz = Jc * fac + jj;
+                    const size_t c = (size_t)Jz * K.NX + I;
+                    T f[4];
+                    fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
+    #pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const size_t gi = (size_t)v * n1 + c;
+                        acc[v] += gprime_of<T, IN, S>(ld, (S)ld.dir(v, c, I, Jz), f[v], fu, gi, adt, adtf, eps) - b[gi];
+                    }
+                }
+            const S inv = (S)1 / (S)(fac * fac);
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const S bv = store_round<S>(acc[v] * inv, bf16);
+                bc[(size_t)v * nc + t] = bv;
+                if (xc) xc[(size_t)v * nc + t] = store_round<S>(dtau_c[t] * bv, bf16);
+            }
+            return;
+        }
+        const int q = (int)(t & 3);
+        const size_t g = FAC2 ? (t >> 4) : (t >> 2);
+        const bool live = g < nc;
+        const size_t cc = live ? g : nc - 1;
+        const int Ic = (int)(cc % NXc), Jc = (int)(cc / NXc);
+        S acc = 0;
+        if (FAC2) {
+            const int ch = (int)((t >> 2) & 3);
+            const int I = 2 * Ic + (ch & 1), Jz = 2 * Jc + (ch >> 1);
+            const size_t c = (size_t)Jz * K.NX + I;
+            const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+            const size_t gi = (size_t)q * n1 + c;
+            const S d = gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
+            const S d2 = d + __shfl_xor_sync(0xffffffffu, d, 4);
+            acc = d2 + __shfl_xor_sync(0xffffffffu, d2, 8);
+            if (ch != 0) return;
+        } else {
+            for (int jj = 0; jj < fac; ++jj)
+                for (int ii = 0; ii < fac; ++ii) {
+                    const int I = Ic * fac + ii, Jz = Jc * fac + jj;
+                    const size_t c = (size_t)Jz * K.NX + I;
+                    const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
+                    const size_t gi = (size_t)q * n1 + c;
+                    acc += gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
+                }
+        }
+        if (!live) return;
+        const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
+        bc[(size_t)q * nc + cc] = bv;
+        if (xc) xc[(size_t)q * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
+    }
+};
+template <class T, int IN, bool VISC, int L, bool FAC2>
 __global__ void __launch_bounds__(256) k_fv_defect_restrict(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *b,
                                                             const double *fu, double adt, int fac,
                                                             typename SOf<T>::type *bc, typename SOf<T>::type *xc,
                                                             const typename SOf<T>::type *dtau_c, int bf16) {
-    jf_pdl_enter();
-    typedef typename SOf<T>::type S;
-    __shared__ PowTab spt;
-    if (IN < 2) load_pt(&spt, K.pt);
-    FLoad<T, IN> ld = ld0;
-    ld.prepare();
-    __syncthreads();
-    const int NXc = K.NX / fac, NZc = K.NZ / fac;
-    const size_t nc = (size_t)NXc * NZc, n1 = (size_t)K.NX * K.NZ;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double eps = ld.step();
-    const float adtf = IN >= 2 ? K.adtf : 0.0f;
-    if (L == 1) {
-        if (t >= nc) return;
-        const int Ic = (int)(t % NXc), Jc = (int)(t / NXc);
-        S acc[4] = {0, 0, 0, 0};
-        for (int jj = 0; jj < fac; ++jj)
-            for (int ii = 0; ii < fac; ++ii) {
-                const int I = Ic * fac + ii, Jz = Jc * fac + jj;
-                const size_t c = (size_t)Jz * K.NX + I;
-                T f[4];
-                fv_cell_op<T, IN, VISC>(K, ld, &spt, c, I, Jz, f);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const size_t gi = (size_t)v * n1 + c;
-                    acc[v] += gprime_of<T, IN, S>(ld, (S)ld.dir(v, c, I, Jz), f[v], fu, gi, adt, adtf, eps) - b[gi];
-                }
-            }
-        const S inv = (S)1 / (S)(fac * fac);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const S bv = store_round<S>(acc[v] * inv, bf16);
-            bc[(size_t)v * nc + t] = bv;
-            if (xc) xc[(size_t)v * nc + t] = store_round<S>(dtau_c[t] * bv, bf16);
-        }
-        return;
-    }
-    const int q = (int)(t & 3);
-    const size_t g = FAC2 ? (t >> 4) : (t >> 2);
-    const bool live = g < nc;
-    const size_t cc = live ? g : nc - 1;
-    const int Ic = (int)(cc % NXc), Jc = (int)(cc / NXc);
-    S acc = 0;
-    if (FAC2) {
-        const int ch = (int)((t >> 2) & 3);
-        const int I = 2 * Ic + (ch & 1), Jz = 2 * Jc + (ch >> 1);
-        const size_t c = (size_t)Jz * K.NX + I;
-        const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
-        const size_t gi = (size_t)q * n1 + c;
-        const S d = gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
-        const S d2 = d + __shfl_xor_sync(0xffffffffu, d, 4);
-        acc = d2 + __shfl_xor_sync(0xffffffffu, d2, 8);
-        if (ch != 0) return;
-    } else {
-        for (int jj = 0; jj < fac; ++jj)
-            for (int ii = 0; ii < fac; ++ii) {
-                const int I = Ic * fac + ii, Jz = Jc * fac + jj;
-                const size_t c = (size_t)Jz * K.NX + I;
-                const T fq = fv_cell_op4<T, IN, VISC>(K, ld, &spt, c, I, Jz, q);
-                const size_t gi = (size_t)q * n1 + c;
-                acc += gprime_of<T, IN, S>(ld, (S)ld.dir(q, c, I, Jz), fq, fu, gi, adt, adtf, eps) - b[gi];
-            }
-    }
-    if (!live) return;
-    const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
-    bc[(size_t)q * nc + cc] = bv;
-    if (xc) xc[(size_t)q * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
+    k_fv_defect_restrict_b<T, IN, VISC, L, FAC2>::run(blockIdx.x, gridDim.x, K, ld0, b, fu, adt, fac, bc, xc, dtau_c, bf16);
 }
 
 // Face-once form for large levels: a block owns a tile of TX x TZ cells.  The
@@ -463,185 +488,199 @@ enum { FV_DEFRES = 3 };
 constexpr int FV_TX = 32;
 
 template <class T, int IN, int MODE, bool VISC, int TZ>
+struct k_fv_tile_b {
+    static constexpr int TPB = FV_TX * TZ, MINB = 0;
+    static constexpr bool GROUP = !VISC && std::is_same<T, TL32>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<FVK> K,
+                                               JfArg<FLoad<T, IN>> ld0, JfArg<const typename SOf<T>::type *> b,
+                                               JfArg<const typename SOf<T>::type *> dtau, JfArg<const double *> fu,
+                                               JfArg<double> adt, JfArg<typename SOf<T>::type *> out,
+                                               JfArg<typename SOf<T>::type *> xc,
+                                               JfArg<const typename SOf<T>::type *> dtau_c, JfArg<int> bf16,
+                                               JfArg<RKS> rk) {
+        jf_pdl_enter();
+        typedef typename SOf<T>::type S;
+        constexpr int TX = FV_TX;
+        // the FP64 power table (the FP32 tangent power needs none)
+        __shared__ double spt_raw[IN < 2 ? sizeof(PowTab) / sizeof(double) : 1];
+        PowTab &spt = *reinterpret_cast<PowTab *>(spt_raw);
+        // the tile's cells and a one-cell halo as face sides: state, 1/rho, p, c
+        // (one pressure / sound speed per cell instead of one per face and side)
+        __shared__ T sU[4][TZ + 2][TX + 2];
+        __shared__ T sIr[TZ + 2][TX + 2], sP[TZ + 2][TX + 2], sC[TZ + 2][TX + 2];
+        __shared__ S sGx[4][TZ][TX + 1];   // net flux H - V through the west face of local cell (i, j)
+        __shared__ S sGz[4][TZ + 1][TX];   // ... through the south face
+        __shared__ S sD[MODE == FV_DEFRES ? 4 : 1][MODE == FV_DEFRES ? TZ : 1][MODE == FV_DEFRES ? TX : 1];
+        if (IN < 2) load_pt(&spt, K.pt);
+        FLoad<T, IN> ld = ld0;
+        ld.prepare();
+        const int NX = K.NX, NZ = K.NZ;
+        const size_t n1 = (size_t)NX * NZ;
+        const int ntx = (NX + TX - 1) / TX;
+        const int I0 = (int)(jf_bid % ntx) * TX, J0 = (int)(jf_bid / ntx) * TZ;
+        const int tx = threadIdx.x % TX, tz = threadIdx.x / TX;
+        const int I = I0 + tx, J = J0 + tz;
+        const bool live = I < NX && J < NZ;
+        const size_t c = live ? (size_t)J * NX + I : 0;
+        // the epilogue's operands, loaded before the face work so that their latency overlaps it
+        S xv[4], bv[4], up0 = 0, dtc = 0;
+        double fuv[4] = {0.0, 0.0, 0.0, 0.0};
+        if (live) {
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const size_t gi = (size_t)v * n1 + c;
+                xv[v] = MODE == FV_RES ? (S)0 : (S)ld.dir(v, c, I, J);
+                bv[v] = MODE == FV_RES ? (S)0 : b[gi];
+                if (IN == 1) fuv[v] = fu[gi];
+            }
+            up0 = (S)oval(ld(0, c, I, J));
+            if (MODE == FV_SMOOTH) dtc = dtau[c];
+        }
+        if (IN < 2) __syncthreads();   // the power table
+        for (int idx = threadIdx.x; idx < (TZ + 2) * (TX + 2); idx += blockDim.x) {
+            const int li = idx % (TX + 2), lj = idx / (TX + 2);
+            int I = I0 + li - 1;
+            const int J = J0 + lj - 1;
+            if (K.periodic) I = I < 0 ? I + NX : (I >= NX ? I - NX : I);
+            if (I >= 0 && I < NX && J >= 0 && J < NZ) {
+                const size_t c = (size_t)J * NX + I;
+                T U[4];
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) U[v] = ld(v, c, I, J) + bgs(K.ub, K.ubf, v * NZ + J, T{});
+                Side<T> sd;
+                side_of(U, K.pc, &spt, sd);
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) sU[v][lj][li] = sd.U[v];
+                sIr[lj][li] = sd.ir;
+                sP[lj][li] = sd.p;
+                sC[lj][li] = sd.c;
+            }
+        }
+        __syncthreads();
+        auto side_at = [&](int lj, int li, Side<T> &sd) {
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) sd.U[v] = sU[v][lj][li];
+            sd.ir = sIr[lj][li];
+            sd.p = sP[lj][li];
+            sd.c = sC[lj][li];
+        };
+        const bool sub = (IN < 2);
+        const auto cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
+        // x face west of local cell (i, j): global face index I0 + i in [0, NX]
+        auto xface = [&](int i, int j) {
+            const int If = I0 + i, J = J0 + j;
+            if (If > NX || J >= NZ) return;
+            const bool wl = !K.periodic && If == 0, wr = !K.periodic && If == NX;
+            Side<T> L, R;
+            T H[4];
+            if (wl) {
+                side_at(j + 1, i + 1, R);
+                mirror_side<T, 0>(R, L);
+            } else if (wr) {
+                side_at(j + 1, i, L);
+                mirror_side<T, 0>(L, R);
+            } else {
+                side_at(j + 1, i, L);
+                side_at(j + 1, i + 1, R);
+            }
+            hllc_s<T, 0>(L, R, H);
+            if (sub) {
+                const double *hb = wl ? K.hbxw : (wr ? K.hbxw + 4 * NZ : K.hbx);
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * NZ + J], T{});
+            }
+            if (VISC && !wl && !wr) {
+                T V[4];
+                visc2_s(L, R, cx, V);
+    #pragma unroll
+                for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
+            }
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) sGx[v][j][i] = (S)oval(H[v]);
+        };
+        // z face south of local cell (i, j): global face index J0 + j in [0, NZ]
+        auto zface = [&](int i, int j) {
+            const int I = I0 + i, Jf = J0 + j;
+            if (I >= NX || Jf > NZ) return;
+            const bool wl = Jf == 0, wr = Jf == NZ;
+            Side<T> B, Tp;
+            T H[4];
+            if (wl) {
+                side_at(j + 1, i + 1, Tp);
+                mirror_side<T, 1>(Tp, B);
+            } else if (wr) {
+                side_at(j, i + 1, B);
+                mirror_side<T, 1>(B, Tp);
+            } else {
+                side_at(j, i + 1, B);
+                side_at(j + 1, i + 1, Tp);
+            }
+            hllc_s<T, 1>(B, Tp, H);
+            if (sub) {
+    #pragma unroll
+                for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(K.hbz[v * (NZ + 1) + Jf], T{});
+            }
+            if (VISC && !wl && !wr) {
+                T V[4];
+                visc2_s(B, Tp, cz, V);
+    #pragma unroll
+                for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
+            }
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) sGz[v][j][i] = (S)oval(H[v]);
+        };
+        xface(tx, tz);
+        zface(tx, tz);
+        if (tz == 0) zface(tx, TZ);              // north edge of the tile
+        else if (tz == 1 && tx < TZ) xface(TX, tx);   // east edge of the tile
+        __syncthreads();
+        const S iHx = pick<S>(K.iHx, K.iHxf), iHz = pick<S>(K.iHz, K.iHzf);
+        const float adtf = IN >= 2 ? K.adtf : 0.0f;
+        const double eps = ld.step();
+        if (live) {
+    #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                S f = (sGx[v][tz][tx] - sGx[v][tz][tx + 1]) * iHx + (sGz[v][tz][tx] - sGz[v][tz + 1][tx]) * iHz;
+                if (v == 2) f -= pick<S>(K.g, K.gf) * up0;   // -g rho' (tangent: -g x_rho)
+                const size_t gi = (size_t)v * n1 + c;
+                if (MODE == FV_RES) {
+                    out[gi] = f;
+                    continue;
+                }
+                const S x = xv[v];
+                S gx;
+                if (IN == 1) gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)f - fuv[v]) / eps);
+                else gx = x - (S)adtf * f;
+                if (MODE == FV_SMOOTH) out[gi] = store_round<S>(rk_stage<S>(rk, x, dtc, bv[v] - gx, gi), bf16);
+                else if (MODE == FV_DEFECT) out[gi] = gx - bv[v];
+                else sD[v][tz][tx] = gx - bv[v];
+            }
+        }
+        if (MODE != FV_DEFRES) return;
+        __syncthreads();
+        // 2 x 2 restriction: thread (ci, cj) of the first TX/2 x TZ/2 threads
+        const int ci = threadIdx.x % (TX / 2), cj = threadIdx.x / (TX / 2);
+        if (cj >= TZ / 2) return;
+        const int Ic = I0 / 2 + ci, Jc = J0 / 2 + cj, NXc = NX / 2, NZc = NZ / 2;
+        if (Ic >= NXc || Jc >= NZc) return;
+        const size_t nc = (size_t)NXc * NZc, cc = (size_t)Jc * NXc + Ic;
+    #pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const S a = (sD[v][2 * cj][2 * ci] + sD[v][2 * cj][2 * ci + 1]) +
+                        (sD[v][2 * cj + 1][2 * ci] + sD[v][2 * cj + 1][2 * ci + 1]);
+            const S bv = store_round<S>(a * (S)0.25, bf16);
+            out[(size_t)v * nc + cc] = bv;
+            if (xc) xc[(size_t)v * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
+        }
+    }
+};
+template <class T, int IN, int MODE, bool VISC, int TZ>
 __global__ void __launch_bounds__(FV_TX * TZ) k_fv_tile(FVK K, FLoad<T, IN> ld0, const typename SOf<T>::type *b,
                                                       const typename SOf<T>::type *dtau, const double *fu,
                                                       double adt, typename SOf<T>::type *out,
                                                       typename SOf<T>::type *xc,
                                                       const typename SOf<T>::type *dtau_c, int bf16, RKS rk) {
-    jf_pdl_enter();
-    typedef typename SOf<T>::type S;
-    constexpr int TX = FV_TX;
-    // the FP64 power table (the FP32 tangent power needs none)
-    __shared__ double spt_raw[IN < 2 ? sizeof(PowTab) / sizeof(double) : 1];
-    PowTab &spt = *reinterpret_cast<PowTab *>(spt_raw);
-    // the tile's cells and a one-cell halo as face sides: state, 1/rho, p, c
-    // (one pressure / sound speed per cell instead of one per face and side)
-    __shared__ T sU[4][TZ + 2][TX + 2];
-    __shared__ T sIr[TZ + 2][TX + 2], sP[TZ + 2][TX + 2], sC[TZ + 2][TX + 2];
-    __shared__ S sGx[4][TZ][TX + 1];   // net flux H - V through the west face of local cell (i, j)
-    __shared__ S sGz[4][TZ + 1][TX];   // ... through the south face
-    __shared__ S sD[MODE == FV_DEFRES ? 4 : 1][MODE == FV_DEFRES ? TZ : 1][MODE == FV_DEFRES ? TX : 1];
-    if (IN < 2) load_pt(&spt, K.pt);
-    FLoad<T, IN> ld = ld0;
-    ld.prepare();
-    const int NX = K.NX, NZ = K.NZ;
-    const size_t n1 = (size_t)NX * NZ;
-    const int ntx = (NX + TX - 1) / TX;
-    const int I0 = (int)(blockIdx.x % ntx) * TX, J0 = (int)(blockIdx.x / ntx) * TZ;
-    const int tx = threadIdx.x % TX, tz = threadIdx.x / TX;
-    const int I = I0 + tx, J = J0 + tz;
-    const bool live = I < NX && J < NZ;
-    const size_t c = live ? (size_t)J * NX + I : 0;
-    // the epilogue's operands, loaded before the face work so that their latency overlaps it
-    S xv[4], bv[4], up0 = 0, dtc = 0;
-    double fuv[4] = {0.0, 0.0, 0.0, 0.0};
-    if (live) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const size_t gi = (size_t)v * n1 + c;
-            xv[v] = MODE == FV_RES ? (S)0 : (S)ld.dir(v, c, I, J);
-            bv[v] = MODE == FV_RES ? (S)0 : b[gi];
-            if (IN == 1) fuv[v] = fu[gi];
-        }
-        up0 = (S)oval(ld(0, c, I, J));
-        if (MODE == FV_SMOOTH) dtc = dtau[c];
-    }
-    if (IN < 2) __syncthreads();   // the power table
-    for (int idx = threadIdx.x; idx < (TZ + 2) * (TX + 2); idx += blockDim.x) {
-        const int li = idx % (TX + 2), lj = idx / (TX + 2);
-        int I = I0 + li - 1;
-        const int J = J0 + lj - 1;
-        if (K.periodic) I = I < 0 ? I + NX : (I >= NX ? I - NX : I);
-        if (I >= 0 && I < NX && J >= 0 && J < NZ) {
-            const size_t c = (size_t)J * NX + I;
-            T U[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) U[v] = ld(v, c, I, J) + bgs(K.ub, K.ubf, v * NZ + J, T{});
-            Side<T> sd;
-            side_of(U, K.pc, &spt, sd);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sU[v][lj][li] = sd.U[v];
-            sIr[lj][li] = sd.ir;
-            sP[lj][li] = sd.p;
-            sC[lj][li] = sd.c;
-        }
-    }
-    __syncthreads();
-    auto side_at = [&](int lj, int li, Side<T> &sd) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sd.U[v] = sU[v][lj][li];
-        sd.ir = sIr[lj][li];
-        sd.p = sP[lj][li];
-        sd.c = sC[lj][li];
-    };
-    const bool sub = (IN < 2);
-    const auto cx = mkc(K.vcx, K.vcxf, T{}), cz = mkc(K.vcz, K.vczf, T{});
-    // x face west of local cell (i, j): global face index I0 + i in [0, NX]
-    auto xface = [&](int i, int j) {
-        const int If = I0 + i, J = J0 + j;
-        if (If > NX || J >= NZ) return;
-        const bool wl = !K.periodic && If == 0, wr = !K.periodic && If == NX;
-        Side<T> L, R;
-        T H[4];
-        if (wl) {
-            side_at(j + 1, i + 1, R);
-            mirror_side<T, 0>(R, L);
-        } else if (wr) {
-            side_at(j + 1, i, L);
-            mirror_side<T, 0>(L, R);
-        } else {
-            side_at(j + 1, i, L);
-            side_at(j + 1, i + 1, R);
-        }
-        hllc_s<T, 0>(L, R, H);
-        if (sub) {
-            const double *hb = wl ? K.hbxw : (wr ? K.hbxw + 4 * NZ : K.hbx);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(hb[v * NZ + J], T{});
-        }
-        if (VISC && !wl && !wr) {
-            T V[4];
-            visc2_s(L, R, cx, V);
-#pragma unroll
-            for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sGx[v][j][i] = (S)oval(H[v]);
-    };
-    // z face south of local cell (i, j): global face index J0 + j in [0, NZ]
-    auto zface = [&](int i, int j) {
-        const int I = I0 + i, Jf = J0 + j;
-        if (I >= NX || Jf > NZ) return;
-        const bool wl = Jf == 0, wr = Jf == NZ;
-        Side<T> B, Tp;
-        T H[4];
-        if (wl) {
-            side_at(j + 1, i + 1, Tp);
-            mirror_side<T, 1>(Tp, B);
-        } else if (wr) {
-            side_at(j, i + 1, B);
-            mirror_side<T, 1>(B, Tp);
-        } else {
-            side_at(j, i + 1, B);
-            side_at(j + 1, i + 1, Tp);
-        }
-        hllc_s<T, 1>(B, Tp, H);
-        if (sub) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) H[v] = H[v] - mk(K.hbz[v * (NZ + 1) + Jf], T{});
-        }
-        if (VISC && !wl && !wr) {
-            T V[4];
-            visc2_s(B, Tp, cz, V);
-#pragma unroll
-            for (int v = 1; v < 4; ++v) H[v] = H[v] - V[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sGz[v][j][i] = (S)oval(H[v]);
-    };
-    xface(tx, tz);
-    zface(tx, tz);
-    if (tz == 0) zface(tx, TZ);              // north edge of the tile
-    else if (tz == 1 && tx < TZ) xface(TX, tx);   // east edge of the tile
-    __syncthreads();
-    const S iHx = pick<S>(K.iHx, K.iHxf), iHz = pick<S>(K.iHz, K.iHzf);
-    const float adtf = IN >= 2 ? K.adtf : 0.0f;
-    const double eps = ld.step();
-    if (live) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            S f = (sGx[v][tz][tx] - sGx[v][tz][tx + 1]) * iHx + (sGz[v][tz][tx] - sGz[v][tz + 1][tx]) * iHz;
-            if (v == 2) f -= pick<S>(K.g, K.gf) * up0;   // -g rho' (tangent: -g x_rho)
-            const size_t gi = (size_t)v * n1 + c;
-            if (MODE == FV_RES) {
-                out[gi] = f;
-                continue;
-            }
-            const S x = xv[v];
-            S gx;
-            if (IN == 1) gx = (S)((eps == 0.0) ? (double)x : (double)x - adt * ((double)f - fuv[v]) / eps);
-            else gx = x - (S)adtf * f;
-            if (MODE == FV_SMOOTH) out[gi] = store_round<S>(rk_stage<S>(rk, x, dtc, bv[v] - gx, gi), bf16);
-            else if (MODE == FV_DEFECT) out[gi] = gx - bv[v];
-            else sD[v][tz][tx] = gx - bv[v];
-        }
-    }
-    if (MODE != FV_DEFRES) return;
-    __syncthreads();
-    // 2 x 2 restriction: thread (ci, cj) of the first TX/2 x TZ/2 threads
-    const int ci = threadIdx.x % (TX / 2), cj = threadIdx.x / (TX / 2);
-    if (cj >= TZ / 2) return;
-    const int Ic = I0 / 2 + ci, Jc = J0 / 2 + cj, NXc = NX / 2, NZc = NZ / 2;
-    if (Ic >= NXc || Jc >= NZc) return;
-    const size_t nc = (size_t)NXc * NZc, cc = (size_t)Jc * NXc + Ic;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const S a = (sD[v][2 * cj][2 * ci] + sD[v][2 * cj][2 * ci + 1]) +
-                    (sD[v][2 * cj + 1][2 * ci] + sD[v][2 * cj + 1][2 * ci + 1]);
-        const S bv = store_round<S>(a * (S)0.25, bf16);
-        out[(size_t)v * nc + cc] = bv;
-        if (xc) xc[(size_t)v * nc + cc] = store_round<S>(dtau_c[cc] * bv, bf16);
-    }
+    k_fv_tile_b<T, IN, MODE, VISC, TZ>::run(blockIdx.x, gridDim.x, K, ld0, b, dtau, fu, adt, out, xc, dtau_c, bf16, rk);
 }
 
 // FV pseudo-time step sizes: dtau = sigma / (1 + adt lambda), lambda = sum_faces
@@ -661,78 +700,97 @@ JF_D float wave_speed_r<float>(const float U[4], int D, const PhysC &P, const Po
 }
 
 template <class S>
+struct k_fv_dtau_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<FVK> K, JfArg<const S *> u,
+                                               JfArg<double> adt, JfArg<double> sigma, JfArg<S *> dtau) {
+        jf_pdl_enter();
+        __shared__ PowTab spt;
+        load_pt(&spt, K.pt);
+        __syncthreads();
+        const int NX = K.NX, NZ = K.NZ;
+        const size_t n1 = (size_t)NX * NZ;
+        const size_t c = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (c >= n1) return;
+        const int I = (int)(c % NX), Jz = (int)(c / NX);
+        auto st = [&](int i, int j, S U[4]) {
+            const size_t cc = (size_t)j * NX + i;
+            for (int v = 0; v < 4; ++v) U[v] = u[(size_t)v * n1 + cc] + pick<S>(K.ub[v * NZ + j], K.ubf[v * NZ + j]);
+        };
+        S U[4], V[4];
+        st(I, Jz, U);
+        const S sx = wave_speed_r<S>(U, 0, K.pc, &spt), sz = wave_speed_r<S>(U, 1, K.pc, &spt);
+        S eW = sx, eE = sx, eS = sz, eN = sz;
+        if (I > 0 || K.periodic) { st(I > 0 ? I - 1 : NX - 1, Jz, V); eW = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
+        if (I < NX - 1 || K.periodic) { st(I < NX - 1 ? I + 1 : 0, Jz, V); eE = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
+        if (Jz > 0) { st(I, Jz - 1, V); eS = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
+        if (Jz < NZ - 1) { st(I, Jz + 1, V); eN = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
+        const S iHx = (S)K.iHx, iHz = (S)K.iHz;
+        const S lam = (S)0.5 * (eW + eE) * iHx + (S)0.5 * (eS + eN) * iHz + (S)(2.0 * K.mu) * (iHx * iHx + iHz * iHz);
+        dtau[c] = (S)sigma / ((S)1 + (S)adt * lam);
+    }
+};
+template <class S>
 __global__ void k_fv_dtau(FVK K, const S *u, double adt, double sigma, S *dtau) {
-    jf_pdl_enter();
-    __shared__ PowTab spt;
-    load_pt(&spt, K.pt);
-    __syncthreads();
-    const int NX = K.NX, NZ = K.NZ;
-    const size_t n1 = (size_t)NX * NZ;
-    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n1) return;
-    const int I = (int)(c % NX), Jz = (int)(c / NX);
-    auto st = [&](int i, int j, S U[4]) {
-        const size_t cc = (size_t)j * NX + i;
-        for (int v = 0; v < 4; ++v) U[v] = u[(size_t)v * n1 + cc] + pick<S>(K.ub[v * NZ + j], K.ubf[v * NZ + j]);
-    };
-    S U[4], V[4];
-    st(I, Jz, U);
-    const S sx = wave_speed_r<S>(U, 0, K.pc, &spt), sz = wave_speed_r<S>(U, 1, K.pc, &spt);
-    S eW = sx, eE = sx, eS = sz, eN = sz;
-    if (I > 0 || K.periodic) { st(I > 0 ? I - 1 : NX - 1, Jz, V); eW = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
-    if (I < NX - 1 || K.periodic) { st(I < NX - 1 ? I + 1 : 0, Jz, V); eE = fmax(sx, wave_speed_r<S>(V, 0, K.pc, &spt)); }
-    if (Jz > 0) { st(I, Jz - 1, V); eS = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
-    if (Jz < NZ - 1) { st(I, Jz + 1, V); eN = fmax(sz, wave_speed_r<S>(V, 1, K.pc, &spt)); }
-    const S iHx = (S)K.iHx, iHz = (S)K.iHz;
-    const S lam = (S)0.5 * (eW + eE) * iHx + (S)0.5 * (eS + eN) * iHz + (S)(2.0 * K.mu) * (iHx * iHx + iHz * iHz);
-    dtau[c] = (S)sigma / ((S)1 + (S)adt * lam);
+    k_fv_dtau_b<S>::run(blockIdx.x, gridDim.x, K, u, adt, sigma, dtau);
 }
 
 // DG pseudo-time step per element: lambda_E = (k+1)^2 max_nodes(|v| + c)(1/hx + 1/hz)
 // + 2 mu (k+1)^4 (1/hx^2 + 1/hz^2).
 template <class R>
+struct k_dg_dtau_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<const R *> U,
+                                               JfArg<const R *> ubv, JfArg<int> nx, JfArg<int> nz, JfArg<int> np1,
+                                               JfArg<PhysC> pc, JfArg<const PowTab *> pt, JfArg<double> ihx,
+                                               JfArg<double> ihz, JfArg<double> mu, JfArg<double> adt,
+                                               JfArg<double> sigma, JfArg<double *> dtau, JfArg<float *> dtauf) {
+        jf_pdl_enter();
+        __shared__ PowTab spt;
+        if (sizeof(R) == 8) load_pt(&spt, pt);
+        __syncthreads();
+        // one warp per element, one lane per node, max over the lanes
+        const int n_el = nx * nz;
+        const int lane = threadIdx.x & 31;
+        const int e = (int)(((size_t)jf_bid * blockDim.x + threadIdx.x) >> 5);
+        if (e >= n_el) return;   // uniform over the warp
+        const int NP = np1 * np1;
+        const size_t N1 = (size_t)n_el * NP;
+        const int ez = e / nx;
+        const size_t nrow = (size_t)nz * np1;
+        R sp = 0;
+        if (lane < NP) {
+            const int J = ez * np1 + lane / np1;
+            R W[4];
+            for (int v = 0; v < 4; ++v) W[v] = U[v * N1 + (size_t)e * NP + lane] + ubv[v * nrow + J];
+            if (sizeof(R) == 8) {
+                const double ir = 1.0 / (double)W[0];
+                const double p = pc.p0 * pow_gamma_tab(pc.R_over_p0 * (double)W[3], &spt);
+                sp = (R)(sqrt(((double)W[1] * ir) * ((double)W[1] * ir) + ((double)W[2] * ir) * ((double)W[2] * ir)) +
+                         sqrt(pc.gamma * p * ir));
+            } else {
+                const float ir = 1.0f / (float)W[0];
+                const float p = pc.p0f * __powf(pc.R_over_p0f * (float)W[3], pc.gammaf);
+                sp = (R)(sqrtf(((float)W[1] * ir) * ((float)W[1] * ir) + ((float)W[2] * ir) * ((float)W[2] * ir)) +
+                         sqrtf(pc.gammaf * p * ir));
+            }
+        }
+    #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+        if (lane != 0) return;
+        const double vmax = (double)sp;
+        const double n2 = (double)np1 * np1;
+        const double lam = n2 * vmax * (ihx + ihz) + 2.0 * mu * n2 * n2 * (ihx * ihx + ihz * ihz);
+        const double d = sigma / (1.0 + adt * lam);
+        if (dtau) dtau[e] = d;
+        if (dtauf) dtauf[e] = (float)d;
+    }
+};
+template <class R>
 __global__ void k_dg_dtau(const R *U, const R *ubv, int nx, int nz, int np1, PhysC pc, const PowTab *pt,
                           double ihx, double ihz, double mu, double adt, double sigma, double *dtau,
                           float *dtauf) {
-    jf_pdl_enter();
-    __shared__ PowTab spt;
-    if (sizeof(R) == 8) load_pt(&spt, pt);
-    __syncthreads();
-    // one warp per element, one lane per node, max over the lanes
-    const int n_el = nx * nz;
-    const int lane = threadIdx.x & 31;
-    const int e = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (e >= n_el) return;   // uniform over the warp
-    const int NP = np1 * np1;
-    const size_t N1 = (size_t)n_el * NP;
-    const int ez = e / nx;
-    const size_t nrow = (size_t)nz * np1;
-    R sp = 0;
-    if (lane < NP) {
-        const int J = ez * np1 + lane / np1;
-        R W[4];
-        for (int v = 0; v < 4; ++v) W[v] = U[v * N1 + (size_t)e * NP + lane] + ubv[v * nrow + J];
-        if (sizeof(R) == 8) {
-            const double ir = 1.0 / (double)W[0];
-            const double p = pc.p0 * pow_gamma_tab(pc.R_over_p0 * (double)W[3], &spt);
-            sp = (R)(sqrt(((double)W[1] * ir) * ((double)W[1] * ir) + ((double)W[2] * ir) * ((double)W[2] * ir)) +
-                     sqrt(pc.gamma * p * ir));
-        } else {
-            const float ir = 1.0f / (float)W[0];
-            const float p = pc.p0f * __powf(pc.R_over_p0f * (float)W[3], pc.gammaf);
-            sp = (R)(sqrtf(((float)W[1] * ir) * ((float)W[1] * ir) + ((float)W[2] * ir) * ((float)W[2] * ir)) +
-                     sqrtf(pc.gammaf * p * ir));
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
-    if (lane != 0) return;
-    const double vmax = (double)sp;
-    const double n2 = (double)np1 * np1;
-    const double lam = n2 * vmax * (ihx + ihz) + 2.0 * mu * n2 * n2 * (ihx * ihx + ihz * ihz);
-    const double d = sigma / (1.0 + adt * lam);
-    if (dtau) dtau[e] = d;
-    if (dtauf) dtauf[e] = (float)d;
+    k_dg_dtau_b<R>::run(blockIdx.x, gridDim.x, U, ubv, nx, nz, np1, pc, pt, ihx, ihz, mu, adt, sigma, dtau, dtauf);
 }
 
 // ---- transfer -------------------------------------------------------------
@@ -756,214 +814,291 @@ __device__ __forceinline__ void load_ttab(const TK &K, R sV[NP1][NP1], R sVi[NP1
 // T^mf: DG (Si) -> FV (So), arithmetic in the storage precision.  Block: EPB
 // elements x NP subcells.
 template <class Si, class So, int NP1>
-__global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix, So *x0, const So *dtau0) {
-    jf_pdl_enter();
-    typedef typename RealOf<Si, So>::type R;
-    constexpr int NP = NP1 * NP1;
-    constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
-    __shared__ R su[EPB][4][NP];
-    __shared__ R st[EPB][4][NP];
-    __shared__ R sc[EPB][4];
-    __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
-    load_ttab<R, NP1>(K, sV, sVi, som);
-    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
-    const int e = blockIdx.x * EPB + le;
-    const bool act = e < K.n_el;
-    const size_t N1 = (size_t)K.n_el * NP;
-    const int i = node % NP1, j = node / NP1;   // subcell (i along x, j along z) / node (a, b)
-    if (act)
-        for (int q = 0; q < 4; ++q) su[le][q][node] = (R)u[q * N1 + (size_t)e * NP + node];
-    __syncthreads();
-    // t1(i, b) = sum_a V[i][a] u(a, b), stored at [b][i]
-    if (act)
-        for (int q = 0; q < 4; ++q) {
-            R acc = 0;
-#pragma unroll
-            for (int a = 0; a < NP1; ++a) acc = fma(sV[i][a], su[le][q][j * NP1 + a], acc);
-            st[le][q][j * NP1 + i] = acc;
-        }
-    __syncthreads();
-    R Tu[4];
-    if (act)
-        for (int q = 0; q < 4; ++q) {
-            R acc = 0;
-#pragma unroll
-            for (int b = 0; b < NP1; ++b) acc = fma(sV[j][b], st[le][q][b * NP1 + i], acc);
-            Tu[q] = acc;
-        }
-    __syncthreads();
-    if (act)
-        for (int q = 0; q < 4; ++q) su[le][q][node] = Tu[q];
-    __syncthreads();
-    if (act && node < 4) {
-        // m_E(T u)/|E| = subcell mean; m_E(u)/|E| by the midpoint weights on the subcell values
-        const int q = node;
-        R mfv = 0, mnc = 0;
-        for (int jj = 0; jj < NP1; ++jj)
-            for (int ii = 0; ii < NP1; ++ii) {
-                const R x = su[le][q][jj * NP1 + ii];
-                mfv += x;
-                mnc = fma(som[ii] * som[jj], x, mnc);
+struct k_to_fv_b {
+    static constexpr int TPB = 128, MINB = 0;
+    static constexpr bool GROUP = std::is_same<So, float>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<TK> K, JfArg<const Si *> u,
+                                               JfArg<So *> v, JfArg<int> massfix, JfArg<So *> x0,
+                                               JfArg<const So *> dtau0) {
+        jf_pdl_enter();
+        typedef typename RealOf<Si, So>::type R;
+        constexpr int NP = NP1 * NP1;
+        constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+        __shared__ R su[EPB][4][NP];
+        __shared__ R st[EPB][4][NP];
+        __shared__ R sc[EPB][4];
+        __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
+        load_ttab<R, NP1>(K, sV, sVi, som);
+        const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+        const int e = jf_bid * EPB + le;
+        const bool act = e < K.n_el;
+        const size_t N1 = (size_t)K.n_el * NP;
+        const int i = node % NP1, j = node / NP1;   // subcell (i along x, j along z) / node (a, b)
+        if (act)
+            for (int q = 0; q < 4; ++q) su[le][q][node] = (R)u[q * N1 + (size_t)e * NP + node];
+        __syncthreads();
+        // t1(i, b) = sum_a V[i][a] u(a, b), stored at [b][i]
+        if (act)
+            for (int q = 0; q < 4; ++q) {
+                R acc = 0;
+    #pragma unroll
+                for (int a = 0; a < NP1; ++a) acc = fma(sV[i][a], su[le][q][j * NP1 + a], acc);
+                st[le][q][j * NP1 + i] = acc;
             }
-        sc[le][q] = massfix ? (mfv / (R)NP - mnc) : (R)0;
+        __syncthreads();
+        R Tu[4];
+        if (act)
+            for (int q = 0; q < 4; ++q) {
+                R acc = 0;
+    #pragma unroll
+                for (int b = 0; b < NP1; ++b) acc = fma(sV[j][b], st[le][q][b * NP1 + i], acc);
+                Tu[q] = acc;
+            }
+        __syncthreads();
+        if (act)
+            for (int q = 0; q < 4; ++q) su[le][q][node] = Tu[q];
+        __syncthreads();
+        if (act && node < 4) {
+            // m_E(T u)/|E| = subcell mean; m_E(u)/|E| by the midpoint weights on the subcell values
+            const int q = node;
+            R mfv = 0, mnc = 0;
+            for (int jj = 0; jj < NP1; ++jj)
+                for (int ii = 0; ii < NP1; ++ii) {
+                    const R x = su[le][q][jj * NP1 + ii];
+                    mfv += x;
+                    mnc = fma(som[ii] * som[jj], x, mnc);
+                }
+            sc[le][q] = massfix ? (mfv / (R)NP - mnc) : (R)0;
+        }
+        __syncthreads();
+        if (!act) return;
+        const int ez = e / K.nx, ex = e % K.nx;
+        const size_t I = (size_t)ex * NP1 + i, Jr = (size_t)ez * NP1 + j;
+        const size_t n1 = (size_t)K.NX * K.NZ;
+        for (int q = 0; q < 4; ++q) {
+            const So val = (So)(Tu[q] - sc[le][q]);
+            v[q * n1 + Jr * K.NX + I] = val;
+            if (x0) x0[q * n1 + Jr * K.NX + I] = dtau0[Jr * K.NX + I] * val;   // first step from zero
+        }
     }
-    __syncthreads();
-    if (!act) return;
-    const int ez = e / K.nx, ex = e % K.nx;
-    const size_t I = (size_t)ex * NP1 + i, Jr = (size_t)ez * NP1 + j;
-    const size_t n1 = (size_t)K.NX * K.NZ;
-    for (int q = 0; q < 4; ++q) {
-        const So val = (So)(Tu[q] - sc[le][q]);
-        v[q * n1 + Jr * K.NX + I] = val;
-        if (x0) x0[q * n1 + Jr * K.NX + I] = dtau0[Jr * K.NX + I] * val;   // first step from zero
-    }
+};
+template <class Si, class So, int NP1>
+__global__ void __launch_bounds__(128) k_to_fv(TK K, const Si *u, So *v, int massfix, So *x0, const So *dtau0) {
+    k_to_fv_b<Si, So, NP1>::run(blockIdx.x, gridDim.x, K, u, v, massfix, x0, dtau0);
 }
 
 // T^-1_mf: FV (Si) -> DG (So); acc 0: store, 1: add
 template <class Si, class So, int NP1>
-__global__ void __launch_bounds__(128) k_to_dg(TK K, const Si *v, So *u, int massfix, int acc_mode) {
-    jf_pdl_enter();
-    typedef typename RealOf<Si, So>::type R;
-    constexpr int NP = NP1 * NP1;
-    constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
-    __shared__ R sv[EPB][4][NP];
-    __shared__ R st[EPB][4][NP];
-    __shared__ R sc[EPB][4];
-    __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
-    load_ttab<R, NP1>(K, sV, sVi, som);
-    const int le = threadIdx.x / NP, node = threadIdx.x % NP;
-    const int e = blockIdx.x * EPB + le;
-    const bool act = e < K.n_el;
-    const size_t n1 = (size_t)K.NX * K.NZ;
-    const int a = node % NP1, b = node / NP1;
-    const int ez = act ? e / K.nx : 0, ex = act ? e % K.nx : 0;
-    if (act) {
-        const size_t I = (size_t)ex * NP1 + a, Jr = (size_t)ez * NP1 + b;   // subcell (a, b) here
-        for (int q = 0; q < 4; ++q) sv[le][q][node] = (R)v[q * n1 + Jr * K.NX + I];
-    }
-    __syncthreads();
-    if (act)
-        for (int q = 0; q < 4; ++q) {   // t1(a, j) = sum_i Vinv[a][i] v(i, j), at [j][a]
-            R acc = 0;
-#pragma unroll
-            for (int i = 0; i < NP1; ++i) acc = fma(sVi[a][i], sv[le][q][b * NP1 + i], acc);
-            st[le][q][b * NP1 + a] = acc;
+struct k_to_dg_b {
+    static constexpr int TPB = 128, MINB = 0;
+    static constexpr bool GROUP = std::is_same<Si, float>::value;   // a grouped twin is built (lock-step ensembles)
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<TK> K, JfArg<const Si *> v,
+                                               JfArg<So *> u, JfArg<int> massfix, JfArg<int> acc_mode) {
+        jf_pdl_enter();
+        typedef typename RealOf<Si, So>::type R;
+        constexpr int NP = NP1 * NP1;
+        constexpr int EPB = (128 / NP) > 0 ? 128 / NP : 1;
+        __shared__ R sv[EPB][4][NP];
+        __shared__ R st[EPB][4][NP];
+        __shared__ R sc[EPB][4];
+        __shared__ R sV[NP1][NP1], sVi[NP1][NP1], som[NP1];
+        load_ttab<R, NP1>(K, sV, sVi, som);
+        const int le = threadIdx.x / NP, node = threadIdx.x % NP;
+        const int e = jf_bid * EPB + le;
+        const bool act = e < K.n_el;
+        const size_t n1 = (size_t)K.NX * K.NZ;
+        const int a = node % NP1, b = node / NP1;
+        const int ez = act ? e / K.nx : 0, ex = act ? e % K.nx : 0;
+        if (act) {
+            const size_t I = (size_t)ex * NP1 + a, Jr = (size_t)ez * NP1 + b;   // subcell (a, b) here
+            for (int q = 0; q < 4; ++q) sv[le][q][node] = (R)v[q * n1 + Jr * K.NX + I];
         }
-    __syncthreads();
-    R Ti[4];
-    if (act)
-        for (int q = 0; q < 4; ++q) {
-            R acc = 0;
-#pragma unroll
-            for (int jj = 0; jj < NP1; ++jj) acc = fma(sVi[b][jj], st[le][q][jj * NP1 + a], acc);
-            Ti[q] = acc;
-        }
-    if (act && node < 4) {
-        // m_E(T^-1 v)/|E| from the subcell values (T T^-1 v = v) by the midpoint weights,
-        // m_E(v)/|E| the subcell mean
-        const int q = node;
-        R mfv = 0, mnc = 0;
-        for (int jj = 0; jj < NP1; ++jj)
-            for (int ii = 0; ii < NP1; ++ii) {
-                const R x = sv[le][q][jj * NP1 + ii];
-                mfv += x;
-                mnc = fma(som[ii] * som[jj], x, mnc);
+        __syncthreads();
+        if (act)
+            for (int q = 0; q < 4; ++q) {   // t1(a, j) = sum_i Vinv[a][i] v(i, j), at [j][a]
+                R acc = 0;
+    #pragma unroll
+                for (int i = 0; i < NP1; ++i) acc = fma(sVi[a][i], sv[le][q][b * NP1 + i], acc);
+                st[le][q][b * NP1 + a] = acc;
             }
-        sc[le][q] = massfix ? (mnc - mfv / (R)NP) : (R)0;
+        __syncthreads();
+        R Ti[4];
+        if (act)
+            for (int q = 0; q < 4; ++q) {
+                R acc = 0;
+    #pragma unroll
+                for (int jj = 0; jj < NP1; ++jj) acc = fma(sVi[b][jj], st[le][q][jj * NP1 + a], acc);
+                Ti[q] = acc;
+            }
+        if (act && node < 4) {
+            // m_E(T^-1 v)/|E| from the subcell values (T T^-1 v = v) by the midpoint weights,
+            // m_E(v)/|E| the subcell mean
+            const int q = node;
+            R mfv = 0, mnc = 0;
+            for (int jj = 0; jj < NP1; ++jj)
+                for (int ii = 0; ii < NP1; ++ii) {
+                    const R x = sv[le][q][jj * NP1 + ii];
+                    mfv += x;
+                    mnc = fma(som[ii] * som[jj], x, mnc);
+                }
+            sc[le][q] = massfix ? (mnc - mfv / (R)NP) : (R)0;
+        }
+        __syncthreads();
+        if (!act) return;
+        const size_t N1 = (size_t)K.n_el * NP;
+        for (int q = 0; q < 4; ++q) {
+            const size_t gi = q * N1 + (size_t)e * NP + node;
+            const R val = Ti[q] - sc[le][q];
+            u[gi] = acc_mode ? (So)((R)u[gi] + val) : (So)val;
+        }
     }
-    __syncthreads();
-    if (!act) return;
-    const size_t N1 = (size_t)K.n_el * NP;
-    for (int q = 0; q < 4; ++q) {
-        const size_t gi = q * N1 + (size_t)e * NP + node;
-        const R val = Ti[q] - sc[le][q];
-        u[gi] = acc_mode ? (So)((R)u[gi] + val) : (So)val;
-    }
+};
+template <class Si, class So, int NP1>
+__global__ void __launch_bounds__(128) k_to_dg(TK K, const Si *v, So *u, int massfix, int acc_mode) {
+    k_to_dg_b<Si, So, NP1>::run(blockIdx.x, gridDim.x, K, v, u, massfix, acc_mode);
 }
 
 // R: coarse = mean of fac x fac children
 template <class S>
+struct k_restrict_body {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<const S *> f, JfArg<int> NXf,
+                                               JfArg<int> NZf, JfArg<int> fac, JfArg<S *> cz) {
+        jf_pdl_enter();
+        const int NXc = NXf / fac, NZc = NZf / fac;
+        const size_t nc = (size_t)NXc * NZc;
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t >= 4 * nc) return;
+        const int q = (int)(t / nc);
+        const size_t c = t % nc;
+        const int I = (int)(c % NXc), J = (int)(c / NXc);
+        const S *fq = f + (size_t)q * NXf * NZf;
+        S acc = 0;
+        for (int jj = 0; jj < fac; ++jj)
+            for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
+        cz[t] = acc / (S)(fac * fac);
+    }
+};
+template <class S>
 __global__ void k_restrict(const S *f, int NXf, int NZf, int fac, S *cz) {
-    jf_pdl_enter();
-    const int NXc = NXf / fac, NZc = NZf / fac;
-    const size_t nc = (size_t)NXc * NZc;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * nc) return;
-    const int q = (int)(t / nc);
-    const size_t c = t % nc;
-    const int I = (int)(c % NXc), J = (int)(c / NXc);
-    const S *fq = f + (size_t)q * NXf * NZf;
-    S acc = 0;
-    for (int jj = 0; jj < fac; ++jj)
-        for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
-    cz[t] = acc / (S)(fac * fac);
+    k_restrict_body<S>::run(blockIdx.x, gridDim.x, f, NXf, NZf, fac, cz);
 }
 
 // R plus the coarse level's first pseudo-time step from zero: b_c = R r and,
 // when x_c is given, x_c = dtau_c b_c
 template <class S>
+struct k_restrict_b_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<const S *> f, JfArg<int> NXf,
+                                               JfArg<int> NZf, JfArg<int> fac, JfArg<S *> bc, JfArg<S *> xc,
+                                               JfArg<const S *> dtau_c, JfArg<int> bf16) {
+        jf_pdl_enter();
+        const int NXc = NXf / fac, NZc = NZf / fac;
+        const size_t nc = (size_t)NXc * NZc;
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t >= 4 * nc) return;
+        const int q = (int)(t / nc);
+        const size_t c = t % nc;
+        const int I = (int)(c % NXc), J = (int)(c / NXc);
+        const S *fq = f + (size_t)q * NXf * NZf;
+        S acc = 0;
+        for (int jj = 0; jj < fac; ++jj)
+            for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
+        const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
+        bc[t] = bv;
+        if (xc) xc[t] = store_round<S>(dtau_c[c] * bv, bf16);
+    }
+};
+template <class S>
 __global__ void k_restrict_b(const S *f, int NXf, int NZf, int fac, S *bc, S *xc, const S *dtau_c, int bf16 = 0) {
-    jf_pdl_enter();
-    const int NXc = NXf / fac, NZc = NZf / fac;
-    const size_t nc = (size_t)NXc * NZc;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * nc) return;
-    const int q = (int)(t / nc);
-    const size_t c = t % nc;
-    const int I = (int)(c % NXc), J = (int)(c / NXc);
-    const S *fq = f + (size_t)q * NXf * NZf;
-    S acc = 0;
-    for (int jj = 0; jj < fac; ++jj)
-        for (int ii = 0; ii < fac; ++ii) acc += fq[(size_t)(J * fac + jj) * NXf + I * fac + ii];
-    const S bv = store_round<S>(acc / (S)(fac * fac), bf16);
-    bc[t] = bv;
-    if (xc) xc[t] = store_round<S>(dtau_c[c] * bv, bf16);
+    k_restrict_b_b<S>::run(blockIdx.x, gridDim.x, f, NXf, NZf, fac, bc, xc, dtau_c, bf16);
 }
 
 // x = (zero ? 0 : x) - P v
 template <class S>
+struct k_prolong_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<S *> x, JfArg<const S *> vc,
+                                               JfArg<int> NXf, JfArg<int> NZf, JfArg<int> fac, JfArg<int> zero) {
+        jf_pdl_enter();
+        const size_t nf = (size_t)NXf * NZf;
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t >= 4 * nf) return;
+        const int q = (int)(t / nf);
+        const size_t c = t % nf;
+        const int I = (int)(c % NXf), J = (int)(c / NXf);
+        const int NXc = NXf / fac, NZc = NZf / fac;
+        const S pv = vc[(size_t)q * NXc * NZc + (size_t)(J / fac) * NXc + I / fac];
+        x[t] = zero ? -pv : x[t] - pv;
+    }
+};
+template <class S>
 __global__ void k_prolong(S *x, const S *vc, int NXf, int NZf, int fac, int zero) {
-    jf_pdl_enter();
-    const size_t nf = (size_t)NXf * NZf;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * nf) return;
-    const int q = (int)(t / nf);
-    const size_t c = t % nf;
-    const int I = (int)(c % NXf), J = (int)(c / NXf);
-    const int NXc = NXf / fac, NZc = NZf / fac;
-    const S pv = vc[(size_t)q * NXc * NZc + (size_t)(J / fac) * NXc + I / fac];
-    x[t] = zero ? -pv : x[t] - pv;
+    k_prolong_b<S>::run(blockIdx.x, gridDim.x, x, vc, NXf, NZf, fac, zero);
 }
 
 // x = dtau b (first smoothing step from zero)
 template <class S>
+struct k_scale_dtau_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<S *> x, JfArg<const S *> b,
+                                               JfArg<const S *> dtau, JfArg<size_t> n1, JfArg<double> alpha) {
+        jf_pdl_enter();
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t >= 4 * n1) return;
+        x[t] = ((S)alpha * dtau[t % n1]) * b[t];   // alpha = 1: dtau b exactly
+    }
+};
+template <class S>
 __global__ void k_scale_dtau(S *x, const S *b, const S *dtau, size_t n1, double alpha) {
-    jf_pdl_enter();
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * n1) return;
-    x[t] = ((S)alpha * dtau[t % n1]) * b[t];   // alpha = 1: dtau b exactly
+    k_scale_dtau_b<S>::run(blockIdx.x, gridDim.x, x, b, dtau, n1, alpha);
 }
 
+template <class S>
+struct k_scale_dtau_dg_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<S *> z, JfArg<const S *> r,
+                                               JfArg<const S *> dtau, JfArg<size_t> N1, JfArg<int> NP,
+                                               JfArg<double> alpha) {
+        jf_pdl_enter();
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t >= 4 * N1) return;
+        z[t] = ((S)alpha * dtau[(t % N1) / NP]) * r[t];   // alpha = 1: dtau r exactly
+    }
+};
 template <class S>
 __global__ void k_scale_dtau_dg(S *z, const S *r, const S *dtau, size_t N1, int NP, double alpha) {
-    jf_pdl_enter();
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * N1) return;
-    z[t] = ((S)alpha * dtau[(t % N1) / NP]) * r[t];   // alpha = 1: dtau r exactly
+    k_scale_dtau_dg_b<S>::run(blockIdx.x, gridDim.x, z, r, dtau, N1, NP, alpha);
 }
 
+template <class S>
+struct k_neg_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<S *> x, JfArg<const S *> b,
+                                               JfArg<size_t> n) {
+        jf_pdl_enter();
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t < n) x[t] = -b[t];
+    }
+};
 template <class S>
 __global__ void k_neg(S *x, const S *b, size_t n) {
-    jf_pdl_enter();
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) x[t] = -b[t];
+    k_neg_b<S>::run(blockIdx.x, gridDim.x, x, b, n);
 }
 
 template <class S>
+struct k_sub_b {
+    static constexpr int TPB = 0, MINB = 0;
+    static __device__ __forceinline__ void run(unsigned jf_bid, unsigned jf_nblk, JfArg<const S *> r,
+                                               JfArg<const S *> w, JfArg<S *> d, JfArg<size_t> n) {
+        jf_pdl_enter();   // d = r - w
+        const size_t t = (size_t)jf_bid * blockDim.x + threadIdx.x;
+        if (t < n) d[t] = r[t] - w[t];
+    }
+};
+template <class S>
 __global__ void k_sub(const S *r, const S *w, S *d, size_t n) {
-    jf_pdl_enter();   // d = r - w
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) d[t] = r[t] - w[t];
+    k_sub_b<S>::run(blockIdx.x, gridDim.x, r, w, d, n);
 }
 
 __global__ void k_bg_fv(FVK K, double *hbx, double *hbxw, double *hbz) {
@@ -1061,10 +1196,10 @@ int to_fv(jfnk_ctx *c, const Si *u, So *v, cudaStream_t s, So *x0 = nullptr, con
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: jf_launch(k_to_fv<Si, So, 2>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 3: jf_launch(k_to_fv<Si, So, 3>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 4: jf_launch(k_to_fv<Si, So, 4>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
-        case 5: jf_launch(k_to_fv<Si, So, 5>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 2: jf_launch<k_to_fv_b<Si, So, 2>>(k_to_fv<Si, So, 2>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 3: jf_launch<k_to_fv_b<Si, So, 3>>(k_to_fv<Si, So, 3>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 4: jf_launch<k_to_fv_b<Si, So, 4>>(k_to_fv<Si, So, 4>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
+        case 5: jf_launch<k_to_fv_b<Si, So, 5>>(k_to_fv<Si, So, 5>, g, EPB * NP, 0, s, K, u, v, c->opts.massfix && !c->opts.transfer_l2, x0, dtau0); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -1078,10 +1213,10 @@ int to_dg(jfnk_ctx *c, const Si *v, So *u, int acc, cudaStream_t s) {
     const int EPB = (128 / NP) > 0 ? 128 / NP : 1;
     const unsigned g = (unsigned)((c->n_el + EPB - 1) / EPB);
     switch (c->np1) {
-        case 2: jf_launch(k_to_dg<Si, So, 2>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 3: jf_launch(k_to_dg<Si, So, 3>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 4: jf_launch(k_to_dg<Si, So, 4>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
-        case 5: jf_launch(k_to_dg<Si, So, 5>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 2: jf_launch<k_to_dg_b<Si, So, 2>>(k_to_dg<Si, So, 2>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 3: jf_launch<k_to_dg_b<Si, So, 3>>(k_to_dg<Si, So, 3>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 4: jf_launch<k_to_dg_b<Si, So, 4>>(k_to_dg<Si, So, 4>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
+        case 5: jf_launch<k_to_dg_b<Si, So, 5>>(k_to_dg<Si, So, 5>, g, EPB * NP, 0, s, K, v, u, c->opts.massfix && !c->opts.transfer_l2, acc); jf_launched(); break;
         default: return JFNK_EINVAL;
     }
     JF_CK(cudaGetLastError());
@@ -1101,14 +1236,14 @@ void launch_fv(bool l4, unsigned g, int tb, cudaStream_t s, const FVK &K, const 
                const double *fu, double adt, typename SOf<T>::type *out, int bf = 0,
                RKS rk = RKS{nullptr, 0, 1.0, 1.0f}) {
     if (l4) {
-        jf_launch(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf, rk);
+        jf_launch<k_fv_b<T, IN, MODE, V, 4>>(k_fv<T, IN, MODE, V, 4>, g, tb, 0, s, K, ld, x, b, dt, fu, adt, out, bf, rk);
     } else if (tb >= 256) {   // tile rows follow the block size: 32 x 8 or 32 x 4 cells
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 7) / 8));
-        jf_launch(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
+        jf_launch<k_fv_tile_b<T, IN, MODE, V, 8>>(k_fv_tile<T, IN, MODE, V, 8>, gt, FV_TX * 8, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
                   rk);
     } else {
         const unsigned gt = (unsigned)(((K.NX + FV_TX - 1) / FV_TX) * ((K.NZ + 3) / 4));
-        jf_launch(k_fv_tile<T, IN, MODE, V, 4>, gt, FV_TX * 4, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
+        jf_launch<k_fv_tile_b<T, IN, MODE, V, 4>>(k_fv_tile<T, IN, MODE, V, 4>, gt, FV_TX * 4, 0, s, K, ld, b, dt, fu, adt, out, nullptr, nullptr, bf,
                   rk);
     }
     jf_launched();
@@ -1214,7 +1349,7 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
     const bool f2 = L.fac == 2;
     const unsigned g = nblk((l4 ? (f2 ? 16 : 4) : 1) * nc, tb);   // lanes per coarse cell
     c->fv_calls++;
-#define JF_DR(T, IN, V, LN, F2, ...) jf_launch(k_fv_defect_restrict<T, IN, V, LN, F2>, g, tb, 0, s, __VA_ARGS__)
+#define JF_DR(T, IN, V, LN, F2, ...) jf_launch<k_fv_defect_restrict_b<T, IN, V, LN, F2>>(k_fv_defect_restrict<T, IN, V, LN, F2>, g, tb, 0, s, __VA_ARGS__)
 #define JF_DR2(T, IN, V, ...)                                \
     do {                                                     \
         if (!l4) JF_DR(T, IN, V, 1, false, __VA_ARGS__);     \
@@ -1227,10 +1362,10 @@ int fv_defect_restrict(jfnk_ctx *c, int l, const void *x, const void *b, void *b
 #define JF_DRT(T, IN, V, ld, bb, fuu, outc, xcc, dtc_, bff)                                                     \
     do {                                                                                                        \
         if (tz == 8)                                                                                            \
-            jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
+            jf_launch<k_fv_tile_b<T, IN, FV_DEFRES, V, 8>>(k_fv_tile<T, IN, FV_DEFRES, V, 8>, gt, FV_TX * 8, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
                       outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0, 1.0f});                                                                    \
         else                                                                                                    \
-            jf_launch(k_fv_tile<T, IN, FV_DEFRES, V, 4>, gt, FV_TX * 4, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
+            jf_launch<k_fv_tile_b<T, IN, FV_DEFRES, V, 4>>(k_fv_tile<T, IN, FV_DEFRES, V, 4>, gt, FV_TX * 4, 0, s, K, ld, bb, nullptr, fuu, c->mg_adt, \
                       outc, xcc, dtc_, bff, RKS{nullptr, 0, 1.0, 1.0f});                                                                    \
     } while (0)
     if (!l4 && f2) {
@@ -1312,7 +1447,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
                 for (int k = 0; k < ns; ++k) {
                     const double a = c->opts.rk_alpha[k];
                     if (zero && k == 0) {
-                        jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)out, (const S *)L.b,
+                        jf_launch<k_scale_dtau_b<S>>(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)out, (const S *)L.b,
                                   (const S *)L.dtau, n1, a);
                         jf_launched();
                     } else {
@@ -1333,7 +1468,7 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
                 L.r = rest[1];
                 zero = false;
             } else if (zero) {
-                jf_launch(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)L.b, (const S *)L.dtau, n1,
+                jf_launch<k_scale_dtau_b<S>>(k_scale_dtau<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)L.b, (const S *)L.dtau, n1,
                           1.0);
                 jf_launched();
                 zero = false;
@@ -1351,16 +1486,17 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
     if (l < c->nlev - 1) {
         FVLev &C = c->lev[l + 1];
         const bool fuse = c->mid_pre >= 1 && !rk_multi(c);
-        if (zero || c->prec == 64) {
-            // FP64: separate defect and restriction (one thread per fine cell keeps the
-            // FP64-bound defect kernel occupied)
+        if (zero || c->prec == 64 || (L.fac != 2 && !fv_four_lanes(c, n1))) {
+            // FP64, and large levels agglomerated by 3 or 5 (odd k + 1): separate defect
+            // and restriction (one thread per fine cell keeps the defect kernel occupied;
+            // the fused kernel would run fac^2 cells one after another per coarse cell)
             if (zero) {
-                jf_launch(k_neg<S>, nblk(L.n, 256), 256, 0, s, (S *)L.r, (const S *)L.b, L.n);
+                jf_launch<k_neg_b<S>>(k_neg<S>, nblk(L.n, 256), 256, 0, s, (S *)L.r, (const S *)L.b, L.n);
                 jf_launched();
             } else {
                 JF_RET(fv_smooth_or_defect(c, l, FV_DEFECT, L.x, L.b, L.r, s));
             }
-            jf_launch(k_restrict_b<S>, nblk(C.n, 256), 256, 0, s, (const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
+            jf_launch<k_restrict_b_b<S>>(k_restrict_b<S>, nblk(C.n, 256), 256, 0, s, (const S *)L.r, L.NX, L.NZ, L.fac, (S *)C.b,
                                                            fuse ? (S *)C.x : nullptr, (const S *)C.dtau,
                                                            (c->prec == 16 && l + 1 == c->nlev - 1) ? 1 : 0);
             jf_launched();
@@ -1382,14 +1518,14 @@ int mg_cycle_t(jfnk_ctx *c, int l, bool zero, bool first_done, cudaStream_t s) {
             L.x2 = t;
             post -= 1;
         } else {
-            jf_launch(k_prolong<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac,
+            jf_launch<k_prolong_b<S>>(k_prolong<S>, nblk(L.n, 256), 256, 0, s, (S *)L.x, (const S *)C.x, L.NX, L.NZ, L.fac,
                       zero ? 1 : 0);
             jf_launched();
         }
         zero = false;
     }
     JF_RET(smooth(post));
-    if (zero) JF_CK(cudaMemsetAsync(L.x, 0, L.n * sizeof(S), s));
+    if (zero) JF_CK(jf_memset(L.x, 0, L.n * sizeof(S), s));
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -1401,7 +1537,7 @@ template <>
 int dg_smooth_step<double>(jfnk_ctx *c, const double *r, double *&z, double *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        jf_launch(k_scale_dtau_dg<double>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dg, c->npt, NP, 1.0); jf_launched();
+        jf_launch<k_scale_dtau_dg_b<double>>(k_scale_dtau_dg<double>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dg, c->npt, NP, 1.0); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1427,7 +1563,7 @@ template <>
 int dg_smooth_step<float>(jfnk_ctx *c, const float *r, float *&z, float *&z2, bool &zero, cudaStream_t s) {
     const int NP = c->np1 * c->np1;
     if (zero) {
-        jf_launch(k_scale_dtau_dg<float>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dgf, c->npt, NP, 1.0); jf_launched();
+        jf_launch<k_scale_dtau_dg_b<float>>(k_scale_dtau_dg<float>, nblk(c->N, 256), 256, 0, s, z, r, c->dtau_dgf, c->npt, NP, 1.0); jf_launched();
         zero = false;
         JF_CK(cudaGetLastError());
         return JFNK_OK;
@@ -1462,7 +1598,7 @@ int dg_defect<double>(jfnk_ctx *c, const double *r, const double *z, double *d, 
     a.adt = c->mg_adt;
     a.out0 = c->w2;
     JF_RET(dg_apply(c, DG_JV, a, s));
-    jf_launch(k_sub<double>, nblk(c->N, 256), 256, 0, s, r, c->w2, d, c->N); jf_launched();
+    jf_launch<k_sub_b<double>>(k_sub<double>, nblk(c->N, 256), 256, 0, s, r, c->w2, d, c->N); jf_launched();
     JF_CK(cudaGetLastError());
     return JFNK_OK;
 }
@@ -1508,7 +1644,7 @@ int dg_rk_step(jfnk_ctx *c, const S *r, S *&z, S *&z2, S *&z3, bool &zero, cudaS
         if (k == ns - 1 && last_out) out = last_out;
         const double a = c->opts.rk_alpha[k];
         if (zero && k == 0) {
-            jf_launch(k_scale_dtau_dg<S>, nblk(c->N, 256), 256, 0, s, out, r,
+            jf_launch<k_scale_dtau_dg_b<S>>(k_scale_dtau_dg<S>, nblk(c->N, 256), 256, 0, s, out, r,
                       sizeof(S) == 8 ? (const S *)c->dtau_dg : (const S *)c->dtau_dgf, c->npt, NP, a);
             jf_launched();
             JF_CK(cudaGetLastError());
@@ -1608,7 +1744,7 @@ int apply_t(jfnk_ctx *c, const S *r, S *zout, cudaStream_t s) {
         if (i == c->dg_post - 1) z2 = zout;   // the last step writes the output itself
         JF_RET(dg_smooth_step<S>(c, r, z, z2, zero, s));
     }
-    if (c->dg_post == 0) JF_CK(cudaMemcpyAsync(zout, z, c->N * sizeof(S), cudaMemcpyDeviceToDevice, s));
+    if (c->dg_post == 0) JF_CK(jf_memcpy(zout, z, c->N * sizeof(S), cudaMemcpyDeviceToDevice, s));
     for (int l = 0; l < c->nlev; ++l) {
         c->lev[l].x = sx[l];
         c->lev[l].x2 = sx2[l];
@@ -1632,7 +1768,7 @@ int fv_setup_background(jfnk_ctx *c, cudaStream_t s) {
 
 int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
     // every pointer the captured graph holds is context-owned
-    JF_CK(cudaMemcpyAsync(c->Ulin, Uin, 8 * c->N, cudaMemcpyDeviceToDevice, s));
+    JF_CK(jf_memcpy(c->Ulin, Uin, 8 * c->N, cudaMemcpyDeviceToDevice, s));
     const double *U = c->Ulin;
     c->mg_adt = adt;
     c->mg_U = U;
@@ -1640,7 +1776,7 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
     // copy of the state otherwise (a step-size heuristic; one warp per element)
     const unsigned gd = (unsigned)(((size_t)c->n_el * 32 + 127) / 128);
     if (c->prec == 64) {
-        jf_launch(k_dg_dtau<double>, gd, 128, 0, s, U, (const double *)c->ubv, c->grid.nx, c->grid.nz, c->np1,
+        jf_launch<k_dg_dtau_b<double>>(k_dg_dtau<double>, gd, 128, 0, s, U, (const double *)c->ubv, c->grid.nx, c->grid.nz, c->np1,
                   c->pc, c->powtab, 1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt, c->opts.sigma_dg, c->dtau_dg,
                   c->dtau_dgf);
         jf_launched();
@@ -1648,7 +1784,7 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
         JF_RET(to_fv<double, double>(c, U, (double *)c->lev[0].u, s));
     } else {
         JF_RET(blas_copy_d2f(U, c->Usf, c->N, s));
-        jf_launch(k_dg_dtau<float>, gd, 128, 0, s, (const float *)c->Usf, (const float *)c->ubvf, c->grid.nx,
+        jf_launch<k_dg_dtau_b<float>>(k_dg_dtau<float>, gd, 128, 0, s, (const float *)c->Usf, (const float *)c->ubvf, c->grid.nx,
                   c->grid.nz, c->np1, c->pc, c->powtab, 1.0 / c->hx, 1.0 / c->hz, c->phys.mu, adt,
                   c->opts.sigma_dg, c->dtau_dg, c->dtau_dgf);
         jf_launched();
@@ -1662,18 +1798,18 @@ int mg_linearize(jfnk_ctx *c, const double *Uin, double adt, cudaStream_t s) {
         if (l > 0) {
             FVLev &F = c->lev[l - 1];
             if (c->prec == 64)
-                jf_launch(k_restrict<double>, nblk(L.n, 256), 256, 0, s, (const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
+                jf_launch<k_restrict_body<double>>(k_restrict<double>, nblk(L.n, 256), 256, 0, s, (const double *)F.u, F.NX, F.NZ, F.fac, (double *)L.u);
             else
-                jf_launch(k_restrict_b<float>, nblk(L.n, 256), 256, 0, s, (const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u,
+                jf_launch<k_restrict_b_b<float>>(k_restrict_b<float>, nblk(L.n, 256), 256, 0, s, (const float *)F.u, F.NX, F.NZ, F.fac, (float *)L.u,
                                                                    nullptr, nullptr,
                                                                    (c->prec == 16 && l == c->nlev - 1) ? 1 : 0);
             jf_launched();
         }
         if (c->prec == 64) {
             JF_RET(fv_op64(c, l, FV_RES, (const double *)L.u, nullptr, nullptr, (double *)L.fu, s));
-            jf_launch(k_fv_dtau<double>, nblk(n1), 128, 0, s, K, (const double *)L.u, adt, c->opts.sigma_fv, (double *)L.dtau); jf_launched();
+            jf_launch<k_fv_dtau_b<double>>(k_fv_dtau<double>, nblk(n1), 128, 0, s, K, (const double *)L.u, adt, c->opts.sigma_fv, (double *)L.dtau); jf_launched();
         } else {
-            jf_launch(k_fv_dtau<float>, nblk(n1), 128, 0, s, K, (const float *)L.u, adt, c->opts.sigma_fv, (float *)L.dtau); jf_launched();
+            jf_launch<k_fv_dtau_b<float>>(k_fv_dtau<float>, nblk(n1), 128, 0, s, K, (const float *)L.u, adt, c->opts.sigma_fv, (float *)L.dtau); jf_launched();
         }
         JF_CK(cudaGetLastError());
     }
@@ -1742,14 +1878,14 @@ void jf_invalidate_graphs(jfnk_ctx *c) {
 
 int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float *r32) {
     const size_t sS = c->prec == 64 ? 8 : 4;
-    if (c->prec != 64 && r32 && (c->capturing || !c->opts.use_graphs)) {
+    if (c->prec != 64 && r32 && (c->capturing || !c->opts.use_graphs || t_jf_rec)) {
         // inside an Arnoldi step: the FP32 copy of r exists already, and the
         // launches go straight into the caller's stream (or capture)
         return apply_t<float>(c, r32, (float *)z, s);
     }
-    if (c->prec == 64) JF_CK(cudaMemcpyAsync(c->pin, r, 8 * c->N, cudaMemcpyDeviceToDevice, s));
+    if (c->prec == 64) JF_CK(jf_memcpy(c->pin, r, 8 * c->N, cudaMemcpyDeviceToDevice, s));
     else JF_RET(blas_copy_d2f(r, (float *)c->pin, c->N, s));   // FP32 preconditioner: r enters in FP32
-    if (c->opts.use_graphs && !c->capturing) {
+    if (c->opts.use_graphs && !c->capturing && !t_jf_rec) {
         if (!c->mg_graph_valid || c->mg_graph_adt != c->mg_adt) JF_RET(capture(c));
         JF_CK(cudaGraphLaunch(c->mg_graph, s));
         jf_launched((unsigned)c->graph_launches);
@@ -1758,7 +1894,7 @@ int mg_apply(jfnk_ctx *c, const double *r, void *z, cudaStream_t s, const float 
     } else {
         JF_RET(apply_body(c, s));
     }
-    JF_CK(cudaMemcpyAsync(z, c->pout, sS * c->N, cudaMemcpyDeviceToDevice, s));
+    JF_CK(jf_memcpy(z, c->pout, sS * c->N, cudaMemcpyDeviceToDevice, s));
     return JFNK_OK;
 }
 

@@ -82,8 +82,8 @@ int apply_jv(jfnk_ctx *c, const double *U, double adt, const double *y, double *
 
 int read_norm(jfnk_ctx *c, const double *x, double *out, cudaStream_t s) {
     JF_RET(red_dot(c, x, x, c->N, c->scal + S_NORM, RED_SQRT, s));
-    JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal + S_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
-    JF_CK(cudaStreamSynchronize(s));
+    JF_CK(jf_memcpy(c->h_pinned, c->scal + S_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
+    JF_CK(jf_sync(s));
     *out = c->h_pinned[0];
     return JFNK_OK;
 }
@@ -102,7 +102,7 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
         JF_RET(mg_apply(c, vj, (char *)c->Z + (size_t)j * N * (c->prec == 64 ? 8 : 4), s,
                         c->prec == 64 ? nullptr : c->V32 + (size_t)j * N));
     } else {
-        JF_CK(cudaMemcpyAsync((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
+        JF_CK(jf_memcpy((double *)c->Z + (size_t)j * N, vj, 8 * N, cudaMemcpyDeviceToDevice, s));
     }
     bool eps_ready = false;
     const double *zj = z_as_double(c, j, c->w1, s, &rc, &eps_ready);
@@ -117,7 +117,7 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
         JF_RET(blas_cgs2(c, V, c->V32, j + 1, N, w, c->V32 + (size_t)(j + 1) * N, N, c->scal + S_H, c->scal + S_H2,
                          c->scal + S_W1, c->scal + S_NORM, c->scal + S_FLAG, s));   // normalises w too
         if (ph) ph->mark(3, s);
-        JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
+        JF_CK(jf_memcpy(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
         return JFNK_OK;
     }
     JF_RET(blas_mdot(c, V, j + 1, N, w, N, c->scal + S_H, s));
@@ -129,14 +129,14 @@ int arnoldi_step_work(jfnk_ctx *c, const double *U, double adt, int j, cudaStrea
     JF_RET(blas_scale_copy(w, c->scal + S_NORM, w, N, s));
     JF_RET(blas_copy_d2f(w, c->V32 + (size_t)(j + 1) * N, N, s));   // float copy of the basis
     if (ph) ph->mark(3, s);
-    JF_CK(cudaMemcpyAsync(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
+    JF_CK(jf_memcpy(c->h_pinned, c->scal, 8 * S_COUNT, cudaMemcpyDeviceToHost, s));
     return JFNK_OK;
 }
 
 // Arnoldi step j, replayed from a graph captured per j (pointers are all
 // context-owned: U is the context's copy of the Newton iterate).
 int arnoldi_step(jfnk_ctx *c, const double *U, double adt, int j, cudaStream_t s, Phases &ph) {
-    const bool graphs = c->opts.use_graphs && !ph.on && U == c->Ulin && j < 64;
+    const bool graphs = c->opts.use_graphs && !ph.on && U == c->Ulin && j < 64 && !t_jf_rec;
     if (!graphs) return arnoldi_step_work(c, U, adt, j, s, ph.on ? &ph : nullptr);
     if (c->arn_adt != adt) {
         for (int i = 0; i < 64; ++i)
@@ -193,7 +193,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
     const int maxit = c->opts.gmres_max;
     double *V = c->V;
     double H[65][64], cs[64], sn[64], g[65], y[64];
-    JF_CK(cudaMemsetAsync(x, 0, 8 * N, s));
+    JF_CK(jf_memset(x, 0, 8 * N, s));
     double beta;
     JF_RET(read_norm(c, b, &beta, s));
     if (!isfinite(beta)) return JFNK_ENAN;
@@ -201,10 +201,10 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
     if (beta <= tol_abs || beta == 0.0) return JFNK_OK;
     const double *r = b;
     while (*its < maxit) {
-        JF_CK(cudaMemcpyAsync(c->scal + S_NORM, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
+        JF_CK(jf_memcpy(c->scal + S_NORM, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
         JF_RET(blas_scale_copy(r, c->scal + S_NORM, V, N, s));
         JF_RET(blas_copy_d2f(V, c->V32, N, s));
-        JF_CK(cudaStreamSynchronize(s));   // beta lives on the host stack
+        JF_CK(jf_sync(s));   // beta lives on the host stack
         memset(H, 0, sizeof(H));
         for (int i = 0; i <= m; ++i) g[i] = 0.0;
         g[0] = beta;
@@ -212,7 +212,7 @@ int fgmres(jfnk_ctx *c, const double *U, double adt, const double *b, double *x,
         bool conv = false;
         for (int j = 0; j < m; ++j) {
             JF_RET(arnoldi_step(c, U, adt, j, s, ph));
-            JF_CK(cudaStreamSynchronize(s));
+            JF_CK(jf_sync(s));
             if (out_of_time(c)) return JFNK_ETIMEOUT;
             st.t_pre += ph.ms(0, 1);
             st.t_jv += ph.ms(1, 2);
@@ -305,7 +305,7 @@ int newton(jfnk_ctx *c, double *U, double adt, Stats &st, cudaStream_t s) {
         ph.mark(0, s);
         // the context's copy of U^k: the captured Arnoldi graphs hold this pointer
         if (c->mg_on) JF_RET(mg_linearize(c, U, adt, s));
-        else JF_CK(cudaMemcpyAsync(c->Ulin, U, 8 * c->N, cudaMemcpyDeviceToDevice, s));
+        else JF_CK(jf_memcpy(c->Ulin, U, 8 * c->N, cudaMemcpyDeviceToDevice, s));
         ph.mark(1, s);
         JF_RET(blas_scale(-1.0, c->G, c->G, c->N, s));
         int its = 0;
@@ -341,8 +341,8 @@ extern "C" int implicit_step(jfnk_ctx *c, double *U, double dt, int scheme, jfnk
     c->deadline = c->opts.time_budget_ms > 0.0 ? now_s() + 1e-3 * c->opts.time_budget_ms : 0.0;
     Stats st;
     int rc = JFNK_OK;
-    JF_CK(cudaMemcpyAsync(c->Usave, U, 8 * N, cudaMemcpyDeviceToDevice, s));
-    JF_CK(cudaMemcpyAsync(c->Ubs, U, 8 * N, cudaMemcpyDeviceToDevice, s));
+    JF_CK(jf_memcpy(c->Usave, U, 8 * N, cudaMemcpyDeviceToDevice, s));
+    JF_CK(jf_memcpy(c->Ubs, U, 8 * N, cudaMemcpyDeviceToDevice, s));
     int stages = 0;
     if (scheme == 0) {
         stages = 1;
@@ -354,17 +354,17 @@ extern "C" int implicit_step(jfnk_ctx *c, double *U, double dt, int scheme, jfnk
         if (rc == JFNK_OK) {
             // Ubar_2 = U^n + (1 - alpha) dt f(U_1); f(U_1) is the last residual's f
             stages = 2;
-            JF_CK(cudaMemcpyAsync(c->w1, c->fU, 8 * N, cudaMemcpyDeviceToDevice, s));
+            JF_CK(jf_memcpy(c->w1, c->fU, 8 * N, cudaMemcpyDeviceToDevice, s));
             rc = blas_axpby(1.0, c->Usave, (1.0 - a) * dt, c->w1, c->Ubs, N, s);
-            if (rc == JFNK_OK) rc = cudaMemcpyAsync(U, c->Ubs, 8 * N, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+            if (rc == JFNK_OK) rc = jf_memcpy(U, c->Ubs, 8 * N, cudaMemcpyDeviceToDevice, s) == cudaSuccess
                                         ? JFNK_OK
                                         : JFNK_ECUDA;
             if (rc == JFNK_OK) rc = newton(c, U, a * dt, st, s);
         }
     }
     if (rc != JFNK_OK && rc != JFNK_ECUDA) {
-        cudaMemcpyAsync(U, c->Usave, 8 * N, cudaMemcpyDeviceToDevice, s);
-        cudaStreamSynchronize(s);
+        jf_memcpy(U, c->Usave, 8 * N, cudaMemcpyDeviceToDevice, s);
+        jf_sync(s);
     }
     if (stats) {
         stats->status = rc;

@@ -97,6 +97,9 @@ def _lib():
             "jfnk_batch_destroy": (None, [P]),
             "jfnk_batch_step": (I, [P, P, P, P, P, P]),
             "jfnk_batch_dg_residual": (I, [P, P, P, P]),
+            "jfnk_batch_set_mode": (I, [P, I]),
+            "jfnk_batch_last_launches": (I, [P, P, P, P, P]),
+            "jfnk_batch_last_times": (I, [P, P]),
             "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
@@ -114,16 +117,36 @@ def _lib():
 lib = _lib
 
 
-class Batch:
-    """Ensemble members stepped concurrently (jfnk_batch_*)."""
+BATCH_STREAMS, BATCH_LOCKSTEP, BATCH_LOCKSTEP_UNGROUPED = 0, 1, 2
 
-    def __init__(self, contexts, max_threads=0):
+
+class Batch:
+    """Ensemble members stepped together (jfnk_batch_*): concurrently on their own
+    streams (mode BATCH_STREAMS) or in lock-step with one grouped launch per
+    operator across members (BATCH_LOCKSTEP)."""
+
+    def __init__(self, contexts, max_threads=0, mode=BATCH_STREAMS):
         self.contexts = list(contexts)
         arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
         h = C.c_void_p()
         _check(_lib().jfnk_batch_create(arr, len(self.contexts), int(max_threads), C.byref(h)),
                "jfnk_batch_create")
         self.h = h
+        if mode != BATCH_STREAMS:
+            self.set_mode(mode)
+
+    def set_mode(self, mode):
+        _check(_lib().jfnk_batch_set_mode(self.h, int(mode)), "jfnk_batch_set_mode")
+
+    def last_launches(self):
+        """{launches, grouped, member_launches, rounds} of the last lock-step step."""
+        v = [C.c_ulonglong() for _ in range(4)]
+        _check(_lib().jfnk_batch_last_launches(self.h, *[C.byref(x) for x in v]), "jfnk_batch_last_launches")
+        d = dict(zip(("launches", "grouped", "member_launches", "rounds"), [x.value for x in v]))
+        t = (C.c_double * 3)()
+        _check(_lib().jfnk_batch_last_times(self.h, t), "jfnk_batch_last_times")
+        d.update(ms_members=t[0], ms_issue=t[1], ms_device=t[2])
+        return d
 
     def close(self):
         if getattr(self, "h", None):

@@ -24,8 +24,10 @@ def _members():
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("prec", [64, 32])
-def test_batch_step_bitwise_equals_alone(prec):
+@pytest.mark.parametrize("prec,mode", [(64, 0), (32, 0), (32, 1), (64, 1)])
+def test_batch_step_bitwise_equals_alone(prec, mode):
+    # mode 1: lock-step, every operator launch shared by the members that reach it
+    # together (uneven grids and orders, one viscous member)
     import paper_2505_24504_gb300 as P
     ms, U0 = _members()
     alone = []
@@ -37,15 +39,51 @@ def test_batch_step_bitwise_equals_alone(prec):
         alone.append(to_cpu(U))
         ctx.close()
     ctxs = [gpu_context(m, precond_prec=prec) for m in ms]
-    batch = P.Batch(ctxs, max_threads=4)
+    batch = P.Batch(ctxs, max_threads=4, mode=mode)
     Us = [to_gpu(u) for u in U0]
     for _ in range(2):
         status, stats = batch.jfnk_batch_step(Us, [m.dt for m in ms], [m.scheme for m in ms])
         assert status == [0] * len(ms)
         assert all(s.newton_its > 0 for s in stats)
+        if mode == 1:
+            ll = batch.last_launches()
+            assert ll["grouped"] > 0 and ll["launches"] < ll["member_launches"], ll
     torch.cuda.synchronize()
     for a, u in zip(alone, Us):
         assert np.array_equal(a, to_cpu(u))
+    batch.close()
+
+
+@pytest.mark.timeout(600)
+def test_lockstep_same_shape_members_share_launches():
+    # eight members of one shape (different bubbles): bitwise equal to alone, and
+    # far fewer launches than the members would issue alone
+    import paper_2505_24504_gb300 as P
+    w = synth.BUBBLE_Q2_20x10
+    ms = [synth.scaled(w, 20, 10, k=2, scheme=1,
+                       bubble=synth.Bubble(1.0 + 0.4 * i, 8000.0 + 500.0 * i, 2000.0, 2000.0, 2000.0))
+          for i in range(8)]
+    U0 = []
+    for m in ms:
+        dg = oracle_dg(m)
+        U0.append(dg.init_state(m.theta_pert(dg.X, dg.Z)))
+    alone = []
+    for m, u in zip(ms, U0):
+        ctx = gpu_context(m, precond_prec=32)
+        U = to_gpu(u)
+        ctx.implicit_step(U, m.dt, scheme=m.scheme)
+        alone.append(to_cpu(U))
+        ctx.close()
+    ctxs = [gpu_context(m, precond_prec=32) for m in ms]
+    batch = P.Batch(ctxs, mode=P.jfnk.BATCH_LOCKSTEP)
+    Us = [to_gpu(u) for u in U0]
+    status, _ = batch.jfnk_batch_step(Us, [m.dt for m in ms], [m.scheme for m in ms])
+    assert status == [0] * len(ms)
+    ll = batch.last_launches()
+    torch.cuda.synchronize()
+    for a, u in zip(alone, Us):
+        assert np.array_equal(a, to_cpu(u))
+    assert ll["launches"] * 4 < ll["member_launches"], ll
     batch.close()
 
 

@@ -49,7 +49,8 @@ def test_time_budget_gives_etimeout_and_restores_the_state():
 
 
 @pytest.mark.timeout(600)
-def test_nan_in_one_batch_member_fails_only_that_member():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_nan_in_one_batch_member_fails_only_that_member(mode):
     # a NaN written into member 1's state: its residual norm is non-finite, so it
     # returns ENAN with its state restored (NaN included, bit for bit); the other
     # members' results are the bits they get when stepped alone
@@ -66,7 +67,7 @@ def test_nan_in_one_batch_member_fails_only_that_member():
         alone.append(to_cpu(U))
         c.close()
     ctxs = [gpu_context(m, precond_prec=32) for m in ms]
-    batch = P.Batch(ctxs, max_threads=3)
+    batch = P.Batch(ctxs, max_threads=3, mode=mode)
     Us = [to_gpu(u) for u in U0]
     Us[1].view(-1)[17] = float("nan")
     bad = to_cpu(Us[1])
