@@ -93,9 +93,10 @@ namespace {
 constexpr size_t TAB_ALIGN = 256;
 
 // Replay every member's recorded operations on L->s.  Operations that are not
-// launches run as soon as they reach the head of their member's queue; then the
-// launch kind found at the most heads runs once for all those members (the
-// first member in member order breaks ties), until every queue is empty.
+// launches run as soon as they reach the head of their member's queue; then one
+// launch kind at the heads runs once for all the members it heads (the kind
+// whose members have the most operations left; the first member in member
+// order breaks ties), until every queue is empty.
 cudaError_t replay(JfLockstep *L) {
     const int n = (int)L->rec.size();
     std::vector<size_t> h(n, 0);
@@ -121,11 +122,15 @@ cudaError_t replay(JfLockstep *L) {
         auto key_of = [&](const JfOp &o) {
             return Key{(const void *)o.glaunch, o.block.x, o.block.y, o.block.z, o.smem};
         };
-        std::map<Key, int> count;
-        int best = -1, best_n = 0;
+        // each head counts with the operations its member has left in this round, so
+        // that members that are behind advance first and the others wait for them
+        // at the kernels they share (more members per grouped launch)
+        std::map<Key, size_t> count;
+        int best = -1;
+        size_t best_n = 0;
         for (int m = 0; m < n; ++m) {
             if (h[m] >= L->rec[m].ops.size()) continue;
-            const int c = ++count[key_of(L->rec[m].ops[h[m]])];
+            const size_t c = (count[key_of(L->rec[m].ops[h[m]])] += L->rec[m].ops.size() - h[m]);
             if (c > best_n) {
                 best_n = c;
                 best = m;
