@@ -82,6 +82,12 @@ def parse():
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
                    help="only run REPS FP64 FD products (face + volume kernels) of the workload "
                         "and print their CUDA-event times (small profiler captures)")
+    p.add_argument("--profile-ensemble", type=int, default=-1, metavar="MODE",
+                   help="only run one batched step of the ensemble in batch MODE (0 streams, 1 lock-step, "
+                        "2 lock-step without grouping) inside the NVTX range timed_step, after one "
+                        "untimed step (profiler captures)")
+    p.add_argument("--ensemble-order", type=int, default=0, metavar="K",
+                   help="with --profile-ensemble: only the members of order K (0: all)")
     return p.parse_args()
 
 
@@ -765,6 +771,27 @@ def main():
         y = torch.randn(c64.N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
         fm, vm = c64.time_operator(1, U0, y, args.profile_dg)
         print(json.dumps({"profile": "FP64 FD product", "face_ms": fm, "volume_ms": vm, "reps": args.profile_dg}))
+        return
+    if args.profile_ensemble >= 0:
+        members = [m for m in synth.ensemble(args.ensemble) if args.ensemble_order in (0, m.k)]
+        ctxs = [make_context(m, 32) for m in members]
+        Us = [initial_state(c, m) for c, m in zip(ctxs, members)]
+        batch = P.Batch(ctxs, max_threads=args.ensemble_threads, mode=args.profile_ensemble)
+        dts, sch = [m.dt for m in members], [m.scheme for m in members]
+        batch.jfnk_batch_step(Us, dts, sch)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_step")
+        t0 = time.perf_counter()
+        status, _ = batch.jfnk_batch_step(Us, dts, sch, raise_on_error=False)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": "ensemble step", "mode": args.profile_ensemble, "members": len(members),
+                          "order": args.ensemble_order, "ms": ms, "failed": sum(1 for x in status if x != 0),
+                          "launches": batch.last_launches()}))
+        batch.close()
+        for c in ctxs:
+            c.close()
         return
 
     # ---- the product form: FP32 preconditioner ---------------------------------

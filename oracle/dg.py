@@ -10,8 +10,11 @@ K_h: int_E (F_c^pert - F_v) : grad psi + S^pert . psi      (eq. elementint)
 I_h: interior faces: {F_v(U,[[U]])^T : grad psi} + {F_v} : [[psi]]
      all faces:     -(H_c^pert - H_v) : [[psi]]               (eq. surfaceint)
 with H_c = HLLC, the viscous numerical flux read as symmetric interior
-penalty (penalty eta = C_IP (k+1)^2 mu / h on the momentum and rho theta
-components), slip walls with a mirrored ghost state and no viscous wall flux.
+penalty on the variables F_v differentiates: the penalty term is
+C_IP (k+1)^2 / h {A(U)} [[U]] = C_IP (k+1)^2 / h mu {rho} ([[u]], [[w]], [[theta]])
+to first order (A(U) dU = mu (0, d(rho u) - u d rho, d(rho w) - w d rho,
+d(rho theta) - theta d rho), {.} the mean of the two sides), slip walls with a
+mirrored ghost state and no viscous wall flux.
 Volume and face integrals use the collocated GL nodes, so the mass matrix is
 diagonal (Sec. 2.2) and f = M^-1 L_h is a per-node division.
 """
@@ -147,10 +150,10 @@ class DG:
             FvR = viscous_flux(UR, gxL[:, :, iR], ph)
             avg = 0.5 * (FvL + FvR)
             J = ULp - URp
-            pen = eta * J
-            pen[0] = 0.0
             symL = 0.5 * viscous_flux(UL, J, ph)       # 1/2 A(U_L) [U]
             symR = 0.5 * viscous_flux(UR, J, ph)
+            # penalty on the jumps of u, w, theta: (eta / mu) {A(U)} [U]
+            pen = (eta / ph.mu) * (symL + symR)
             # element L (outward +x, trace at +1)
             f[:, :, iL] += sc[None, None, None, None, :] * (
                 t.lp[None, None, None, None, :] * (avg - pen)[..., None]
@@ -215,10 +218,9 @@ class DG:
             FvT = viscous_flux(UT, gzB[:, iT] + dUf, ph)
             avg = 0.5 * (FvB + FvT)
             J = UBp - UTp
-            pen = eta * J
-            pen[0] = 0.0
             symB = 0.5 * viscous_flux(UB, J, ph)
             symT = 0.5 * viscous_flux(UT, J, ph)
+            pen = (eta / ph.mu) * (symB + symT)
             f[:, iB] += sc[None, None, None, :, None] * (
                 t.lp[None, None, None, :, None] * (avg - pen)[:, :, :, None, :]
                 + (2.0 / hz) * t.dlp[None, None, None, :, None] * symB[:, :, :, None, :])

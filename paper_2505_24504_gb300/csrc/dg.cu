@@ -211,20 +211,20 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
 #pragma unroll
         for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
         if (VISC && !wallL && !wallR) {
-            T FL[4], FR[4], Jp[4];
+            T FL[4], FR[4], Jp[4], AL[4], AR[4];
             viscous(UL, gL, K.pc, FL);
             viscous(UR, gR, K.pc, FR);
 #pragma unroll
             for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
-#pragma unroll
-            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + mkc(K.eta_x, K.eta_xf, T{}) * Jp[v];
-            T AL[4], AR[4];
             viscous(UL, Jp, K.pc, AL);
             viscous(UR, Jp, K.pc, AR);
+            // interior penalty on the jumps of u, w, theta: eta {A(U)} [U]
+            const auto eta = mkc(K.eta_x, K.eta_xf, T{});
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sL[c] = half * AL[c + 1];
                 sR[c] = half * AR[c + 1];
+                Phi[c + 1] = Phi[c + 1] - half * (FL[c + 1] + FR[c + 1]) + eta * (sL[c] + sR[c]);
             }
         }
         const size_t fb = ((size_t)ez * (nx + 1) + fx) * NP1 + s;
@@ -305,20 +305,19 @@ __device__ __forceinline__ void faces_body(const DGK &K, const Loader<T, IN> &ld
 #pragma unroll
         for (int c = 0; c < 3; ++c) sL[c] = sR[c] = zero;
         if (VISC && !wallB && !wallT) {
-            T FB[4], FT[4], Jp[4];
+            T FB[4], FT[4], Jp[4], AB[4], AT[4];
             viscous(UB, gB, K.pc, FB);
             viscous(UT, gT, K.pc, FT);
 #pragma unroll
             for (int v = 0; v < 4; ++v) Jp[v] = trB[v] - trT[v];
-#pragma unroll
-            for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + mkc(K.eta_z, K.eta_zf, T{}) * Jp[v];
-            T AB[4], AT[4];
             viscous(UB, Jp, K.pc, AB);
             viscous(UT, Jp, K.pc, AT);
+            const auto eta = mkc(K.eta_z, K.eta_zf, T{});
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sL[c] = half * AB[c + 1];
                 sR[c] = half * AT[c + 1];
+                Phi[c + 1] = Phi[c + 1] - half * (FB[c + 1] + FT[c + 1]) + eta * (sL[c] + sR[c]);
             }
         }
         const size_t fb = ((size_t)fz * nx + ex) * NP1 + s;
@@ -800,20 +799,18 @@ struct k_dgtl_b {
     #pragma unroll
                 for (int v = 0; v < 4; ++v) Phi[v] = H[v];
                 if (VISC && !wallL && !wallR) {
-                    TL32 FL[4], FR[4], Jp[4];
+                    TL32 FL[4], FR[4], Jp[4], AL[4], AR[4];
                     viscous(UL, gL, K.pc, FL);
                     viscous(UR, gR, K.pc, FR);
     #pragma unroll
                     for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
-    #pragma unroll
-                    for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FL[v] + FR[v]) + TLc{K.eta_xf} * Jp[v];
-                    TL32 AL[4], AR[4];
                     viscous(UL, Jp, K.pc, AL);
                     viscous(UR, Jp, K.pc, AR);
     #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         sLv[q] = half * AL[q + 1];
                         sRv[q] = half * AR[q + 1];
+                        Phi[q + 1] = Phi[q + 1] - half * (FL[q + 1] + FR[q + 1]) + TLc{K.eta_xf} * (sLv[q] + sRv[q]);
                     }
                 } else {
     #pragma unroll
@@ -867,20 +864,18 @@ struct k_dgtl_b {
     #pragma unroll
                 for (int v = 0; v < 4; ++v) Phi[v] = H[v];
                 if (VISC && !wallB && !wallT) {
-                    TL32 FB[4], FT[4], Jp[4];
+                    TL32 FB[4], FT[4], Jp[4], AB[4], AT[4];
                     viscous(UL, gB, K.pc, FB);
                     viscous(UR, gT, K.pc, FT);
     #pragma unroll
                     for (int v = 0; v < 4; ++v) Jp[v] = trL[v] - trR[v];
-    #pragma unroll
-                    for (int v = 1; v < 4; ++v) Phi[v] = Phi[v] - half * (FB[v] + FT[v]) + TLc{K.eta_zf} * Jp[v];
-                    TL32 AB[4], AT[4];
                     viscous(UL, Jp, K.pc, AB);
                     viscous(UR, Jp, K.pc, AT);
     #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         sLv[q] = half * AB[q + 1];
                         sRv[q] = half * AT[q + 1];
+                        Phi[q + 1] = Phi[q + 1] - half * (FB[q + 1] + FT[q + 1]) + TLc{K.eta_zf} * (sLv[q] + sRv[q]);
                     }
                 } else {
     #pragma unroll
@@ -1000,8 +995,9 @@ DGK make_K(jfnk_ctx *c) {
     K.mu = c->phys.mu;
     K.gf = (float)K.g;
     const double n1 = c->np1;
-    K.eta_x = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hx;
-    K.eta_z = c->opts.c_ip * n1 * n1 * c->phys.mu / c->hz;
+    // interior-penalty factor C_IP (k+1)^2 / h; the viscosity enters through A(U)
+    K.eta_x = c->opts.c_ip * n1 * n1 / c->hx;
+    K.eta_z = c->opts.c_ip * n1 * n1 / c->hz;
     K.pc = c->pc;
     K.pt = c->powtab;
     K.ubv = c->ubv;

@@ -162,6 +162,29 @@ def test_sipg_operator_symmetric_negative_semidefinite(k):
     assert np.abs(J @ np.ones(J.shape[1])).max() <= 1e-11 * np.abs(J).max()
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_viscous_operator_blind_to_density_at_fixed_velocity_and_theta(k, periodic):
+    # F_v = mu rho (0, grad u, grad w, grad theta) (Sec. 4) sees U only through the
+    # gradients of u, w and theta, so a perturbation of rho alone at fixed u = w = 0 and
+    # fixed theta (rho theta' = theta rho') gives f = 0 even when it jumps between
+    # elements: the interior penalty acts on the jumps of u, w, theta (weighted by
+    # mu rho), not on those of the conserved rho u, rho w, rho theta
+    ph = Physics(cp=3.5, cv=2.5, g=0.0, p0=1.0, theta0=1.3, mu=0.3, background=UNIFORM,
+                 convective=False)
+    dg = DG(4, 3, 0, 1, 0, 1.5, k, ph, periodic_x=periodic)
+    rng = np.random.Generator(np.random.Philox(11))
+    U = dg.zeros()
+    U[0] = 0.2 * rng.standard_normal(U[0].shape)
+    U[3] = (dg.Ub[3] / dg.Ub[0]) * U[0]
+    f = dg.rhs(U)
+    assert np.abs(f).max() <= 1e-11
+    # a theta jump at fixed rho is damped: the same test with rho theta' alone is not blind
+    V = dg.zeros()
+    V[3] = U[0]
+    assert np.abs(dg.rhs(V)).max() > 1e-2
+
+
 @pytest.mark.parametrize("k,order", [(1, 1.8), (2, 2.8)])
 def test_sipg_heat_equation_order(k, order):
     # rho = 1, no convection: d_t (rho theta) = mu Laplacian(rho theta), exact decay
