@@ -78,6 +78,9 @@ def parse():
     p.add_argument("--secondary-steps", type=int, default=3,
                    help="timed steps of the viscous, inertia-gravity and rising-bubble workloads (0: skip)")
     p.add_argument("--no-sweep", action="store_true", help="skip the mg-key sweep and the dt trends")
+    p.add_argument("--no-long", action="store_true",
+                   help="skip the test cases run to their end times (density current 900 s, "
+                        "inertia gravity 3000 s, rising bubble 300 s)")
     p.add_argument("--schedule", default=None, metavar="KEY", help="override the preset's mg key")
     p.add_argument("--profile-dg", type=int, default=0, metavar="REPS",
                    help="only run REPS FP64 FD products (face + volume kernels) of the workload "
@@ -530,6 +533,72 @@ def run_case(w, steps, preset=None, **opt):
             "mg_key": o.get("mg_key", w.mg_key)}
 
 
+def _node_xz(w):
+    """Node coordinates (nz, nx, k+1, k+1) in the library's layout [ez][ex][b][a] of one variable."""
+    import numpy as np
+    xi = np.polynomial.legendre.leggauss(w.k + 1)[0]
+    hx, hz = (w.x1 - w.x0) / w.nx, (w.z1 - w.z0) / w.nz
+    ex = np.arange(w.nx)[None, :, None, None]
+    ez = np.arange(w.nz)[:, None, None, None]
+    X = w.x0 + (ex + (1 + xi[None, None, None, :]) / 2) * hx
+    Z = w.z0 + (ez + (1 + xi[None, None, :, None]) / 2) * hz
+    shape = (w.nz, w.nx, w.k + 1, w.k + 1)
+    return np.broadcast_to(X, shape), np.broadcast_to(Z, shape)
+
+
+def run_long_runs():
+    """The paper's test cases run to their end times (Sec. 4.1-4.3) with the FP32
+    preconditioner: SDIRK2 steps at the workload's dt, every step's status, Newton
+    and GMRES counts, device time, and a transport check of the final state taken
+    from the perturbation variables: the density current's front (largest x at
+    the lowest node row where rho' exceeds rho_surface / 300, i.e. theta' below
+    about -1 K at near-constant pressure), the inertia-gravity packet's centre (the
+    mean flow of 20 m/s carries it from 100 km to 160 km in 3000 s: the centroid
+    of (rho theta)'^2 along the node row nearest mid height), the rising bubble's
+    height (z of the most negative rho')."""
+    import numpy as np
+    import torch
+    cases = ((synth.DENSITY_CURRENT_Q2_256x32, 900.0), (synth.INERTIA_GRAVITY_Q3_80x3, 3000.0),
+             (synth.RISING_BUBBLE_Q3_40x80, 300.0))
+    out = {}
+    for w, T in cases:
+        ctx = make_context(w, 32)
+        U = initial_state(ctx, w)
+        n = int(round(T / w.dt))
+        s = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        failed, newton, gmres = 0, 0, 0
+        e0.record(s)
+        for _ in range(n):
+            st = ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
+            failed += st.status != 0
+            newton += st.newton_its
+            gmres += st.gmres_its
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        a = U.detach().cpu().numpy().reshape((4, w.nz, w.nx, w.k + 1, w.k + 1))
+        X, Z = _node_xz(w)
+        row = {"workload": w.name, "end_time_s": n * w.dt, "steps": n, "failed_steps": failed,
+               "newton_per_step": newton / n, "gmres_per_step": gmres / n, "seconds": ms / 1e3,
+               "steps_per_s": n / (ms / 1e3)}
+        if w is synth.DENSITY_CURRENT_Q2_256x32:
+            cold = a[0, 0, :, 0, :] > 1.161 / 300.0
+            row["front_km"] = float(X[0, :, 0, :][cold].max() / 1e3) if cold.any() else 0.0
+        elif w is synth.INERTIA_GRAVITY_Q3_80x3:
+            mid = np.abs(Z - 0.5 * (w.z0 + w.z1))
+            sel = mid == mid.min()
+            wgt = np.where(sel, a[3] ** 2, 0.0)
+            row["packet_centre_km"] = float((wgt * X).sum() / wgt.sum() / 1e3)
+        else:
+            i = np.argmin(a[0])
+            row["bubble_height_m"] = float(Z.ravel()[i])
+        out[w.name] = row
+        ctx.close()
+    return out
+
+
 def run_mg_sweep():
     """GMRES iterations, operator calls and time of one SDIRK2 (or BE) step for the
     paper's schedule variants (Sec. 4.2): none, mg001111V, mg111111V, mg111111W and
@@ -936,6 +1005,8 @@ def main():
         line["inertia_gravity"]["transfer_l2"] = {k: v for k, v in run_case(igw, args.secondary_steps,
                                                                             transfer_l2=1).items() if k != "workload"}
         line["rising_bubble"] = run_case(synth.RISING_BUBBLE_Q3_40x80, args.secondary_steps)
+    if not args.no_long:
+        line["long_runs"] = run_long_runs()
     if not args.no_sweep:
         line["mg_sweep"] = run_mg_sweep()
         line["dt_trends"] = run_dt_trends()
