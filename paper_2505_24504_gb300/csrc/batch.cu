@@ -16,10 +16,14 @@
 // a grouped block runs the body with its member's arguments, block index and
 // block count, so in both modes a member's result is bit-identical alone and in
 // any batch.
+#include <limits.h>
+#include <linux/futex.h>
+#include <sys/syscall.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
-#include <condition_variable>
 #include <map>
 #include <memory>
 #include <new>
@@ -60,12 +64,16 @@ cudaError_t jf_memset(void *dst, int v, size_t n, cudaStream_t s) {
 
 // Shared state of one lock-step batch step: member states, their recorders and
 // the replay's table memory (device tables filled from pinned staging).
+// Members and coordinator meet through two futex words, so that a round's
+// members wake in parallel instead of one by one through a mutex:
+// `pending` counts the members still running in this round (the last to reach
+// a synchronisation point or to finish wakes the coordinator), `gen` is bumped
+// by the coordinator when the round's replay is complete.
 struct JfLockstep {
-    std::mutex mu;
-    std::condition_variable cv;
     std::vector<int> state;   // 0 running, 1 waiting at a synchronisation, 2 finished
     std::vector<JfRecorder> rec;
-    unsigned gen = 0;
+    std::atomic<int> pending{0};
+    std::atomic<int> gen{0};
     cudaError_t err = cudaSuccess;
     cudaStream_t s = nullptr;
     char *dtab = nullptr;
@@ -76,15 +84,32 @@ struct JfLockstep {
     bool group = true;   // false: every recorded launch replays alone (the same order)
 };
 
+namespace {
+
+static_assert(sizeof(std::atomic<int>) == sizeof(int), "futex word");
+
+void futex_wait(std::atomic<int> *w, int expected) {
+    syscall(SYS_futex, reinterpret_cast<int *>(w), FUTEX_WAIT_PRIVATE, expected, nullptr, nullptr, 0);
+}
+void futex_wake(std::atomic<int> *w) {
+    syscall(SYS_futex, reinterpret_cast<int *>(w), FUTEX_WAKE_PRIVATE, INT_MAX, nullptr, nullptr, 0);
+}
+
+// A member leaves the running set (state 1: at a synchronisation point, 2: finished).
+void member_arrive(JfLockstep *L, int member, int state) {
+    L->state[member] = state;
+    if (L->pending.fetch_sub(1) == 1) futex_wake(&L->pending);
+}
+
+}  // namespace
+
 cudaError_t jf_sync(cudaStream_t s) {
     JfRecorder *r = t_jf_rec;
     if (!r) return cudaStreamSynchronize(s);
     JfLockstep *L = r->ls;
-    std::unique_lock<std::mutex> lk(L->mu);
-    const unsigned g = L->gen;
-    L->state[r->member] = 1;
-    L->cv.notify_all();
-    L->cv.wait(lk, [&] { return L->gen != g; });
+    const int g = L->gen.load();
+    member_arrive(L, r->member, 1);
+    for (int v = L->gen.load(); v == g; v = L->gen.load()) futex_wait(&L->gen, v);
     return L->err;
 }
 
@@ -206,16 +231,10 @@ void coordinate(JfLockstep &L) {
     auto ms = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
     for (;;) {
         const auto t0 = clk::now();
-        std::unique_lock<std::mutex> lk(L.mu);
-        L.cv.wait(lk, [&] {
-            for (int x : L.state)
-                if (x == 0) return false;
-            return true;
-        });
+        for (int v = L.pending.load(); v != 0; v = L.pending.load()) futex_wait(&L.pending, v);
         bool done = true;
         for (int x : L.state)
             if (x != 2) done = false;
-        lk.unlock();
         const auto t1 = clk::now();
         cudaError_t e = L.err == cudaSuccess ? replay(&L) : L.err;
         const auto t2 = clk::now();
@@ -226,14 +245,18 @@ void coordinate(JfLockstep &L) {
         L.ms_device += ms(t2, t3);
         if (e == cudaSuccess) e = es;
         ++L.rounds;
-        lk.lock();
         for (auto &r : L.rec) r.ops.clear();
         L.err = e;
         if (done) return;
+        int run = 0;
         for (int &x : L.state)
-            if (x == 1) x = 0;
-        ++L.gen;
-        L.cv.notify_all();
+            if (x == 1) {
+                x = 0;
+                ++run;
+            }
+        L.pending.store(run);
+        L.gen.fetch_add(1);
+        futex_wake(&L.gen);
     }
 }
 
@@ -261,6 +284,7 @@ int lockstep_step(jfnk_batch *b, double *const *U, const double *dt, const int *
         JfLockstep &L = *Ls.back();
         const int nm = (int)cls[q].size();
         L.state.assign(nm, 0);
+        L.pending.store(nm);
         L.rec.resize(nm);
         L.s = b->streams[cls[q][0]];
         L.dtab = b->dtab + (size_t)q * cap;
@@ -282,9 +306,7 @@ int lockstep_step(jfnk_batch *b, double *const *U, const double *dt, const int *
             rc[i] = implicit_step(b->ctx[i], U[i], dt[i], scheme[i], &st, b->streams[i]);
             t_jf_rec = nullptr;
             if (stats) stats[i] = st;
-            std::lock_guard<std::mutex> lk(L.mu);
-            L.state[j] = 2;
-            L.cv.notify_all();
+            member_arrive(&L, j, 2);
         });
     }
     std::vector<std::thread> coords;

@@ -526,3 +526,21 @@ def test_implicit_step_multistage_smoother_parity(name, prec):
     got = to_cpu(U, dg.shape)
     assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
+
+
+@pytest.mark.timeout(600)
+def test_density_current_runs_past_the_landing_of_the_cold_air():
+    # the viscous density current on its full grid (Q2 256x32, dt = 1 s, FP32
+    # preconditioner) through t = 150 s, past the landing of the cold air near
+    # t = 110 s: every step converges and the state stays finite (the interior
+    # penalty acts on the jumps of u, w, theta; on the conserved variables a theta
+    # jump at constant rho theta grew there until the step failed)
+    w = synth.DENSITY_CURRENT_Q2_256x32
+    dg = oracle_dg(w)
+    ctx = gpu_context(w, precond_prec=32)
+    U = to_gpu(dg.init_state(w.theta_pert(dg.X, dg.Z)))
+    for i in range(150):
+        st = ctx.implicit_step(U, w.dt, scheme=w.scheme, raise_on_error=False)
+        assert st.status == 0, (i, st.status)
+    assert torch.isfinite(U).all()
+    ctx.close()
