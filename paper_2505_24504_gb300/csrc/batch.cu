@@ -117,23 +117,50 @@ namespace {
 
 constexpr size_t TAB_ALIGN = 256;
 
-// Replay every member's recorded operations on L->s.  Operations that are not
-// launches run as soon as they reach the head of their member's queue; then one
-// launch kind at the heads runs once for all the members it heads (the kind
-// whose members have the most operations left; the first member in member
-// order breaks ties), until every queue is empty.
+// Replay every member's recorded operations on L->s.  The round is planned
+// first: operations that are not launches are taken as soon as they reach the
+// head of their member's queue; then one launch kind at the heads is taken once
+// for all the members it heads (the kind whose members have the most operations
+// left; the first member in member order breaks ties), its argument table
+// staged, until every queue is empty.  Then the staged tables go to the device
+// in one copy and the planned operations are issued in order.
+// One step of a planned round: a member's operation replayed as is (m >= 0), or a
+// grouped launch whose table was staged at `off` (m < 0).
+struct Action {
+    int m;
+    size_t i;
+    const JfOp *op;
+    size_t off;
+    int nmem;
+    unsigned total;
+};
+
+// Issue planned actions: one copy of the staged tables, then the operations in order.
+cudaError_t issue(JfLockstep *L, const std::vector<Action> &acts, size_t staged) {
+    if (staged) {
+        const cudaError_t e = cudaMemcpyAsync(L->dtab, L->htab, staged, cudaMemcpyHostToDevice, L->s);
+        if (e != cudaSuccess) return e;
+    }
+    for (const Action &a : acts) {
+        const cudaError_t e = a.m >= 0 ? a.op->run(L->s)
+                                       : a.op->glaunch(L->dtab + a.off, a.nmem, a.total, a.op->block, a.op->smem, L->s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t replay(JfLockstep *L) {
     const int n = (int)L->rec.size();
     std::vector<size_t> h(n, 0);
     size_t off = 0;
     std::vector<int> sel;
+    std::vector<Action> acts;
     for (;;) {
         bool any = false;
         for (int m = 0; m < n; ++m) {
             std::vector<JfOp> &ops = L->rec[m].ops;
             while (h[m] < ops.size() && !ops[h[m]].glaunch) {
-                const cudaError_t e = ops[h[m]].run(L->s);
-                if (e != cudaSuccess) return e;
+                acts.push_back(Action{m, h[m], &ops[h[m]], 0, 0, 0});
                 if (ops[h[m]].kernel) {
                     ++L->launches;
                     ++L->member_launches;
@@ -142,7 +169,7 @@ cudaError_t replay(JfLockstep *L) {
             }
             if (h[m] < ops.size()) any = true;
         }
-        if (!any) return cudaSuccess;
+        if (!any) return issue(L, acts, off);
         using Key = std::tuple<const void *, unsigned, unsigned, unsigned, size_t>;
         auto key_of = [&](const JfOp &o) {
             return Key{(const void *)o.glaunch, o.block.x, o.block.y, o.block.z, o.smem};
@@ -176,16 +203,17 @@ cudaError_t replay(JfLockstep *L) {
         const JfOp &o0 = L->rec[sel[0]].ops[h[sel[0]]];
         if (!L->group) sel.resize(1);
         if (sel.size() == 1) {   // alone: the member's own launch
-            const cudaError_t e = o0.run(L->s);
-            if (e != cudaSuccess) return e;
+            acts.push_back(Action{sel[0], h[sel[0]], &o0, 0, 0, 0});
             ++h[sel[0]];
             continue;
         }
         const size_t es = o0.ent.size(), bytes = es * sel.size();
         if (bytes > L->cap) return cudaErrorInvalidValue;
-        if (off + bytes > L->cap) {   // staging full: let the queued copies drain
-            const cudaError_t e = cudaStreamSynchronize(L->s);
+        if (off + bytes > L->cap) {   // staging full: issue what is planned and let it drain
+            cudaError_t e = issue(L, acts, off);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(L->s);
             if (e != cudaSuccess) return e;
+            acts.clear();
             off = 0;
         }
         unsigned total = 0;
@@ -196,9 +224,7 @@ cudaError_t replay(JfLockstep *L) {
             memcpy(dst, &total, sizeof(unsigned));   // JfEnt::b0
             total += o.nb;
         }
-        cudaError_t e = cudaMemcpyAsync(L->dtab + off, L->htab + off, bytes, cudaMemcpyHostToDevice, L->s);
-        if (e == cudaSuccess) e = o0.glaunch(L->dtab + off, (int)sel.size(), total, o0.block, o0.smem, L->s);
-        if (e != cudaSuccess) return e;
+        acts.push_back(Action{-1, 0, &o0, off, (int)sel.size(), total});
         ++L->grouped;
         off += (bytes + TAB_ALIGN - 1) / TAB_ALIGN * TAB_ALIGN;
         for (int m : sel) ++h[m];
