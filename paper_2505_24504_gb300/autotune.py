@@ -90,10 +90,10 @@ def tuned_context(grid, k, phys, opts, U, reps: int = 3, path: str = DEFAULT_CAC
     return ctx, dict(entry, cached=False)
 
 
-SCHEDULES = ("mg111111V", "mg112211V", "mg122211V", "mg132211V", "mg123311V", "mg222211V", "mg133311V",
-             "mg122222V", "mg001111V", "mg112222V")
+SCHEDULES = ("mg111111V", "mg112211V", "mg122211V", "mg131211V", "mg132211V", "mg132210V", "mg133211V",
+             "mg123311V", "mg222211V", "mg133311V", "mg122222V", "mg001111V", "mg112222V")
 SIGMA_FV = (0.7, 0.85, 1.0, 1.15)
-SIGMA_DG = (0.7, 1.0, 1.3)
+SIGMA_DG = (0.7, 0.8, 0.9, 1.0, 1.3)
 
 
 def schedule_key(grid, k, phys, opts, dt) -> str:

@@ -28,7 +28,7 @@ from oracle.solver import NewtonStats, implicit_step  # noqa: E402
 
 # the schedules the benchmark runs (mg key of Sec. 4, pseudo-time factors of Sec. 3.5)
 RUNS = {
-    "warm_bubble_q3_160x80": (synth.BUBBLE_Q3_160x80, dict(mg_key="mg132211V", sigma_fv=1.0, sigma_dg=1.0)),
+    "warm_bubble_q3_160x80": (synth.BUBBLE_Q3_160x80, dict(mg_key="mg131211V", sigma_fv=1.0, sigma_dg=0.9)),
     "warm_bubble_q2_20x10": (synth.BUBBLE_Q2_20x10, dict(mg_key="mg111111V", sigma_fv=1.0, sigma_dg=1.0)),
 }
 
