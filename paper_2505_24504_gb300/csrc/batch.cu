@@ -120,8 +120,7 @@ constexpr size_t TAB_ALIGN = 256;
 // Replay every member's recorded operations on L->s.  The round is planned
 // first: operations that are not launches are taken as soon as they reach the
 // head of their member's queue; then one launch kind at the heads is taken once
-// for all the members it heads (the kind whose members have the most operations
-// left; the first member in member order breaks ties), its argument table
+// for all the members it heads (see the choice below), its argument table
 // staged, until every queue is empty.  Then the staged tables go to the device
 // in one copy and the planned operations are issued in order.
 // One step of a planned round: a member's operation replayed as is (m >= 0), or a
@@ -150,8 +149,17 @@ cudaError_t issue(JfLockstep *L, const std::vector<Action> &acts, size_t staged)
 }
 
 cudaError_t replay(JfLockstep *L) {
+    using Key = std::tuple<const void *, unsigned, unsigned, unsigned, size_t>;
+    auto key_of = [](const JfOp &o) {
+        return Key{(const void *)o.glaunch, o.block.x, o.block.y, o.block.z, o.smem};
+    };
     const int n = (int)L->rec.size();
     std::vector<size_t> h(n, 0);
+    // the groupable launches each member has still to make in this round, by kind
+    std::vector<std::map<Key, int>> left(n);
+    for (int m = 0; m < n; ++m)
+        for (const JfOp &o : L->rec[m].ops)
+            if (o.glaunch) ++left[m][key_of(o)];
     size_t off = 0;
     std::vector<int> sel;
     std::vector<Action> acts;
@@ -170,38 +178,53 @@ cudaError_t replay(JfLockstep *L) {
             if (h[m] < ops.size()) any = true;
         }
         if (!any) return issue(L, acts, off);
-        using Key = std::tuple<const void *, unsigned, unsigned, unsigned, size_t>;
-        auto key_of = [&](const JfOp &o) {
-            return Key{(const void *)o.glaunch, o.block.x, o.block.y, o.block.z, o.smem};
-        };
-        // each head counts with the operations its member has left in this round, so
-        // that members that are behind advance first and the others wait for them
-        // at the kernels they share (more members per grouped launch)
-        std::map<Key, size_t> count;
-        int best = -1;
-        size_t best_n = 0;
+        // Choose the kind to launch: a kind at some heads that no other member will
+        // still need later in this round (launching it now loses no member), the one
+        // whose members have the most operations left; if every kind at the heads is
+        // still needed by members behind, the kind whose members have the most
+        // operations left (members that are behind advance first)
+        std::map<Key, size_t> weight;
+        std::map<Key, int> heads;
         for (int m = 0; m < n; ++m) {
             if (h[m] >= L->rec[m].ops.size()) continue;
-            const size_t c = (count[key_of(L->rec[m].ops[h[m]])] += L->rec[m].ops.size() - h[m]);
-            if (c > best_n) {
-                best_n = c;
-                best = m;
+            const Key k = key_of(L->rec[m].ops[h[m]]);
+            weight[k] += L->rec[m].ops.size() - h[m];
+            ++heads[k];
+        }
+        const Key *best = nullptr;
+        bool best_free = false;
+        size_t best_w = 0;
+        for (const auto &kv : weight) {
+            int later = 0;   // members not at this kind now that still need it
+            for (int m = 0; m < n; ++m) {
+                if (h[m] >= L->rec[m].ops.size()) continue;
+                auto it = left[m].find(kv.first);
+                const int need = it == left[m].end() ? 0 : it->second;
+                if (need > 0 && !(key_of(L->rec[m].ops[h[m]]) == kv.first)) ++later;
+            }
+            const bool free = later == 0;
+            if (!best || (free && !best_free) || (free == best_free && kv.second > best_w)) {
+                best = &kv.first;
+                best_free = free;
+                best_w = kv.second;
             }
         }
-        // the earliest member holding the winning kind
-        const Key k = key_of(L->rec[best].ops[h[best]]);
-        for (int m = 0; m < n; ++m)
-            if (h[m] < L->rec[m].ops.size() && key_of(L->rec[m].ops[h[m]]) == k) {
-                best = m;
-                break;
-            }
+        const Key k = *best;
         sel.clear();
-        for (int m = best; m < n; ++m)
+        for (int m = 0; m < n; ++m)
             if (h[m] < L->rec[m].ops.size() && key_of(L->rec[m].ops[h[m]]) == k) sel.push_back(m);
         L->member_launches += sel.size();
         ++L->launches;
+        for (int m : sel) --left[m][k];
         const JfOp &o0 = L->rec[sel[0]].ops[h[sel[0]]];
-        if (!L->group) sel.resize(1);
+        if (!L->group) {   // every member alone, in member order
+            for (int m : sel) {
+                acts.push_back(Action{m, h[m], &L->rec[m].ops[h[m]], 0, 0, 0});
+                ++h[m];
+            }
+            L->launches += sel.size() - 1;
+            continue;
+        }
         if (sel.size() == 1) {   // alone: the member's own launch
             acts.push_back(Action{sel[0], h[sel[0]], &o0, 0, 0, 0});
             ++h[sel[0]];
