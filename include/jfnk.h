@@ -333,6 +333,18 @@ int jfnk_fv_residual(jfnk_ctx *ctx, int level, const double *u_dev, double *f_de
  * accuracy can be checked against CUDA's pow. */
 int jfnk_eos_pressure(jfnk_ctx *ctx, const double *E_dev, size_t n, double *p_dev, void *stream);
 
+/* out = y - alpha_dt J(U) y, the FP32 DG product of the preconditioner's
+ * smoothing steps (Sec. 3.5) at state U' (contexts with precond_prec < 64):
+ * tangent-linear FP32 fluxes in the launch form dg_fused selects, widened to
+ * FP64.
+ * U, y, out: device arrays of N doubles in the state layout.  J is the
+ * derivative of f = M^-1 L_h (eq. convDiscr) at U along y.  Overwrites the
+ * preconditioner's FP32 linearisation and workspace (the next implicit_step
+ * or mg_precondition linearises again).  Errors: JFNK_EINVAL for a null
+ * pointer or an FP64-preconditioner context. */
+int jfnk_tangent_product(jfnk_ctx *ctx, const double *U_dev, const double *y_dev, double alpha_dt,
+                         double *out_dev, void *stream);
+
 /* Times the two kernels of one DG operator evaluation with CUDA events
  * recorded on `stream` around each launch: which 0 = FP64 residual,
  * 1 = FP64 finite-difference product with direction y (in the form the

@@ -642,6 +642,21 @@ int jfnk_eos_pressure(jfnk_ctx *c, const double *E, size_t n, double *p, void *s
 
 int jfnk_fv_levels(const jfnk_ctx *c) { return c ? c->nlev : 0; }
 
+int jfnk_tangent_product(jfnk_ctx *c, const double *U, const double *y, double adt, double *out, void *stream) {
+    if (!c || !U || !y || !out || c->prec == 64) return JFNK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    JF_RET(blas_copy_d2f(y, (float *)c->pz, c->N, s));
+    JF_RET(blas_copy_d2f(U, c->Usf, c->N, s));
+    DGArgs a = {};
+    a.U = U;
+    a.Uf = c->Usf;
+    a.yf = (const float *)c->pz;
+    a.adt = adt;
+    a.out0 = c->pz2;
+    JF_RET(dg_apply(c, DG_TLJV, a, s));
+    return blas_copy_f2d((const float *)c->pz2, out, c->N, s);
+}
+
 int jfnk_time_operator(jfnk_ctx *c, int which, const double *U, const double *y, int reps, double *ms,
                        void *stream) {
     if (!c || !U || !ms || reps < 1 || which < 0 || which > 4 || (which > 0 && which != 4 && !y)) return JFNK_EINVAL;

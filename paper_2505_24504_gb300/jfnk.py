@@ -102,6 +102,7 @@ def _lib():
             "jfnk_batch_last_times": (I, [P, P]),
             "jfnk_norm2_noalloc": (I, [P, S, P, P]),
             "jfnk_time_operator": (I, [P, I, P, P, I, P, P]),
+            "jfnk_tangent_product": (I, [P, P, P, D, P, P]),
             "jfnk_launch_count": (C.c_ulonglong, []),
             "jfnk_autotune": (I, [P, P, P, I, P, P, P]),
             "jfnk_strerror": (C.c_char_p, [I]),
@@ -286,6 +287,10 @@ class Context:
     def eos_pressure(self, E, p, stream=None):
         _check(_lib().jfnk_eos_pressure(self.h, _ptr(E), E.numel(), _ptr(p), _stream(stream)),
                "jfnk_eos_pressure")
+
+    def tangent_product(self, U, y, adt, out, stream=None):
+        _check(_lib().jfnk_tangent_product(self.h, _ptr(U), _ptr(y), float(adt), _ptr(out), _stream(stream)),
+               "jfnk_tangent_product")
 
     def time_operator(self, which, U, y, reps, stream=None):
         ms = (C.c_double * 2)()
