@@ -380,6 +380,12 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
     __shared__ O sDx[NP1][NP1], sDz[NP1][NP1];
     __shared__ O sDn[NP1][NP1];
     __shared__ O sl[8][NP1];
+    __shared__ double sce[2];   // eps and adt / eps of the FD modes: one IEEE division per block
+    if ((MODE == DG_JV || MODE == DG_SMOOTH64) && threadIdx.x == 0) {
+        const double e0 = *A.eps;
+        sce[0] = e0;
+        sce[1] = e0 != 0.0 ? A.adt / e0 : 0.0;
+    }
     if (IN != 2) load_powtab(&spt, K.pt);
     Loader<T, IN> ld = ld0;
     ld.prepare();
@@ -479,8 +485,8 @@ __device__ __forceinline__ void volume_body(const DGK &K, const Loader<T, IN> &l
     if (!active) return;
     const O lmxa = sl[0][a], lpxa = sl[1][a], dlmxa = sl[2][a], dlpxa = sl[3][a];
     const O lmzb = sl[4][b], lpzb = sl[5][b], dlmzb = sl[6][b], dlpzb = sl[7][b];
-    const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? *A.eps : 0.0;
-    const double ceps = eps != 0.0 ? A.adt / eps : 0.0;   // adt / eps once per thread
+    const double eps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? sce[0] : 0.0;
+    const double ceps = (MODE == DG_JV || MODE == DG_SMOOTH64) ? sce[1] : 0.0;
     const float adtf = (MODE == DG_TLJV || MODE == DG_TLSMOOTH) ? A.adtf : 0.0f;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
