@@ -78,3 +78,49 @@ def test_norm_wrappers_reject_bad_arguments_before_any_launch():
         jfnk.norm2_noalloc(x64, out, n=-1)
     with pytest.raises(ValueError):
         jfnk.norm2_noalloc(x64, torch.zeros(1, dtype=torch.float32))
+
+
+def test_create_rejects_invalid_arguments_before_any_device_call(libpath):
+    # jfnk_create checks the order, the grid, the physical constants and the
+    # options before its first CUDA call, so every case below returns
+    # JFNK_EINVAL (-1) on a host without a GPU as on one with a GPU
+    import paper_2505_24504_gb300 as P
+    from paper_2505_24504_gb300.jfnk import JfnkError
+
+    def grid(**kw):
+        a = dict(nx=4, nz=2, x0=0.0, x1=4000.0, z0=0.0, z1=2000.0, periodic_x=0)
+        a.update(kw)
+        return P.Grid(a["nx"], a["nz"], a["x0"], a["x1"], a["z0"], a["z1"], a["periodic_x"])
+
+    def phys(**kw):
+        a = dict(cp=1005.0, cv=717.95, g=9.81, p0=1e5, theta0=300.0, mu=0.0, background=0, ubg=0.0, wbg=0.0,
+                 N_bv=0.0)
+        a.update(kw)
+        return P.Physics(*a.values())
+
+    cases = [
+        (grid(), 0, phys(), {}), (grid(), 5, phys(), {}),
+        (grid(nx=0), 2, phys(), {}), (grid(nz=0), 2, phys(), {}), (grid(nx=-3), 2, phys(), {}),
+        (grid(x1=0.0), 2, phys(), {}), (grid(z1=-1.0), 2, phys(), {}),
+        (grid(), 2, phys(cp=700.0), {}), (grid(), 2, phys(cv=0.0), {}), (grid(), 2, phys(p0=0.0), {}),
+        (grid(), 2, phys(theta0=-1.0), {}), (grid(), 2, phys(mu=-1.0), {}),
+        (grid(), 2, phys(background=3), {}), (grid(), 2, phys(background=2, N_bv=0.0), {}),
+        (grid(), 2, phys(), dict(gmres_restart=0)), (grid(), 2, phys(), dict(gmres_restart=65)),
+        (grid(), 2, phys(), dict(gmres_max=0)), (grid(), 2, phys(), dict(newton_max=0)),
+        (grid(), 2, phys(), dict(precond_prec=48)), (grid(), 2, phys(), dict(precond_fd_eps=-1.0)),
+        (grid(), 2, phys(), dict(time_budget_ms=-5.0)), (grid(), 2, phys(), dict(dg_fused=3)),
+        (grid(), 2, phys(), dict(rk_stages=5)), (grid(), 2, phys(), dict(rk_stages=2, rk_alpha=(0.5, 0.0))),
+        (grid(), 2, phys(), dict(tile_faces=96)), (grid(), 2, phys(), dict(tile_volume=3)),
+        (grid(), 2, phys(), dict(tile_fv=512)),
+    ]
+    for g, k, ph, opt in cases:
+        with pytest.raises(JfnkError) as ei:
+            P.Context(g, k, ph, P.Opts.defaults(**opt))
+        assert ei.value.code == -1, (g.nx, g.nz, k, opt)
+    # the valid arguments themselves are not what fails: on a GPU they create a
+    # context, without one the first CUDA call reports JFNK_ECUDA (-3)
+    try:
+        c = P.Context(grid(), 2, phys(), P.Opts.defaults())
+        c.close()
+    except JfnkError as e:
+        assert e.code == -3, e.code
