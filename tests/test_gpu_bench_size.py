@@ -1,9 +1,10 @@
 """The benchmark's own configuration against the FP64 oracle, element by
 element: warm bubble on DG Q3 160 x 80 (819,200 unknowns), 5 FV levels, the
 schedule and launch shapes of the benchmark (presets.WARM_BUBBLE_Q3_160x80),
-FP64 and FP32 preconditioner forms.  The oracle's SDIRK2 step takes a few
-minutes on one host core, so this module is marked slow; it still runs with
--m gpu."""
+FP64 and FP32 preconditioner forms; and the operators at the largest size of
+any workload (the ensemble's DG Q4 member on 320 x 160 quads).  The oracle's
+SDIRK2 step takes a few minutes on one host core, so this module is marked
+slow; it still runs with -m gpu."""
 import numpy as np
 import pytest
 
@@ -112,3 +113,42 @@ def test_sdirk2_step_at_bench_size(dg, oracle_step, prec):
     got = to_cpu(U, dg.shape)
     assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref - U0)
+
+
+# The largest configuration of any workload: the ensemble's biggest member,
+# DG Q4 on 320 x 160 quads (5,120,000 unknowns).
+BIG = max(synth.ensemble(64), key=lambda m: m.n_unknowns)
+
+
+@pytest.fixture(scope="module")
+def big():
+    dg = oracle_dg(BIG)
+    return dg, perturbed_state(BIG, dg, seed=71, scale=0.2)
+
+
+def test_operators_at_the_largest_size(big):
+    dg, Up = big
+    assert BIG.k == 4 and BIG.n_unknowns == 5_120_000
+    ctx = gpu_context(BIG, precond_prec=32)
+    U = to_gpu(Up)
+    # FP64 residual, element by element
+    f = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.dg_residual(U, f)
+    got, ref = to_cpu(f, dg.shape), dg.rhs(Up)
+    assert rel(got, ref) <= 1e-12
+    for v in range(4):
+        assert np.abs(got[v] - ref[v]).max() <= 1e-12 * np.abs(ref[v]).max()
+    # FP64 FD product at a large step (bound of its cancellation, as at the bench size)
+    y = synth.random_perturbation(dg.shape[1:], 72)
+    adt, eps = (1 - 2 ** -0.5) * BIG.dt, 1e-3
+    refj = dg.jv(Up, ref, y, adt, eps=eps)
+    Jy = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.jv_product(U, None, to_gpu(y), adt, eps, Jy)
+    f1 = dg.rhs(Up + eps * y)
+    bound = adt * 1e-12 * (np.linalg.norm(f1) + np.linalg.norm(ref)) / eps + 1e-13 * np.linalg.norm(refj)
+    assert np.linalg.norm(to_cpu(Jy, dg.shape) - refj) <= bound
+    # FP32 DG product of the preconditioner against the complex-step product
+    exact = dg.jv_exact(Up, y, adt)
+    out = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    ctx.tangent_product(U, to_gpu(y), adt, out)
+    assert np.linalg.norm(to_cpu(out, dg.shape) - exact) <= 2e-3 * np.linalg.norm(exact - y)
