@@ -769,7 +769,8 @@ def cpu_baseline(w):
     """The oracle on the host: a bounded sample of this workload's step on one
     core scaled to steps/s by the oracle's own counts, plus one whole step of the
     small warm-bubble workload on one core and on every core at once (independent
-    steps in `nproc` processes)."""
+    steps in `nproc` processes), and one whole step of the viscous density
+    current on one core."""
     import multiprocessing as mp
     rec = oracle_counts()
     smp = OracleSampler(w, PRESET)
@@ -779,6 +780,8 @@ def cpu_baseline(w):
     sampled = time.perf_counter() - t0
     sec = smp.seconds_per_step(rec)
     one = _oracle_whole_step_seconds(synth.BUBBLE_Q2_20x10)
+    wv = synth.DENSITY_CURRENT_Q2_256x32
+    visc = _oracle_whole_step_seconds(wv)
     ncores = min(len(os.sched_getaffinity(0)), 64)
     t1 = time.perf_counter()
     with mp.get_context("spawn").Pool(ncores) as pool:
@@ -793,7 +796,10 @@ def cpu_baseline(w):
             "small_workload_whole_step": {"workload": synth.BUBBLE_Q2_20x10.name, "seconds_1_core": one,
                                           "steps_per_s_1_core": 1.0 / one, "cores_all": ncores,
                                           "steps_per_s_all_cores": ncores / wall,
-                                          "note": "independent steps, one process per core"}}
+                                          "note": "independent steps, one process per core"},
+            "viscous_workload_whole_step": {"workload": wv.name, "seconds_1_core": visc,
+                                            "steps_per_s_1_core": 1.0 / visc,
+                                            "dof_per_s_1_core": wv.n_unknowns / visc}}
 
 
 def run_reference(args):
