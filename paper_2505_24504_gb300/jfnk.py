@@ -160,8 +160,23 @@ class Batch:
         except Exception:
             pass
 
+    def _member_states(self, *lists):
+        """Per (arrays, name): one contiguous float64 CUDA state per member, of that
+        member's size (every count, dtype and length checked before the rest)."""
+        for states, what in lists:
+            if len(states) != len(self.contexts):
+                raise ValueError(f"{what}: {len(states)} arrays for {len(self.contexts)} members")
+            for c, t in zip(self.contexts, states):
+                _vec(t, c.N, what)
+        for states, _ in lists:
+            for t in states:
+                _ptr(t)
+
     def jfnk_batch_step(self, states, dts, schemes, raise_on_error=True):
         n = len(self.contexts)
+        self._member_states((states, "states"))
+        if len(dts) != n or len(schemes) != n:
+            raise ValueError(f"dts and schemes need one entry per member ({n})")
         U = (C.c_void_p * n)(*[s.data_ptr() for s in states])
         dt = (C.c_double * n)(*[float(x) for x in dts])
         sc = (C.c_int * n)(*[int(x) for x in schemes])
@@ -176,6 +191,7 @@ class Batch:
         """f_m = M^-1 L_h(U_m) for all members: one face and one volume launch per
         (order, viscous) group of members."""
         n = len(self.contexts)
+        self._member_states((states, "states"), (outs, "outs"))
         U = (C.c_void_p * n)(*[_ptr(s).value for s in states])
         f = (C.c_void_p * n)(*[_ptr(o).value for o in outs])
         _check(_lib().jfnk_batch_dg_residual(self.h, U, f, _stream(stream)), "jfnk_batch_dg_residual")
@@ -202,6 +218,21 @@ def norm2_noalloc(x, out, n=None, stream=None):
 
 def launch_count() -> int:
     return int(_lib().jfnk_launch_count())
+
+
+def _vec(t, n, what, at_least=False):
+    """t unchanged after checking that it is float64 with n elements (at least n
+    with at_least).  The library indexes every array by the context's sizes, so a
+    shorter or narrower tensor would be read or written past its end: refuse it
+    before anything is launched.  None passes (optional arguments)."""
+    import torch
+    if t is None:
+        return t
+    if t.dtype != torch.float64:
+        raise ValueError(f"{what}: expected float64, got {t.dtype}")
+    if t.numel() < n or (not at_least and t.numel() != n):
+        raise ValueError(f"{what}: expected {'at least ' if at_least else ''}{n} elements, got {t.numel()}")
+    return t
 
 
 def _ptr(t):
@@ -260,20 +291,26 @@ class Context:
         return x, z
 
     def jfnk_init_state(self, theta_pert, U, stream=None):
+        _vec(theta_pert, self.N // 4, "theta_pert")
+        _vec(U, self.N, "U")
         _check(_lib().jfnk_init_state(self.h, _ptr(theta_pert), _ptr(U), _stream(stream)), "jfnk_init_state")
 
     def dg_residual(self, U, f, stream=None):
+        self._states(U=U, f=f)
         _check(_lib().dg_residual(self.h, _ptr(U), _ptr(f), _stream(stream)), "dg_residual")
 
     def jv_product(self, U, fU, y, alpha_dt, eps, Jy, stream=None):
+        self._states(U=U, fU=fU, y=y, Jy=Jy)
         _check(_lib().jv_product(self.h, _ptr(U), _ptr(fU), _ptr(y), float(alpha_dt), float(eps), _ptr(Jy),
                                  _stream(stream)), "jv_product")
 
     def mg_precondition(self, U, alpha_dt, r, z, stream=None):
+        self._states(U=U, r=r, z=z)
         _check(_lib().mg_precondition(self.h, _ptr(U), float(alpha_dt), _ptr(r), _ptr(z), _stream(stream)),
                "mg_precondition")
 
     def implicit_step(self, U, dt, scheme=1, stream=None, raise_on_error=True) -> Stats:
+        self._states(U=U)
         st = Stats()
         rc = _lib().implicit_step(self.h, _ptr(U), float(dt), int(scheme), C.byref(st), _stream(stream))
         if raise_on_error:
@@ -285,20 +322,35 @@ class Context:
         _check(_lib().jfnk_norm2(self.h, _ptr(x), n, _ptr(out), _stream(stream)), "jfnk_norm2")
 
     def eos_pressure(self, E, p, stream=None):
+        _vec(E, 0, "E", at_least=True)
+        _vec(p, E.numel(), "p", at_least=True)
         _check(_lib().jfnk_eos_pressure(self.h, _ptr(E), E.numel(), _ptr(p), _stream(stream)),
                "jfnk_eos_pressure")
 
     def tangent_product(self, U, y, adt, out, stream=None):
+        self._states(U=U, y=y, out=out)
         _check(_lib().jfnk_tangent_product(self.h, _ptr(U), _ptr(y), float(adt), _ptr(out), _stream(stream)),
                "jfnk_tangent_product")
 
     def time_operator(self, which, U, y, reps, stream=None):
+        self._states(U=U, y=y)
         ms = (C.c_double * 2)()
         _check(_lib().jfnk_time_operator(self.h, int(which), _ptr(U), _ptr(y), int(reps), ms, _stream(stream)),
                "jfnk_time_operator")
         return ms[0], ms[1]
 
+    def _states(self, **arrays):
+        """Every given array is a float64 state-sized vector (N elements)."""
+        for name, t in arrays.items():
+            _vec(t, self.N, name)
+
+    def _fv_size(self, level):
+        X, Z = C.c_int(), C.c_int()
+        _check(_lib().jfnk_fv_level_size(self.h, int(level), C.byref(X), C.byref(Z)), "jfnk_fv_level_size")
+        return 4 * X.value * Z.value
+
     def jfnk_autotune(self, U, y, reps=3, stream=None):
+        self._states(U=U, y=y)
         best = (C.c_int * 4)()
         ms = (C.c_double * 2)()
         _check(_lib().jfnk_autotune(self.h, _ptr(U), _ptr(y), int(reps), best, ms, _stream(stream)),
@@ -316,11 +368,18 @@ class Context:
         return out
 
     def transfer_to_fv(self, u, v, stream=None):
+        self._states(u=u)
+        _vec(v, self._fv_size(0), "v")
         _check(_lib().jfnk_transfer_to_fv(self.h, _ptr(u), _ptr(v), _stream(stream)), "jfnk_transfer_to_fv")
 
     def transfer_to_dg(self, v, u, stream=None):
+        self._states(u=u)
+        _vec(v, self._fv_size(0), "v")
         _check(_lib().jfnk_transfer_to_dg(self.h, _ptr(v), _ptr(u), _stream(stream)), "jfnk_transfer_to_dg")
 
     def fv_residual(self, level, u, f, stream=None):
+        n = self._fv_size(level)
+        _vec(u, n, "u")
+        _vec(f, n, "f")
         _check(_lib().jfnk_fv_residual(self.h, int(level), _ptr(u), _ptr(f), _stream(stream)),
                "jfnk_fv_residual")

@@ -124,3 +124,36 @@ def test_create_rejects_invalid_arguments_before_any_device_call(libpath):
         c.close()
     except JfnkError as e:
         assert e.code == -3, e.code
+
+
+def test_context_wrappers_reject_wrong_dtype_or_length_before_any_launch():
+    # every array the library receives is indexed by the context's sizes: the
+    # binding refuses a float32 array, a short one and a wrong member count
+    # before it calls the library (objects built without a library context, so
+    # a call that got through would fail on the null handle instead)
+    torch = pytest.importorskip("torch")
+    from paper_2505_24504_gb300 import jfnk
+    ctx = object.__new__(jfnk.Context)
+    ctx.N, ctx.h = 64, None
+    good = torch.zeros(64, dtype=torch.float64)
+    short = torch.zeros(63, dtype=torch.float64)
+    f32 = torch.zeros(64, dtype=torch.float32)
+    calls = [
+        lambda: ctx.dg_residual(short, good), lambda: ctx.dg_residual(good, f32),
+        lambda: ctx.jv_product(good, None, short, 1.0, 0.0, good), lambda: ctx.jv_product(good, f32, good, 1.0, 0.0, good),
+        lambda: ctx.mg_precondition(good, 1.0, good, f32), lambda: ctx.implicit_step(short, 1.0),
+        lambda: ctx.implicit_step(f32, 1.0), lambda: ctx.tangent_product(good, good, 1.0, short),
+        lambda: ctx.jfnk_init_state(good, good), lambda: ctx.eos_pressure(good, short),
+        lambda: ctx.time_operator(1, good, f32, 1), lambda: ctx.jfnk_autotune(short, good),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="float64|elements"):
+            call()
+    b = object.__new__(jfnk.Batch)
+    b.contexts, b.h = [ctx, ctx], None
+    with pytest.raises(ValueError, match="members"):
+        b.jfnk_batch_step([good], [1.0], [1])
+    with pytest.raises(ValueError, match="elements"):
+        b.jfnk_batch_step([good, short], [1.0, 1.0], [1, 1])
+    with pytest.raises(ValueError, match="float64"):
+        b.jfnk_batch_dg_residual([good, good], [good, f32])
